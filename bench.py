@@ -1,0 +1,341 @@
+"""Benchmark: OBK-RCM time to solution on one GB300 (and replicas on N GPUs).
+
+Workload (default): the symmetrised 12-nearest-neighbour matrix of n =
+1,000,000 points uniform in the unit cube (off-diagonals N(0,1), diagonal 1.2 x
+the row's absolute off-diagonal sum, scattered by a random relabelling),
+x* ~ N(0,1), f = A x*, cosine threshold 0.1, FP64, stop at
+||f - A x|| / ||f|| <= 1e-8.
+
+One step = the whole hot path through the C ABI on inputs resident in HBM:
+obk_create (extension, RCM, permutation, row norms, grouping, layout) +
+obk_solve (sweeps to tolerance with residual checks, un-permutation).
+K steps are timed with CUDA events on the library's stream between barriers.
+The matrix (190 MB) is larger than L2 (129 MB), so no explicit flush is done.
+
+Also reported: e2e (the same step with host buffers: H2D of A and f and D2H
+of x inside the timed region), the sweep kernel's roofline (differential CUDA
+event timing of solves with 10 and 60 sweeps), the CPU oracle's time on this
+host (cpu_baseline) and SM clocks sampled during the timed region.
+
+`--impl reference` runs the CPU oracle on the same workload instead.
+N > 1 (torchrun): independent replicas, one system per rank, no collective on
+the data path (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+FP64_PEAK_TFLOPS = 1.25  # 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (nominal table)
+
+
+def workload(name: str, rank: int):
+    import synth
+
+    if name == "knn1m":
+        s = synth.knn_dominant(1_000_000, 12, seed=1001 + 100 * rank)
+        return s, dict(workload="knn_n1e6_12nn_fp64", n=1_000_000, knn=12, diag_factor=1.2, thr=0.1,
+                       tol=1e-8, precision="fp64")
+    if name == "dominant2000":
+        s = synth.random_dominant(2000, 7, seed=1000 + 100 * rank)
+        return s, dict(workload="random_dominant_n2000_fp64", n=2000, thr=0.1, tol=1e-8, precision="fp64")
+    if name == "knn200k":
+        s = synth.knn_dominant(200_000, 12, seed=1001 + 100 * rank)
+        return s, dict(workload="knn_n2e5_12nn_fp64", n=200_000, knn=12, thr=0.1, tol=1e-8, precision="fp64")
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=2)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [t.strip() for t in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(MEASURED) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def run_reference(args, cfg, s):
+    """The CPU oracle on the same workload (rank 0 only)."""
+    import oracle
+
+    A = s.A
+    oracle.build()
+    nrun = max(1, min(args.steps, 3))
+    t_all = []
+    info = None
+    for _ in range(nrun):
+        t0 = time.perf_counter()
+        st, x, info = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=cfg["thr"], tol=cfg["tol"],
+                                   maxit=10000)
+        t_all.append(time.perf_counter() - t0)
+    v = float(np.mean(t_all))
+    sample = (f"{nrun} full oracle solve(s) of the workload (of {args.steps} requested steps; "
+              f"{info.sweeps} sweeps, single-threaded plain C)")
+    line = {"metric": "time_to_solution", "value": v, "unit": "s", "higher_is_better": False,
+            "impl": "reference", "n_gpus": args.gpus, "steps": nrun, "warmup": 0, "ms_per_step": v * 1e3,
+            "dtype": "f64", "data": "synthetic", "config": cfg, "scaling": "weak", "vs_baseline": None,
+            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="knn1m")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        s, cfg = workload(args.workload, 0)
+        run_reference(args, cfg, s)
+        return
+
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    import paper_2401_00672_gb300 as obk
+
+    s, cfg = workload(args.workload, rank)
+    A = s.A
+    dev = torch.device("cuda", local_rank)
+    rp = torch.from_numpy(A.row_ptr).to(dev)
+    ci = torch.from_numpy(A.col_idx).to(dev)
+    v = torch.from_numpy(A.val).to(dev)
+    f = torch.from_numpy(s.f).to(dev)
+    x = torch.empty(A.n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    tol = cfg["tol"]
+
+    def step():
+        h = obk.Handle(rp, ci, v, A.m, A.n, thr=cfg["thr"], stream=stream.cuda_stream)
+        st, _, info = h.solve(f, None, tol=tol, maxit=10000, out=x)
+        h.close()
+        return st, info
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 0)):
+        st, info = step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    launches0 = obk.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        st, info = step()
+        infos.append((st, info))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    launches = obk.kernel_launches() - launches0
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st, info = infos[-1]
+    xh = x.cpu().numpy()
+    err_xstar = float(np.linalg.norm(xh - s.xstar) / np.linalg.norm(s.xstar))
+
+    # roofline of the sweep kernel: two solves on one prepared handle, 10 and 60
+    # sweeps with a residual only at start and end; the difference is 50 sweeps
+    h = obk.Handle(rp, ci, v, A.m, A.n, thr=cfg["thr"], stream=stream.cuda_stream)
+    N, nnz_gm = h.N, A.nnz
+    per = {}
+    for k in (10, 60):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        best = None
+        for _ in range(3):
+            e0.record(stream)
+            h.solve(f, None, tol=1e-300, maxit=k, out=x, opts=obk.Opts(check_every=1 << 30))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_ = e0.elapsed_time(e1)
+            best = t_ if best is None else min(best, t_)
+        per[k] = best
+    h.close()
+    sweep_ms = (per[60] - per[10]) / 50.0
+    # algorithmic bytes of one sweep: A read once (8 B value + 4 B column per
+    # entry), row pointers (4 B/row as int32), f and 1/||A_i||^2 (8 + 8 B/row),
+    # x read and written (16 B/row)
+    bytes_sweep = 12.0 * nnz_gm + 4.0 * (N + 1) + 8.0 * N + 8.0 * N + 16.0 * N
+    flops_sweep = 4.0 * nnz_gm  # one multiply-add per entry in each of the two phases
+    hbm_peak, hbm_src = peaks()
+    gbs = bytes_sweep / (sweep_ms * 1e-3) / 1e9
+    tfs = flops_sweep / (sweep_ms * 1e-3) / 1e12
+    frac_hbm = gbs / hbm_peak
+    frac_alu = tfs / FP64_PEAK_TFLOPS
+    if frac_alu >= frac_hbm:
+        roof = {"bound": "alu", "achieved": round(tfs, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": round(frac_alu, 4), "traffic": None,
+                "peak_source": "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)",
+                "kernel": "obk_solve_kernel (sweep phases)", "hbm_frac_of_measured": round(frac_hbm, 4)}
+    else:
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(frac_hbm, 4), "traffic": None, "peak_source": hbm_src,
+                "kernel": "obk_solve_kernel (sweep phases)", "alu_frac_of_nominal_fp64": round(frac_alu, 4)}
+    roof["sweep_ms"] = round(sweep_ms, 5)
+    roof["bytes_per_sweep"] = bytes_sweep
+
+    e2e = None
+    if not args.no_e2e:
+        # same step through the C ABI with pinned host buffers
+        rp_h = torch.from_numpy(A.row_ptr).pin_memory()
+        ci_h = torch.from_numpy(A.col_idx).pin_memory()
+        v_h = torch.from_numpy(A.val).pin_memory()
+        f_h = torch.from_numpy(s.f).pin_memory()
+        x_h = torch.empty(A.n, dtype=torch.float64).pin_memory()
+        k2 = max(1, min(args.steps, 3))
+
+        def step_host():
+            hh = obk.Handle(rp_h, ci_h, v_h, A.m, A.n, thr=cfg["thr"], stream=stream.cuda_stream)
+            hh.solve(f_h, None, tol=tol, maxit=10000, out=x_h)
+            hh.close()
+
+        step_host()
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k2):
+            step_host()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1) / k2
+        if dist is not None:
+            t = torch.tensor([ems], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        h2d = A.row_ptr.nbytes + A.col_idx.nbytes + A.val.nbytes + s.f.nbytes
+        e2e = {"value": ems / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(A.n * 8), "steps": k2}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        t0 = time.perf_counter()
+        st_o, x_o, io = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=cfg["thr"], tol=tol,
+                                     maxit=10000)
+        t_cpu = time.perf_counter() - t0
+        par = float(np.linalg.norm(xh - x_o) / np.linalg.norm(x_o))
+        cpu = {"value": t_cpu, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": f"one full solve of the workload ({io.sweeps} sweeps), single-threaded plain C",
+               "x_rel_diff_vs_gpu": par, "oracle_sweeps": io.sweeps}
+
+    if rank == 0:
+        line = {
+            "metric": "time_to_solution", "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(cfg, parallelism=f"replicas{world}", l2="inputs larger than L2 (A = "
+                           f"{(A.val.nbytes + A.col_idx.nbytes) / 1e6:.0f} MB), no flush"),
+            "throughput_solves_per_s": world * 1e3 / ms,
+            "sweeps": info.sweeps, "groups": info.groups, "setup_ms": info.setup_ms, "solve_ms": info.solve_ms,
+            "rel_res": info.rel_res, "status": st, "x_err_vs_xstar": err_xstar,
+            "bandwidth": [info.bandwidth_before, info.bandwidth_after],
+            "gpu_launches": int(launches // max(args.steps, 1)), "gpu_launches_timed_region": int(launches),
+            "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

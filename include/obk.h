@@ -1,0 +1,189 @@
+/*
+ * obk.h -- C ABI of the GB300 OBK-RCM library (libobk.so).
+ *
+ * OBK-RCM (Liang & Li, arXiv 2401.00672) solves a sparse linear system
+ * A x = f with A in R^{m x n} (Eq. 1.1) by an orthogonal-block Kaczmarz
+ * iteration: reorder with Reverse Cuthill-McKee (Section 3.2, Eq. 3.1-3.2),
+ * group mutually near-orthogonal rows by a cosine threshold (Section 3.3), and
+ * project x onto one group at a time (Eq. 1.3 / Eq. 3.3, Algorithm 4).  For
+ * m != n the square extended matrices of Section 4 are used (Algorithm 5:
+ * [A, O] for m > n; Algorithm 6: [A; O] for m < n).
+ *
+ * Every call is synchronous unless stated: it returns after its GPU work has
+ * finished.  All pointers are borrowed for the duration of the call only; the
+ * library copies what it keeps.  Host/device placement of the f, x0 and x_out
+ * vectors is detected per pointer (cudaPointerGetAttributes): device or
+ * managed memory is used in place, anything else is treated as host memory.
+ * A handle or server must not be used from two threads at once.  No call
+ * aborts the process; on error a message is available from obk_last_error().
+ */
+#ifndef OBK_H
+#define OBK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define OBK_API __attribute__((visibility("default")))
+#else
+#define OBK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OBK_OK = 0,              /* converged (rel. residual <= tol) / success        */
+    OBK_NOT_CONVERGED = 1,   /* maxit reached or stagnation; x and info are valid */
+    OBK_PENDING = 2,         /* obk_poll: request not finished yet                */
+    OBK_ERR_INVALID = -1,    /* bad argument or malformed CSR                     */
+    OBK_ERR_NOMEM = -2,      /* device or host allocation failed                  */
+    OBK_ERR_BUDGET = -3,     /* request can never fit the server's HBM budget     */
+    OBK_ERR_TIMEOUT = -4,    /* a bounded device wait expired (kernel returned)   */
+    OBK_ERR_CUDA = -5,       /* CUDA runtime error (message in obk_last_error)    */
+    OBK_ERR_CANCELLED = -6,  /* request cancelled before it finished              */
+    OBK_ERR_NOT_FOUND = -7   /* unknown ticket                                    */
+} obk_status;
+
+/* Sparse matrix in CSR form, 0-based.  row_ptr has m+1 monotone entries from 0
+ * to nnz; columns strictly increase inside each row (sorted, no duplicates);
+ * values are finite.  device_ptrs = 1 when the three arrays live in device
+ * memory of the current device, 0 for host memory. */
+typedef struct {
+    const int64_t* row_ptr;
+    const int32_t* col_idx;
+    const double* val;
+    int64_t nnz;
+    int32_t device_ptrs;
+} obk_csr;
+
+typedef struct obk_handle obk_handle;
+typedef struct obk_server obk_server;
+
+/* Solve options.  Zero-initialised fields take the defaults given. */
+typedef struct {
+    int32_t precision;      /* 0 = FP64 sweeps (default); 1 = FP32 inner sweeps with
+                               FP64 iterative refinement (residual, norms, correction) */
+    int32_t check_every;    /* FP64: residual checked after every check_every-th sweep
+                               (default 1)                                             */
+    int32_t inner_sweeps;   /* precision 1: FP32 sweeps per refinement step (0 = auto)  */
+    int32_t max_outer;      /* precision 1: refinement steps at most (0 = 100)          */
+    double stagnation;      /* FP64: stop with OBK_NOT_CONVERGED when the relative
+                               residual moved less than this over 10 checks (0 = off)  */
+    int64_t timeout_spins;  /* bound on every device-side wait (0 = default, ~seconds) */
+    int32_t rows_per_warp;  /* sweep kernel: rows handled by one warp (0 = autotune)    */
+    int32_t reserved;
+} obk_opts;
+
+typedef struct {
+    int64_t sweeps;           /* sweeps performed (FP32 inner sweeps for precision 1)  */
+    double rel_res;           /* ||f - A x|| / ||f|| at the last check (FP64)          */
+    double setup_ms;          /* obk_create device time (extend, RCM, groups, layout)  */
+    double solve_ms;          /* obk_solve device time                                 */
+    int64_t groups;           /* number of row groups G                                */
+    int64_t bandwidth_before; /* half bandwidth of the (extended) input                */
+    int64_t bandwidth_after;  /* half bandwidth after the RCM permutation              */
+    int64_t outer_iters;      /* precision 1: refinement steps                          */
+    double sweep_ms;          /* device time inside the sweep loop                     */
+    int64_t n_conflicts;      /* row pairs (i > j) with |cos| >= threshold             */
+    int32_t status;           /* obk_status of the solve                               */
+    int32_t reserved;
+} obk_info;
+
+/* Create a solver for A (m x n) with cosine threshold thr in (0, 1].
+ * Copies A to the device, builds the extended square matrix (Section 4) when
+ * m != n, computes the RCM permutation (Section 3.2), the permuted matrix
+ * (Eq. 3.1), row norms ||A_i||^2 (Eq. 1.2), the row groups under
+ * |cos| >= thr conflicts (Section 3.3) and the sweep layout.  Uses the current
+ * CUDA device.  Errors: OBK_ERR_INVALID (m, n <= 0; thr outside (0, 1];
+ * malformed CSR; NaN/Inf values), OBK_ERR_NOMEM, OBK_ERR_CUDA, OBK_ERR_TIMEOUT.
+ * On success *out owns all device memory it uses until obk_destroy. */
+OBK_API obk_status obk_create(const obk_csr* A, int64_t m, int64_t n, double thr, obk_handle** out);
+
+/* Same as obk_create, with work issued on `stream` (a cudaStream_t; NULL = the
+ * library's own stream). */
+OBK_API obk_status obk_create_on_stream(const obk_csr* A, int64_t m, int64_t n, double thr,
+                                void* stream, obk_handle** out);
+
+/* Solve A x = f (Algorithm 4; Algorithms 5-6 when m != n) from x0.
+ * f: m values; x0: n values or NULL for x0 = 0; x_out: n values written with the
+ * result in the original ordering (x = P^T x~, then x^(1:n) for m > n).
+ * Stops after the first residual check with ||f - A x||/||f|| <= tol
+ * (OBK_OK), at maxit sweeps or on stagnation (OBK_NOT_CONVERGED, x valid).
+ * Errors: OBK_ERR_INVALID (tol <= 0, maxit < 1, NaN/Inf in f or x0),
+ * OBK_ERR_TIMEOUT, OBK_ERR_CUDA.  info may be NULL. */
+OBK_API obk_status obk_solve(obk_handle* h, const double* f, const double* x0, double tol, int64_t maxit,
+                     double* x_out, obk_info* info);
+
+/* obk_solve with options (opts may be NULL = defaults). */
+OBK_API obk_status obk_solve_ex(obk_handle* h, const obk_opts* opts, const double* f, const double* x0,
+                        double tol, int64_t maxit, double* x_out, obk_info* info);
+
+/* Setup results, for inspection and bit-exact comparisons.  All outputs are
+ * caller-allocated (host or device, detected per pointer).
+ *   obk_get_dims:   N (= max(m, n)), nnz, G.
+ *   obk_get_perm:   perm[N], perm[k] = original index placed at position k.
+ *   obk_get_groups: group_of[N] in permuted order (-1 for all-zero rows, which
+ *                   take no part in the iteration).
+ *   obk_get_row_norms: nsq[N], ||A~_k||^2 in permuted order (FP64, columns
+ *                   ascending, no fused multiply-add). */
+OBK_API obk_status obk_get_dims(const obk_handle* h, int64_t* N, int64_t* nnz, int64_t* G);
+OBK_API obk_status obk_get_perm(const obk_handle* h, int32_t* perm);
+OBK_API obk_status obk_get_groups(const obk_handle* h, int32_t* group_of);
+OBK_API obk_status obk_get_row_norms(const obk_handle* h, double* nsq);
+OBK_API obk_status obk_get_info(const obk_handle* h, obk_info* info);
+
+/* Residual check on its own: *rel_res = ||f - A x||_2 / ||f||_2 (or ||f - A x||_2
+ * when f = 0) for A (m x n) in CSR form, in FP64 (the stop rule of the solve).
+ * f has m and x has n values; A->device_ptrs says where A lives, f and x are
+ * detected per pointer.  The sum of squares is reduced deterministically: fixed
+ * tiles of 4096 rows, each summed in a fixed order, then the tiles in index
+ * order, so the result does not depend on the device or launch.  Allocates
+ * device scratch (two doubles per tile, plus copies of host inputs).
+ * Errors: OBK_ERR_INVALID (NULL pointers, m or n <= 0), OBK_ERR_NOMEM, OBK_ERR_CUDA. */
+OBK_API obk_status obk_residual(const obk_csr* A, int64_t m, int64_t n, const double* f, const double* x,
+                                double* rel_res);
+
+/* Release every resource of h (NULL is ignored). */
+OBK_API void obk_destroy(obk_handle* h);
+
+/* ---- request loop (continuous batching) ------------------------------ */
+
+/* Create a server that admits requests while the device memory they need fits
+ * hbm_budget_bytes (0 = 150 GB) and runs admitted requests concurrently on
+ * max_streams CUDA streams (0 = 8). */
+OBK_API obk_status obk_server_create(size_t hbm_budget_bytes, int32_t max_streams, obk_server** out);
+
+/* Queue one solve.  A, f and x0 (may be NULL) are copied before the call
+ * returns.  *ticket identifies the request for obk_poll.  Errors:
+ * OBK_ERR_INVALID, OBK_ERR_BUDGET (the request alone exceeds the budget). */
+OBK_API obk_status obk_submit(obk_server* s, const obk_csr* A, int64_t m, int64_t n, double thr,
+                      const double* f, const double* x0, double tol, int64_t maxit,
+                      const obk_opts* opts, uint64_t* ticket);
+
+/* Returns OBK_PENDING while the request runs; otherwise its final status, with
+ * x_out (n values, host) and info filled when not NULL.  A finished request is
+ * released by the first obk_poll that returns its final status. */
+OBK_API obk_status obk_poll(obk_server* s, uint64_t ticket, double* x_out, obk_info* info);
+
+/* Cancel a queued or running request (it finishes with OBK_ERR_CANCELLED). */
+OBK_API obk_status obk_cancel(obk_server* s, uint64_t ticket);
+
+/* Wait for every request, then release the server (NULL is ignored). */
+OBK_API void obk_server_destroy(obk_server* s);
+
+/* Last error message of the calling thread ("" if none). */
+OBK_API const char* obk_last_error(void);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all handles and servers together). */
+OBK_API int64_t obk_kernel_launches(void);
+
+/* Library version string. */
+OBK_API const char* obk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OBK_H */

@@ -1,0 +1,278 @@
+"""GB300 OBK-RCM: Python binding of the C ABI in ``include/obk.h``.
+
+Argument marshalling only: every step of the method (extension, RCM, grouping,
+sweeps, residual checks, refinement, request loop) runs in ``libobk.so``'s CUDA
+kernels.  Arrays may be numpy arrays (host memory) or CUDA torch tensors (device
+memory of the current device); PyTorch is used only for device memory and
+streams.  There is no CPU fallback: importing this package without the built
+library raises ``ImportError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libobk.so")
+
+OBK_OK, OBK_NOT_CONVERGED, OBK_PENDING = 0, 1, 2
+OBK_ERR_INVALID, OBK_ERR_NOMEM, OBK_ERR_BUDGET = -1, -2, -3
+OBK_ERR_TIMEOUT, OBK_ERR_CUDA, OBK_ERR_CANCELLED, OBK_ERR_NOT_FOUND = -4, -5, -6, -7
+
+EXPORTS = [
+    "obk_create", "obk_create_on_stream", "obk_solve", "obk_solve_ex", "obk_get_dims", "obk_get_perm",
+    "obk_get_groups", "obk_get_row_norms", "obk_get_info", "obk_destroy", "obk_server_create",
+    "obk_submit", "obk_poll", "obk_cancel", "obk_server_destroy", "obk_last_error", "obk_version",
+    "obk_kernel_launches", "obk_residual",
+]
+
+
+class ObkError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class _Csr(ctypes.Structure):
+    _fields_ = [("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("nnz", ctypes.c_int64), ("device_ptrs", ctypes.c_int32)]
+
+
+class Opts(ctypes.Structure):
+    """obk_opts (see include/obk.h); zero fields take the library defaults."""
+    _fields_ = [("precision", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("inner_sweeps", ctypes.c_int32), ("max_outer", ctypes.c_int32),
+                ("stagnation", ctypes.c_double), ("timeout_spins", ctypes.c_int64),
+                ("rows_per_warp", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int64), ("rel_res", ctypes.c_double), ("setup_ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double), ("groups", ctypes.c_int64),
+                ("bandwidth_before", ctypes.c_int64), ("bandwidth_after", ctypes.c_int64),
+                ("outer_iters", ctypes.c_int64), ("sweep_ms", ctypes.c_double),
+                ("n_conflicts", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+@dataclasses.dataclass
+class Info:
+    sweeps: int
+    rel_res: float
+    setup_ms: float
+    solve_ms: float
+    groups: int
+    bandwidth_before: int
+    bandwidth_after: int
+    outer_iters: int
+    sweep_ms: float
+    n_conflicts: int
+    status: int
+
+
+def _info(ci: _Info) -> Info:
+    return Info(*(getattr(ci, f[0]) for f in _Info._fields_ if f[0] != "reserved"))
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libobk.so is not built ({LIB_PATH}); run __graft_entry__.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    sig = {
+        "obk_create": ([vp, i64, i64, dbl, vp], ctypes.c_int),
+        "obk_create_on_stream": ([vp, i64, i64, dbl, vp, vp], ctypes.c_int),
+        "obk_solve": ([vp, vp, vp, dbl, i64, vp, vp], ctypes.c_int),
+        "obk_solve_ex": ([vp, vp, vp, vp, dbl, i64, vp, vp], ctypes.c_int),
+        "obk_get_dims": ([vp, vp, vp, vp], ctypes.c_int),
+        "obk_get_perm": ([vp, vp], ctypes.c_int),
+        "obk_get_groups": ([vp, vp], ctypes.c_int),
+        "obk_get_row_norms": ([vp, vp], ctypes.c_int),
+        "obk_get_info": ([vp, vp], ctypes.c_int),
+        "obk_destroy": ([vp], None),
+        "obk_server_create": ([ctypes.c_size_t, i32, vp], ctypes.c_int),
+        "obk_submit": ([vp, vp, i64, i64, dbl, vp, vp, dbl, i64, vp, vp], ctypes.c_int),
+        "obk_poll": ([vp, ctypes.c_uint64, vp, vp], ctypes.c_int),
+        "obk_cancel": ([vp, ctypes.c_uint64], ctypes.c_int),
+        "obk_server_destroy": ([vp], None),
+        "obk_last_error": ([], ctypes.c_char_p),
+        "obk_version": ([], ctypes.c_char_p),
+        "obk_kernel_launches": ([], ctypes.c_int64),
+        "obk_residual": ([vp, i64, i64, vp, vp, vp], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def kernel_launches() -> int:
+    """CUDA kernels launched by libobk.so in this process so far."""
+    return int(lib.obk_kernel_launches())
+
+
+def last_error() -> str:
+    return lib.obk_last_error().decode()
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise ObkError(rc, f"{what}: {last_error()}")
+    return rc
+
+
+def _ptr(a, dtype):
+    """(pointer, is_device, keepalive) for a numpy array or a CUDA torch tensor."""
+    if a is None:
+        return None, False, None
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        import torch
+
+        want = {np.float64: torch.float64, np.int64: torch.int64, np.int32: torch.int32}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {want} tensor")
+        return ctypes.c_void_p(a.data_ptr()), bool(a.is_cuda), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data_as(ctypes.c_void_p), False, arr
+
+
+class Handle:
+    """One system A (m x n) prepared on the GPU: obk_create ... obk_destroy."""
+
+    def __init__(self, row_ptr, col_idx, val, m: int, n: int, thr: float = 0.1, stream=None):
+        p_rp, d1, k1 = _ptr(row_ptr, np.int64)
+        p_ci, d2, k2 = _ptr(col_idx, np.int32)
+        p_v, d3, k3 = _ptr(val, np.float64)
+        if not (d1 == d2 == d3):
+            raise TypeError("row_ptr, col_idx and val must all be host or all be device arrays")
+        nnz = int(k1[-1]) if not d1 else int(k1[-1].item())
+        self._csr = _Csr(p_rp, p_ci, p_v, nnz, 1 if d1 else 0)
+        self._h = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream) if stream else None
+        _check(lib.obk_create_on_stream(ctypes.byref(self._csr), m, n, float(thr), st, ctypes.byref(self._h)),
+               "obk_create")
+        self.m, self.n = m, n
+        N, nz, G = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        lib.obk_get_dims(self._h, ctypes.byref(N), ctypes.byref(nz), ctypes.byref(G))
+        self.N, self.nnz, self.G = N.value, nz.value, G.value
+
+    def solve(self, f, x0=None, tol: float = 1e-8, maxit: int = 1000, out=None, opts: Opts | None = None):
+        """Returns (status, x, Info); x is numpy unless `out` (a CUDA tensor) is given."""
+        pf, _, kf = _ptr(f, np.float64)
+        px, _, kx = _ptr(x0, np.float64)
+        if out is None:
+            out = np.empty(self.n, np.float64)
+        po, _, ko = _ptr(out, np.float64)
+        info = _Info()
+        rc = lib.obk_solve_ex(self._h, ctypes.byref(opts) if opts is not None else None, pf, px, float(tol),
+                              int(maxit), po, ctypes.byref(info))
+        _check(rc, "obk_solve")
+        return rc, ko, _info(info)
+
+    def _get(self, fn, dtype):
+        a = np.empty(self.N, dtype)
+        _check(fn(self._h, a.ctypes.data_as(ctypes.c_void_p)), fn.__name__)
+        return a
+
+    def perm(self) -> np.ndarray:
+        return self._get(lib.obk_get_perm, np.int32)
+
+    def groups(self) -> np.ndarray:
+        return self._get(lib.obk_get_groups, np.int32)
+
+    def row_norms(self) -> np.ndarray:
+        return self._get(lib.obk_get_row_norms, np.float64)
+
+    def info(self) -> Info:
+        i = _Info()
+        _check(lib.obk_get_info(self._h, ctypes.byref(i)), "obk_get_info")
+        return _info(i)
+
+    def close(self):
+        if self._h:
+            lib.obk_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def residual(row_ptr, col_idx, val, m, n, f, x) -> float:
+    """obk_residual: ||f - A x|| / ||f|| in FP64 (deterministic tile reduction)."""
+    p_rp, dev, k1 = _ptr(row_ptr, np.int64)
+    p_ci, _, k2 = _ptr(col_idx, np.int32)
+    p_v, _, k3 = _ptr(val, np.float64)
+    nnz = int(k1[-1]) if not dev else int(k1[-1].item())
+    csr = _Csr(p_rp, p_ci, p_v, nnz, 1 if dev else 0)
+    pf, _, kf = _ptr(f, np.float64)
+    px, _, kx = _ptr(x, np.float64)
+    out = ctypes.c_double()
+    _check(lib.obk_residual(ctypes.byref(csr), m, n, pf, px, ctypes.byref(out)), "obk_residual")
+    return out.value
+
+
+def solve(row_ptr, col_idx, val, m, n, f, x0=None, thr=0.1, tol=1e-8, maxit=1000, opts=None):
+    """One-shot obk_create + obk_solve + obk_destroy; returns (status, x, Info)."""
+    with Handle(row_ptr, col_idx, val, m, n, thr) as h:
+        return h.solve(f, x0, tol, maxit, opts=opts)
+
+
+class Server:
+    """Request loop (obk_server_*): submit systems, poll for results."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, max_streams: int = 0):
+        self._s = ctypes.c_void_p()
+        _check(lib.obk_server_create(int(hbm_budget_bytes), int(max_streams), ctypes.byref(self._s)),
+               "obk_server_create")
+
+    def submit(self, row_ptr, col_idx, val, m, n, f, x0=None, thr=0.1, tol=1e-8, maxit=1000,
+               opts: Opts | None = None) -> int:
+        p_rp, dev, k1 = _ptr(row_ptr, np.int64)
+        p_ci, _, k2 = _ptr(col_idx, np.int32)
+        p_v, _, k3 = _ptr(val, np.float64)
+        nnz = int(k1[-1]) if not dev else int(k1[-1].item())
+        csr = _Csr(p_rp, p_ci, p_v, nnz, 1 if dev else 0)
+        pf, _, kf = _ptr(f, np.float64)
+        px, _, kx = _ptr(x0, np.float64)
+        t = ctypes.c_uint64()
+        _check(lib.obk_submit(self._s, ctypes.byref(csr), m, n, float(thr), pf, px, float(tol), int(maxit),
+                              ctypes.byref(opts) if opts is not None else None, ctypes.byref(t)), "obk_submit")
+        return t.value
+
+    def poll(self, ticket: int, n: int):
+        """(status, x or None, Info or None); status OBK_PENDING while running."""
+        x = np.empty(n, np.float64)
+        info = _Info()
+        rc = lib.obk_poll(self._s, ctypes.c_uint64(ticket), x.ctypes.data_as(ctypes.c_void_p), ctypes.byref(info))
+        if rc == OBK_PENDING:
+            return rc, None, None
+        return rc, x, _info(info)
+
+    def cancel(self, ticket: int) -> int:
+        return lib.obk_cancel(self._s, ctypes.c_uint64(ticket))
+
+    def close(self):
+        if self._s:
+            lib.obk_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,571 @@
+// capi.cu -- the C ABI declared in include/obk.h: handles, solves, setup
+// queries and device plumbing (extension to a square system, permutation of
+// the right-hand side, un-permutation of the result).
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/obk.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace obk {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+DevInfo dev_info()
+{
+    static std::mutex mu;
+    static std::vector<DevInfo> cache;
+    int dev = 0;
+    OBK_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& d : cache)
+        if (d.device == dev) return d;
+    DevInfo d{};
+    d.device = dev;
+    int v = 0;
+    OBK_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+    d.sms = v;
+    OBK_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev));
+    d.l2_bytes = (size_t)v;
+    OBK_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    d.smem_optin = (size_t)v;
+    cache.push_back(d);
+    return d;
+}
+
+namespace {
+
+constexpr int kBlock = 256;
+inline unsigned grid_for(int64_t n) { return (unsigned)std::min<int64_t>(ceil_div(n, kBlock) + 1, 65535); }
+
+#define GRID_STRIDE(i, n)                                                              \
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); \
+         i += (int64_t)gridDim.x * blockDim.x)
+
+__global__ void extend_rowptr(int64_t m, int64_t N, int64_t nnz, int64_t* rp)
+{
+    GRID_STRIDE(k, N - m) rp[m + 1 + k] = nnz;
+}
+
+__global__ void check_rowptr_ends(const int64_t* rp, int64_t m, int64_t nnz, int* bad)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0 && (rp[0] != 0 || rp[m] != nnz)) atomicOr(bad, 16);
+}
+
+__global__ void check_finite(const double* a, int64_t n, int* bad)
+{
+    GRID_STRIDE(i, n) if (!isfinite(a[i])) atomicOr(bad, 32);
+}
+
+__global__ void gather_gm(int64_t Ngm, const int32_t* src, const double* f, int64_t m, double* out)
+{
+    GRID_STRIDE(k, Ngm)
+    {
+        int32_t o = src[k];
+        out[k] = o < m ? f[o] : 0.0;
+    }
+}
+
+__global__ void permute_x0(int64_t N, const int32_t* perm, const double* x0, int64_t n, double* x)
+{
+    GRID_STRIDE(k, N)
+    {
+        int32_t o = perm[k];
+        x[k] = (x0 && o < n) ? x0[o] : 0.0;
+    }
+}
+
+__global__ void unpermute_x(int64_t N, const int32_t* perm, const double* x, int64_t n, double* out)
+{
+    GRID_STRIDE(k, N)
+    {
+        int32_t o = perm[k];
+        if (o < n) out[o] = x[k];
+    }
+}
+
+__global__ void compose_src(int64_t Ngm, const int32_t* grp_row, const int32_t* perm, int32_t* src)
+{
+    GRID_STRIDE(k, Ngm) src[k] = perm[grp_row[k]];
+}
+
+__global__ void zero_row_flags(int64_t N, const int32_t* group_of, int32_t* flag)
+{
+    GRID_STRIDE(k, N) flag[k] = group_of[k] < 0 ? 1 : 0;
+}
+
+__global__ void zero_row_list(int64_t N, const int32_t* flag, const int64_t* scan, const int32_t* perm,
+                              int32_t* out)
+{
+    GRID_STRIDE(k, N) if (flag[k]) out[scan[k]] = perm[k];
+}
+
+// deterministic sum of squares: fixed grid, fixed per-thread order, ordered final pass
+constexpr int kRedBlocks = 256;
+__global__ void sumsq_partial(const double* a, const int32_t* idx, int64_t n, int64_t m, double* part)
+{
+    __shared__ double ws[kBlock / 32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = idx ? idx[i] : i;
+        double v = j < m ? a[j] : 0.0;
+        s = fma(v, v, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kBlock / 32; ++k) t += ws[k];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void sumsq_final(const double* part, double* out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kRedBlocks; ++k) t += part[k];
+        *out = t;
+    }
+}
+
+double sum_squares(const double* a, const int32_t* idx, int64_t n, int64_t m, cudaStream_t st)
+{
+    if (n <= 0) return 0.0;
+    DBuf<double> part(kRedBlocks + 1, st);
+    sumsq_partial<<<kRedBlocks, kBlock, 0, st>>>(a, idx, n, m, part.p);
+    OBK_CHECK_LAUNCH();
+    sumsq_final<<<1, 32, 0, st>>>(part.p, part.p + kRedBlocks);
+    OBK_CHECK_LAUNCH();
+    return read_scalar(part.p + kRedBlocks, st);
+}
+
+// ---- residual check with per-tile partial sums ----------------------------
+// Tile t covers rows [t*kResTile, (t+1)*kResTile); one block per tile, one warp
+// per row, lanes over the row's entries; the block sums its rows' r^2 and f^2
+// in a fixed order.  part[2t] = sum r^2, part[2t+1] = sum f^2.
+constexpr int kResTile = 4096;
+__global__ void residual_tiles(int64_t m, const int64_t* rp, const int32_t* ci, const double* v, const double* f,
+                               const double* x, double* part)
+{
+    __shared__ double wr[kBlock / 32], wf[kBlock / 32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t r0 = (int64_t)blockIdx.x * kResTile, r1 = r0 + kResTile < m ? r0 + kResTile : m;
+    double sr = 0.0, sf = 0.0;
+    for (int64_t i = r0 + w; i < r1; i += kBlock / 32) {
+        double acc = 0.0;
+        for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += 32) acc = fma(v[e], x[ci[e]], acc);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        double r = f[i] - acc;
+        sr = fma(r, r, sr);
+        sf = fma(f[i], f[i], sf);
+    }
+    if (lane == 0) { wr[w] = sr; wf[w] = sf; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < kBlock / 32; ++k) { a += wr[k]; b += wf[k]; }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+__global__ void residual_final(const double* part, int64_t ntiles, double* out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int64_t t = 0; t < ntiles; ++t) { a += part[2 * t]; b += part[2 * t + 1]; }
+        *out = b > 0.0 ? sqrt(a) / sqrt(b) : sqrt(a);
+    }
+}
+
+bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copy n elements into a device buffer, from host or device memory.
+template <class T>
+void to_device(T* dst, const T* src, int64_t n, bool src_dev, cudaStream_t st)
+{
+    if (n <= 0) return;
+    OBK_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(T), src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             st));
+}
+
+struct Timer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaStream_t s;
+    explicit Timer(cudaStream_t st) : s(st)
+    {
+        OBK_CUDA(cudaEventCreate(&a));
+        OBK_CUDA(cudaEventCreate(&b));
+        OBK_CUDA(cudaEventRecord(a, s));
+    }
+    double stop_ms()
+    {
+        float ms = 0.f;
+        OBK_CUDA(cudaEventRecord(b, s));
+        OBK_CUDA(cudaEventSynchronize(b));
+        OBK_CUDA(cudaEventElapsedTime(&ms, a, b));
+        return ms;
+    }
+    ~Timer()
+    {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+}  // namespace
+}  // namespace obk
+
+using namespace obk;
+
+struct obk_handle {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int64_t m = 0, n = 0, N = 0, nnz = 0;
+    double thr = 0.1;
+    DBuf<int32_t> perm;      // N
+    DBuf<int32_t> src_gm;    // Ngm: extended original index of each group-major row
+    DBuf<int32_t> zero_src;  // extended original indices of all-zero rows
+    int64_t n_zero = 0;
+    DBuf<int> err;
+    SweepLayout L;
+    obk_info info{};
+    RcmStats rcm{};
+};
+
+static obk_status fail(const Error& e)
+{
+    set_last_error(e.msg);
+    return (obk_status)e.status;
+}
+
+#define OBK_API_BEGIN try {
+#define OBK_API_END                                                            \
+    }                                                                          \
+    catch (const Error& e) { return fail(e); }                                 \
+    catch (const std::bad_alloc&) { return fail(Error{-2, "host allocation failed"}); } \
+    catch (...) { return fail(Error{-5, "unexpected internal error"}); }
+
+extern "C" {
+
+const char* obk_last_error(void) { return g_last_error.c_str(); }
+const char* obk_version(void) { return "obk-gb300 0.1 (sm_103a)"; }
+int64_t obk_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+obk_status obk_create_on_stream(const obk_csr* A, int64_t m, int64_t n, double thr, void* stream,
+                                obk_handle** out)
+{
+    OBK_API_BEGIN
+    set_last_error("");
+    if (!out) throw Error{-1, "out is NULL"};
+    *out = nullptr;
+    if (!A || m <= 0 || n <= 0) throw Error{-1, "m and n must be positive and A non-NULL"};
+    if (!(thr > 0.0 && thr <= 1.0)) throw Error{-1, "cos_threshold must lie in (0, 1]"};
+    if (A->nnz < 0 || (A->nnz > 0 && (!A->col_idx || !A->val)) || !A->row_ptr)
+        throw Error{-1, "malformed CSR arguments"};
+    if (std::max(m, n) >= (int64_t)INT32_MAX || A->nnz >= (int64_t)UINT32_MAX)
+        throw Error{-1, "dimensions exceed the 32-bit index range"};
+    obk_handle* h = new obk_handle();
+    try {
+        OBK_CUDA(cudaGetDevice(&h->device));
+        if (stream) {
+            h->st = (cudaStream_t)stream;
+        } else {
+            OBK_CUDA(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
+            h->own_stream = true;
+        }
+        cudaStream_t st = h->st;
+        Timer tm(st);
+        h->m = m;
+        h->n = n;
+        h->N = std::max(m, n);
+        h->nnz = A->nnz;
+        h->thr = thr;
+        int64_t N = h->N, nnz = A->nnz;
+        h->err.alloc(1, st);
+        OBK_CUDA(cudaMemsetAsync(h->err.p, 0, sizeof(int), st));
+        // device copy of A with the extended row pointer (Algorithms 5-6)
+        bool dev = A->device_ptrs != 0;
+        DBuf<int64_t> rp(N + 1, st);
+        DBuf<int32_t> ci(std::max<int64_t>(nnz, 1), st);
+        DBuf<double> v(std::max<int64_t>(nnz, 1), st);
+        to_device(rp.p, A->row_ptr, m + 1, dev, st);
+        to_device(ci.p, A->col_idx, nnz, dev, st);
+        to_device(v.p, A->val, nnz, dev, st);
+        DBuf<int> bad(1, st);
+        validate_csr(m, n, rp.p, ci.p, v.p, nnz, bad.p, st);
+        check_rowptr_ends<<<1, 32, 0, st>>>(rp.p, m, nnz, bad.p);
+        OBK_CHECK_LAUNCH();
+        int b = read_scalar(bad.p, st);
+        if (b) throw Error{-1, "malformed CSR (code " + std::to_string(b) +
+                                   ": 1 row_ptr, 2 column range, 4 unsorted/duplicate, 8 non-finite, "
+                                   "16 row_ptr ends)"};
+        if (N > m) {
+            extend_rowptr<<<grid_for(N - m), kBlock, 0, st>>>(m, N, nnz, rp.p);
+            OBK_CHECK_LAUNCH();
+        }
+        h->info.bandwidth_before = half_bandwidth(N, rp.p, ci.p, nnz, st);
+        // Reverse Cuthill-McKee (Section 3.2) and A~ = P A^ P^T (Eq. 3.1)
+        h->perm.alloc(N, st);
+        rcm_reorder(N, rp.p, ci.p, nnz, h->perm.p, kDefaultSpins, h->err.p, &h->rcm, st);
+        DBuf<int32_t> iperm(N, st);
+        DBuf<int64_t> rpt(N + 1, st);
+        DBuf<int32_t> cit(std::max<int64_t>(nnz, 1), st);
+        DBuf<double> vt(std::max<int64_t>(nnz, 1), st);
+        permute_csr(N, rp.p, ci.p, v.p, nnz, h->perm.p, iperm.p, rpt.p, cit.p, vt.p, st);
+        rp.release();
+        ci.release();
+        v.release();
+        h->info.bandwidth_after = half_bandwidth(N, rpt.p, cit.p, nnz, st);
+        // norms, groups and sweep layout (Section 3.3)
+        group_build(N, rpt.p, cit.p, vt.p, nnz, thr, kDefaultSpins, h->err.p, h->L, true, st);
+        h->info.groups = h->L.G;
+        h->info.n_conflicts = h->L.n_conflicts;
+        h->src_gm.alloc(std::max<int64_t>(h->L.Ngm, 1), st);
+        if (h->L.Ngm) {
+            compose_src<<<grid_for(h->L.Ngm), kBlock, 0, st>>>(h->L.Ngm, h->L.grp_row.p, h->perm.p, h->src_gm.p);
+            OBK_CHECK_LAUNCH();
+        }
+        DBuf<int32_t> zf(N, st);
+        DBuf<int64_t> zs(N + 1, st);
+        zero_row_flags<<<grid_for(N), kBlock, 0, st>>>(N, h->L.group_of.p, zf.p);
+        OBK_CHECK_LAUNCH();
+        exclusive_scan_i32_to_i64(zf.p, zs.p, N, st);
+        h->n_zero = read_scalar(zs.p + N, st);
+        h->zero_src.alloc(std::max<int64_t>(h->n_zero, 1), st);
+        zero_row_list<<<grid_for(N), kBlock, 0, st>>>(N, zf.p, zs.p, h->perm.p, h->zero_src.p);
+        OBK_CHECK_LAUNCH();
+        h->info.setup_ms = tm.stop_ms();
+        OBK_CUDA(cudaStreamSynchronize(st));
+    } catch (...) {
+        obk_destroy(h);
+        throw;
+    }
+    *out = h;
+    return OBK_OK;
+    OBK_API_END
+}
+
+obk_status obk_create(const obk_csr* A, int64_t m, int64_t n, double thr, obk_handle** out)
+{
+    return obk_create_on_stream(A, m, n, thr, nullptr, out);
+}
+
+obk_status obk_solve_ex(obk_handle* h, const obk_opts* opts, const double* f, const double* x0, double tol,
+                        int64_t maxit, double* x_out, obk_info* info)
+{
+    OBK_API_BEGIN
+    set_last_error("");
+    if (!h || !f || !x_out) throw Error{-1, "handle, f and x_out must be non-NULL"};
+    if (!(tol > 0.0) || maxit < 1) throw Error{-1, "tol must be > 0 and maxit >= 1"};
+    obk_opts o{};
+    if (opts) o = *opts;
+    if (o.precision != 0 && o.precision != 1) throw Error{-1, "precision must be 0 or 1"};
+    if (o.check_every < 0 || o.inner_sweeps < 0 || o.max_outer < 0 || o.timeout_spins < 0)
+        throw Error{-1, "negative option"};
+    if (o.rows_per_warp != 0 && o.rows_per_warp != 1 && o.rows_per_warp != 2 && o.rows_per_warp != 4 &&
+        o.rows_per_warp != 8)
+        throw Error{-1, "rows_per_warp must be 0, 1, 2, 4 or 8"};
+    OBK_CUDA(cudaSetDevice(h->device));
+    cudaStream_t st = h->st;
+    int64_t m = h->m, n = h->n, N = h->N;
+    Timer tm(st);
+    bool fdev = is_device_ptr(f), xdev = x0 && is_device_ptr(x0), odev = is_device_ptr(x_out);
+    DBuf<double> fd(m, st), x0d, xt(N, st), fgm(std::max<int64_t>(h->L.Ngm, 1), st);
+    to_device(fd.p, f, m, fdev, st);
+    DBuf<int> bad(1, st);
+    OBK_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+    check_finite<<<grid_for(m), kBlock, 0, st>>>(fd.p, m, bad.p);
+    OBK_CHECK_LAUNCH();
+    if (x0) {
+        x0d.alloc(n, st);
+        to_device(x0d.p, x0, n, xdev, st);
+        check_finite<<<grid_for(n), kBlock, 0, st>>>(x0d.p, n, bad.p);
+        OBK_CHECK_LAUNCH();
+    }
+    if (read_scalar(bad.p, st)) throw Error{-1, "f or x0 holds NaN or Inf"};
+    // x~0 = P x^0, f in group-major order, ||f||^2 and the all-zero rows' share
+    permute_x0<<<grid_for(N), kBlock, 0, st>>>(N, h->perm.p, x0 ? x0d.p : nullptr, n, xt.p);
+    OBK_CHECK_LAUNCH();
+    if (h->L.Ngm) {
+        gather_gm<<<grid_for(h->L.Ngm), kBlock, 0, st>>>(h->L.Ngm, h->src_gm.p, fd.p, m, fgm.p);
+        OBK_CHECK_LAUNCH();
+    }
+    double fnorm2 = sum_squares(fd.p, nullptr, m, m, st);
+    double zero_f2 = sum_squares(fd.p, h->zero_src.p, h->n_zero, m, st);
+    SolveArgs a;
+    a.precision = o.precision;
+    a.check_every = o.check_every > 0 ? o.check_every : 1;
+    a.inner_sweeps = o.inner_sweeps;
+    a.max_outer = o.max_outer > 0 ? o.max_outer : 100;
+    a.stagnation = o.stagnation;
+    a.tol = tol;
+    a.maxit = maxit;
+    a.spin_limit = o.timeout_spins > 0 ? o.timeout_spins : kDefaultSpins;
+    a.sub = o.rows_per_warp > 0 ? 32 / o.rows_per_warp : 0;
+    SolveResult r = run_solve(h->L, fgm.p, fnorm2, zero_f2, xt.p, a, h->err.p, st);
+    // x = P^T x~, then x^(1:n)
+    double* xo = x_out;
+    DBuf<double> xtmp;
+    if (!odev) {
+        xtmp.alloc(n, st);
+        xo = xtmp.p;
+    }
+    unpermute_x<<<grid_for(N), kBlock, 0, st>>>(N, h->perm.p, xt.p, n, xo);
+    OBK_CHECK_LAUNCH();
+    if (!odev) OBK_CUDA(cudaMemcpyAsync(x_out, xo, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    double ms = tm.stop_ms();
+    OBK_CUDA(cudaStreamSynchronize(st));
+    h->info.sweeps = r.sweeps;
+    h->info.rel_res = r.rel_res;
+    h->info.solve_ms = ms;
+    h->info.outer_iters = r.outer;
+    h->info.sweep_ms = r.sweep_ms;
+    h->info.status = r.status;
+    if (info) *info = h->info;
+    return r.status == 0 ? OBK_OK : OBK_NOT_CONVERGED;
+    OBK_API_END
+}
+
+obk_status obk_solve(obk_handle* h, const double* f, const double* x0, double tol, int64_t maxit, double* x_out,
+                     obk_info* info)
+{
+    return obk_solve_ex(h, nullptr, f, x0, tol, maxit, x_out, info);
+}
+
+obk_status obk_get_dims(const obk_handle* h, int64_t* N, int64_t* nnz, int64_t* G)
+{
+    if (!h) { set_last_error("handle is NULL"); return OBK_ERR_INVALID; }
+    if (N) *N = h->N;
+    if (nnz) *nnz = h->nnz;
+    if (G) *G = h->L.G;
+    return OBK_OK;
+}
+
+static obk_status copy_out(const obk_handle* h, void* dst, const void* src, size_t bytes)
+{
+    OBK_API_BEGIN
+    if (!h || !dst) throw Error{-1, "NULL argument"};
+    OBK_CUDA(cudaSetDevice(h->device));
+    bool ddev = is_device_ptr(dst);
+    OBK_CUDA(cudaMemcpyAsync(dst, src, bytes, ddev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+    OBK_CUDA(cudaStreamSynchronize(h->st));
+    return OBK_OK;
+    OBK_API_END
+}
+
+obk_status obk_get_perm(const obk_handle* h, int32_t* perm)
+{
+    if (!h) { set_last_error("handle is NULL"); return OBK_ERR_INVALID; }
+    return copy_out(h, perm, h->perm.p, h->N * sizeof(int32_t));
+}
+
+obk_status obk_get_groups(const obk_handle* h, int32_t* group_of)
+{
+    if (!h) { set_last_error("handle is NULL"); return OBK_ERR_INVALID; }
+    return copy_out(h, group_of, h->L.group_of.p, h->N * sizeof(int32_t));
+}
+
+obk_status obk_get_row_norms(const obk_handle* h, double* nsq)
+{
+    if (!h) { set_last_error("handle is NULL"); return OBK_ERR_INVALID; }
+    return copy_out(h, nsq, h->L.nsq.p, h->N * sizeof(double));
+}
+
+obk_status obk_get_info(const obk_handle* h, obk_info* info)
+{
+    if (!h || !info) { set_last_error("NULL argument"); return OBK_ERR_INVALID; }
+    *info = h->info;
+    return OBK_OK;
+}
+
+obk_status obk_residual(const obk_csr* A, int64_t m, int64_t n, const double* f, const double* x, double* rel_res)
+{
+    OBK_API_BEGIN
+    set_last_error("");
+    if (!A || !f || !x || !rel_res || !A->row_ptr || m <= 0 || n <= 0 || A->nnz < 0 ||
+        (A->nnz > 0 && (!A->col_idx || !A->val)))
+        throw Error{-1, "NULL pointer or non-positive size"};
+    cudaStream_t st;
+    OBK_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    try {
+        bool adev = A->device_ptrs != 0, fdev = is_device_ptr(f), xdev = is_device_ptr(x);
+        int64_t nnz = A->nnz, ntiles = ceil_div(m, kResTile);
+        DBuf<int64_t> rp;
+        DBuf<int32_t> ci;
+        DBuf<double> v, fd, xd, part(2 * ntiles + 1, st);
+        const int64_t* prp = A->row_ptr;
+        const int32_t* pci = A->col_idx;
+        const double* pv = A->val;
+        if (!adev) {
+            rp.alloc(m + 1, st);
+            ci.alloc(std::max<int64_t>(nnz, 1), st);
+            v.alloc(std::max<int64_t>(nnz, 1), st);
+            to_device(rp.p, A->row_ptr, m + 1, false, st);
+            to_device(ci.p, A->col_idx, nnz, false, st);
+            to_device(v.p, A->val, nnz, false, st);
+            prp = rp.p;
+            pci = ci.p;
+            pv = v.p;
+        }
+        const double* pf = f;
+        const double* px = x;
+        if (!fdev) { fd.alloc(m, st); to_device(fd.p, f, m, false, st); pf = fd.p; }
+        if (!xdev) { xd.alloc(n, st); to_device(xd.p, x, n, false, st); px = xd.p; }
+        residual_tiles<<<(unsigned)ntiles, kBlock, 0, st>>>(m, prp, pci, pv, pf, px, part.p);
+        OBK_CHECK_LAUNCH();
+        residual_final<<<1, 32, 0, st>>>(part.p, ntiles, part.p + 2 * ntiles);
+        OBK_CHECK_LAUNCH();
+        *rel_res = read_scalar(part.p + 2 * ntiles, st);
+    } catch (...) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+        throw;
+    }
+    OBK_CUDA(cudaStreamSynchronize(st));
+    OBK_CUDA(cudaStreamDestroy(st));
+    return OBK_OK;
+    OBK_API_END
+}
+
+void obk_destroy(obk_handle* h)
+{
+    if (!h) return;
+    cudaSetDevice(h->device);
+    cudaStream_t st = h->st;
+    if (st) cudaStreamSynchronize(st);
+    bool own = h->own_stream;
+    delete h;  // buffers are freed on st
+    if (st) {
+        cudaStreamSynchronize(st);
+        if (own) cudaStreamDestroy(st);
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,196 @@
+// common.cuh -- shared device/host helpers of the OBK-RCM CUDA library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+namespace obk {
+
+// ---- error plumbing ----------------------------------------------------
+
+// Thrown inside the library, converted to an obk_status at the C boundary.
+struct Error {
+    int status;
+    std::string msg;
+};
+
+void set_last_error(const std::string& msg);
+
+#define OBK_CUDA(call)                                                                 \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            throw ::obk::Error{-5, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+
+// Every kernel launch of the library is followed by OBK_CHECK_LAUNCH (or goes
+// through OBK_COOP_LAUNCH), which also counts it for obk_kernel_launches().
+void count_launch();
+#define OBK_CHECK_LAUNCH()              \
+    do {                                \
+        ::obk::count_launch();          \
+        OBK_CUDA(cudaGetLastError());   \
+    } while (0)
+#define OBK_COOP_LAUNCH(k, g, b, a, s)                                        \
+    do {                                                                      \
+        ::obk::count_launch();                                                \
+        OBK_CUDA(cudaLaunchCooperativeKernel((const void*)(k), g, b, a, 0, s)); \
+    } while (0)
+
+constexpr int kWarp = 32;
+
+// Error word written by device code (0 = fine).
+enum DevErr : int { kDevOk = 0, kDevTimeout = 1, kDevOverflow = 2 };
+
+// Default bound on device-side spin waits (iterations of a poll loop, each at
+// least one L2 round trip): a few seconds at most.
+constexpr long long kDefaultSpins = 1LL << 23;
+
+// ---- bounded grid barrier ------------------------------------------------
+//
+// Sense-counting barrier for kernels launched cooperatively (all blocks
+// co-resident).  Every wait is bounded: after `limit` polls the block records
+// kDevTimeout in *err and returns false; callers must then leave the kernel.
+// bar[0] = arrival counter, bar[1] = generation.
+struct GridBarrier {
+    unsigned int* bar;
+    int* err;
+    long long limit;
+};
+
+__device__ __forceinline__ unsigned ld_volatile_u32(const unsigned* p)
+{
+    return *reinterpret_cast<const volatile unsigned*>(p);
+}
+__device__ __forceinline__ int ld_volatile_i32(const int* p)
+{
+    return *reinterpret_cast<const volatile int*>(p);
+}
+
+__device__ __forceinline__ bool grid_sync(const GridBarrier& gb)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+        unsigned gen = ld_volatile_u32(gb.bar + 1);
+        __threadfence();
+        unsigned arrived = atomicAdd(gb.bar, 1u);
+        if (arrived == nb - 1) {
+            atomicExch(gb.bar, 0u);
+            __threadfence();
+            atomicAdd(gb.bar + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (ld_volatile_u32(gb.bar + 1) == gen) {
+                if (++spins > gb.limit || ld_volatile_i32(gb.err) != 0) {
+                    atomicCAS(gb.err, 0, (int)kDevTimeout);
+                    ok = 0;
+                    break;
+                }
+                if (spins > 64) __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (ld_volatile_i32(gb.err) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---- small helpers -----------------------------------------------------
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+inline int bits_for(uint64_t maxval)
+{
+    int b = 0;
+    while (b < 64 && (maxval >> b) != 0) ++b;
+    return b == 0 ? 1 : b;
+}
+
+// Device properties of the current device (cached per device).
+struct DevInfo {
+    int device;
+    int sms;
+    size_t l2_bytes;
+    size_t smem_optin;
+};
+DevInfo dev_info();
+
+// Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync).
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    cudaStream_t s = nullptr;
+    DBuf() = default;
+    DBuf(size_t count, cudaStream_t st) { alloc(count, st); }
+    void alloc(size_t count, cudaStream_t st)
+    {
+        release();
+        s = st;
+        n = count;
+        if (count) {
+            cudaError_t e = cudaMallocAsync((void**)&p, count * sizeof(T), st);
+            if (e != cudaSuccess) {
+                p = nullptr;
+                (void)cudaGetLastError();
+                throw Error{-2, "device allocation of " + std::to_string(count * sizeof(T)) +
+                                    " bytes failed: " + cudaGetErrorString(e)};
+            }
+        }
+    }
+    void release()
+    {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        n = 0;
+    }
+    ~DBuf() { release(); }
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; o.n = 0; }
+    DBuf& operator=(DBuf&& o) noexcept
+    {
+        if (this != &o) { release(); p = o.p; n = o.n; s = o.s; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+// ---- primitives (primitives.cu) -----------------------------------------
+
+// out[i] = sum_{k<i} in[k] for i in [0, n]; out has n+1 entries (out[n] = total).
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);
+void exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t st);
+
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the
+// key.  keys/vals are sorted in place (scratch allocated internally).
+void radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaStream_t st);
+
+// Read one value back (synchronises the stream).
+template <class T>
+T read_scalar(const T* dptr, cudaStream_t st)
+{
+    T v;
+    OBK_CUDA(cudaMemcpyAsync(&v, dptr, sizeof(T), cudaMemcpyDeviceToHost, st));
+    OBK_CUDA(cudaStreamSynchronize(st));
+    return v;
+}
+
+// Cooperative launch helper: grid = min(want, co-resident capacity).
+int coop_grid(const void* kernel, int block, size_t smem, int64_t want_blocks);
+
+}  // namespace obk
+
+namespace obk {
+// Sort (key, value) pairs by key inside each segment [ptr[s], ptr[s+1]).
+// Keys within a segment should be distinct for a deterministic result.
+void segmented_sort_u32(const int64_t* ptr, int64_t nseg, uint32_t* keys, uint32_t* vals,
+                        cudaStream_t st);
+}  // namespace obk

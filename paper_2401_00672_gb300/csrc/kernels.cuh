@@ -1,0 +1,102 @@
+// kernels.cuh -- internal interfaces between the library's translation units.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace obk {
+
+struct RcmStats {
+    int64_t components = 0;
+    int64_t levels = 0;
+    int64_t gl_rounds = 0;
+    int64_t graph_edges = 0;
+};
+
+// perm[k] = vertex placed at position k by Reverse Cuthill-McKee (rcm.cu).
+void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, int32_t* perm,
+                 long long spin_limit, int* d_err, RcmStats* stats, cudaStream_t st);
+
+// Sorted neighbour lists of pattern(A + A^T) without self loops (rcm.cu).
+void build_sym_graph(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, DBuf<int64_t>& gp,
+                     DBuf<int32_t>& adj, cudaStream_t st);
+
+// ---- setup.cu ---------------------------------------------------------------
+
+// Returns nonzero flags in *d_bad if the CSR is malformed (see obk.h).
+void validate_csr(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                  int64_t nnz, int* d_bad, cudaStream_t st);
+
+int64_t half_bandwidth(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, cudaStream_t st);
+
+// A~ = P A P^T with sorted columns.
+void permute_csr(int64_t N, const int64_t* rp, const int32_t* ci, const double* v, int64_t nnz,
+                 const int32_t* perm, int32_t* iperm, int64_t* rp_t, int32_t* ci_t, double* v_t,
+                 cudaStream_t st);
+
+// Everything the sweep needs, in device memory.
+struct SweepLayout {
+    int64_t N = 0, nnz = 0;
+    int64_t G = 0;          // groups
+    int64_t Ngm = 0;        // rows that belong to a group (nonzero rows)
+    int64_t nseg = 0;       // (group, column) segments of the column mirror
+    int64_t nnz_gm = 0;     // entries of grouped rows
+    int64_t n_conflicts = 0;
+    // group-major CSR: rows of group 0, then group 1, ...
+    DBuf<int64_t> grp_rp;   // Ngm+1
+    DBuf<int32_t> grp_ci;   // nnz_gm (columns in permuted numbering)
+    DBuf<double> grp_v;     // nnz_gm
+    DBuf<float> grp_v32;    // nnz_gm (precision form)
+    DBuf<double> grp_inv;   // Ngm, 1 / ||A_i||^2
+    DBuf<float> grp_inv32;  // Ngm
+    DBuf<int32_t> grp_row;  // Ngm, permuted row index of each group-major row
+    DBuf<int64_t> gptr;     // G+1 (device)
+    std::vector<int64_t> h_gptr;
+    // column mirror for the x update: entries ordered by (group, column, row)
+    DBuf<int64_t> gseg_ptr; // G+1, first segment of each group
+    std::vector<int64_t> h_gseg_ptr;
+    DBuf<int64_t> seg_ptr;  // nseg+1, first mirror entry of each segment
+    DBuf<int32_t> seg_col;  // nseg
+    DBuf<int32_t> mir_row;  // nnz_gm, group-major row index
+    DBuf<double> mir_val;   // nnz_gm
+    DBuf<float> mir_val32;  // nnz_gm
+    // permuted-order results kept for inspection
+    DBuf<double> nsq;       // N
+    DBuf<int32_t> group_of; // N
+};
+
+// Row norms, pair cosines, greedy first-fit groups and the sweep layout
+// (paper Section 3.3 at one row per block).
+void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* v, int64_t nnz,
+                 double thr, long long spin_limit, int* d_err, SweepLayout& L, bool want_fp32,
+                 cudaStream_t st);
+
+// ---- sweep.cu -----------------------------------------------------------------
+
+struct SolveArgs {
+    int precision = 0;
+    int check_every = 1;
+    int inner_sweeps = 0;
+    int max_outer = 100;
+    double stagnation = 0.0;
+    double tol = 1e-8;
+    int64_t maxit = 1000;
+    long long spin_limit = kDefaultSpins;
+    int sub = 0;  // lanes per row (0 = choose)
+};
+
+struct SolveResult {
+    int status = 0;
+    int64_t sweeps = 0;
+    int64_t outer = 0;
+    double rel_res = 0.0;
+    double sweep_ms = 0.0;
+};
+
+// x (N, permuted order) is updated in place; f_gm (Ngm) is f in group-major
+// order; fnorm2 = ||f~||^2 and zero_f2 = sum of f_i^2 over all-zero rows.
+SolveResult run_solve(const SweepLayout& L, const double* f_gm, double fnorm2, double zero_f2,
+                      double* x, const SolveArgs& a, int* d_err, cudaStream_t st);
+
+}  // namespace obk

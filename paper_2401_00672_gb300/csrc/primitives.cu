@@ -1,0 +1,371 @@
+// primitives.cu -- scan and stable radix sort used by the setup kernels.
+#include "common.cuh"
+
+namespace obk {
+
+namespace {
+
+constexpr int kScanBlock = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+// Block-wide exclusive scan of one value per thread (int64).
+__device__ int64_t block_exclusive_scan(int64_t v, int64_t* total)
+{
+    __shared__ int64_t warp_sums[kScanBlock / kWarp];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_sums[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t w = lane < kScanBlock / kWarp ? warp_sums[lane] : 0;
+        int64_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < kScanBlock / kWarp) warp_sums[lane] = wi - w;
+        if (lane == kScanBlock / kWarp - 1) *total = wi;
+    }
+    __syncthreads();
+    int64_t r = inc - v + warp_sums[wid];
+    __syncthreads();
+    return r;
+}
+
+template <class Tin>
+__global__ void scan_tile_sums(const Tin* in, int64_t n, int64_t* tile_sums)
+{
+    int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int64_t s = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + (int64_t)k * kScanBlock + threadIdx.x;
+        if (i < n) s += (int64_t)in[i];
+    }
+    __shared__ int64_t tot;
+    block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+// Single-block exclusive scan of the tile sums (any length, sequential tiles).
+__global__ void scan_tile_offsets(int64_t* sums, int64_t ntiles)
+{
+    __shared__ int64_t tot;
+    int64_t carry = 0;
+    for (int64_t base = 0; base < ntiles; base += kScanBlock) {
+        int64_t i = base + threadIdx.x;
+        int64_t v = i < ntiles ? sums[i] : 0;
+        int64_t ex = block_exclusive_scan(v, &tot);
+        if (i < ntiles) sums[i] = ex + carry;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[ntiles] = carry;
+}
+
+template <class Tin>
+__global__ void scan_tile_apply(const Tin* in, int64_t* out, int64_t n, const int64_t* offs,
+                                int64_t ntiles)
+{
+    // each thread owns kScanItems consecutive elements of the tile
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t loc[kScanItems];
+    int64_t s = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + k;
+        loc[k] = i < n ? (int64_t)in[i] : 0;
+        s += loc[k];
+    }
+    __shared__ int64_t tot;
+    int64_t ex = block_exclusive_scan(s, &tot) + offs[blockIdx.x];
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + k;
+        if (i < n) out[i] = ex;
+        ex += loc[k];
+    }
+    if (blockIdx.x == ntiles - 1 && threadIdx.x == 0) out[n] = offs[ntiles];
+}
+
+template <class Tin>
+void exclusive_scan_impl(const Tin* in, int64_t* out, int64_t n, cudaStream_t st)
+{
+    if (n == 0) {
+        OBK_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), st));
+        return;
+    }
+    int64_t ntiles = ceil_div(n, kScanTile);
+    DBuf<int64_t> sums(ntiles + 1, st);
+    scan_tile_sums<Tin><<<(unsigned)ntiles, kScanBlock, 0, st>>>(in, n, sums.p);
+    OBK_CHECK_LAUNCH();
+    scan_tile_offsets<<<1, kScanBlock, 0, st>>>(sums.p, ntiles);
+    OBK_CHECK_LAUNCH();
+    scan_tile_apply<Tin><<<(unsigned)ntiles, kScanBlock, 0, st>>>(in, out, n, sums.p, ntiles);
+    OBK_CHECK_LAUNCH();
+}
+
+// ---- stable LSD radix sort, 8-bit digits ---------------------------------
+
+constexpr int kSortBlock = 256;
+constexpr int kSortItems = 16;  // keys per thread per tile (processed in rounds)
+constexpr int kSortTile = kSortBlock * kSortItems;
+constexpr int kRadix = 256;
+
+__global__ void radix_hist(const uint64_t* keys, int64_t n, int shift, int64_t* hist, int64_t ntiles)
+{
+    __shared__ unsigned cnt[kRadix];
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) cnt[d] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int k = 0; k < kSortItems; ++k) {
+        int64_t i = base + (int64_t)k * kSortBlock + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 0xff], 1u);
+    }
+    __syncthreads();
+    // digit-major layout: hist[d * ntiles + tile]
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[(int64_t)d * ntiles + blockIdx.x] = cnt[d];
+}
+
+// Stable scatter: keys of a tile are ranked in input order.  The tile is
+// processed in rounds of kSortBlock consecutive keys; within a round a key's
+// rank is (keys of the same digit in earlier rounds of this tile) + (same digit
+// in earlier warps of this round) + (same digit in earlier lanes of its warp).
+__global__ void radix_scatter(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                              uint32_t* vals_out, int64_t n, int shift, const int64_t* offs,
+                              int64_t ntiles)
+{
+    constexpr int kWarps = kSortBlock / kWarp;
+    __shared__ int64_t base_off[kRadix];
+    __shared__ unsigned warp_cnt[kWarps][kRadix];
+    __shared__ unsigned round_tot[kRadix];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
+        base_off[d] = offs[(int64_t)d * ntiles + blockIdx.x];
+    int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+    unsigned lt_mask = (1u << lane) - 1u;
+    for (int r = 0; r < kSortItems; ++r) {
+        int64_t round0 = tile0 + (int64_t)r * kSortBlock;
+        if (round0 >= n) break;  // uniform across the block
+        for (int t = threadIdx.x; t < kWarps * kRadix; t += blockDim.x) (&warp_cnt[0][0])[t] = 0;
+        __syncthreads();
+        int64_t i = round0 + threadIdx.x;
+        bool valid = i < n;
+        uint64_t key = valid ? keys_in[i] : 0;
+        uint32_t val = valid ? vals_in[i] : 0;
+        unsigned d = valid ? (unsigned)((key >> shift) & 0xff) : (unsigned)kRadix;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned rank_in_warp = __popc(peers & lt_mask);
+        if (valid && rank_in_warp == 0) warp_cnt[wid][d] = __popc(peers);
+        __syncthreads();
+        for (int dd = threadIdx.x; dd < kRadix; dd += blockDim.x) {
+            unsigned run = 0;
+            for (int w = 0; w < kWarps; ++w) {
+                unsigned c = warp_cnt[w][dd];
+                warp_cnt[w][dd] = run;
+                run += c;
+            }
+            round_tot[dd] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            int64_t pos = base_off[d] + warp_cnt[wid][d] + rank_in_warp;
+            keys_out[pos] = key;
+            vals_out[pos] = val;
+        }
+        __syncthreads();
+        for (int dd = threadIdx.x; dd < kRadix; dd += blockDim.x) base_off[dd] += round_tot[dd];
+        __syncthreads();
+    }
+}
+
+
+// ---- segmented sort of (u32 key, u32 value) by key inside each segment ------
+//
+// Segments [ptr[s], ptr[s+1]).  Short segments are insertion-sorted by one
+// thread, medium ones by one block with a bitonic network in shared memory,
+// and the rare long ones by the global radix sort on (segment, key).
+
+constexpr int kSegShort = 32;
+constexpr int kSegMedium = 2048;
+
+__global__ void segsort_short(const int64_t* ptr, int64_t nseg, uint32_t* keys, uint32_t* vals,
+                              int32_t* longs, int32_t* nlong, int32_t* huge, int32_t* nhuge)
+{
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    int64_t b = ptr[s], e = ptr[s + 1], len = e - b;
+    if (len <= 1) return;
+    if (len > kSegMedium) { huge[atomicAdd(nhuge, 1)] = (int32_t)s; return; }
+    if (len > kSegShort) { longs[atomicAdd(nlong, 1)] = (int32_t)s; return; }
+    uint32_t k[kSegShort], v[kSegShort];
+    for (int t = 0; t < len; ++t) { k[t] = keys[b + t]; v[t] = vals[b + t]; }
+    for (int t = 1; t < len; ++t) {
+        uint32_t kk = k[t], vv = v[t];
+        int u = t - 1;
+        while (u >= 0 && k[u] > kk) { k[u + 1] = k[u]; v[u + 1] = v[u]; --u; }
+        k[u + 1] = kk;
+        v[u + 1] = vv;
+    }
+    for (int t = 0; t < len; ++t) { keys[b + t] = k[t]; vals[b + t] = v[t]; }
+}
+
+__global__ void segsort_medium(const int64_t* ptr, const int32_t* longs, uint32_t* keys, uint32_t* vals)
+{
+    __shared__ unsigned long long buf[kSegMedium];
+    int64_t s = longs[blockIdx.x];
+    int64_t b = ptr[s], len = ptr[s + 1] - b;
+    int P = 1;
+    while (P < len) P <<= 1;
+    for (int t = threadIdx.x; t < P; t += blockDim.x)
+        buf[t] = t < len ? (((unsigned long long)keys[b + t]) << 32) | vals[b + t] : ~0ull;
+    __syncthreads();
+    for (int kk = 2; kk <= P; kk <<= 1)
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < P; t += blockDim.x) {
+                int o = t ^ j;
+                if (o > t) {
+                    bool up = (t & kk) == 0;
+                    unsigned long long a = buf[t], c = buf[o];
+                    if ((a > c) == up) { buf[t] = c; buf[o] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    for (int t = threadIdx.x; t < len; t += blockDim.x) {
+        keys[b + t] = (uint32_t)(buf[t] >> 32);
+        vals[b + t] = (uint32_t)buf[t];
+    }
+}
+
+__global__ void segsort_huge_gather(const int64_t* ptr, const int32_t* huge, const int64_t* hoff,
+                                    int32_t nh, const uint32_t* keys, uint64_t* k64, uint32_t* pos)
+{
+    for (int h = blockIdx.x; h < nh; h += gridDim.x) {
+        int64_t b = ptr[huge[h]], len = ptr[huge[h] + 1] - b, o = hoff[h];
+        for (int64_t t = threadIdx.x; t < len; t += blockDim.x) {
+            k64[o + t] = ((uint64_t)h << 32) | keys[b + t];
+            pos[o + t] = (uint32_t)(b + t);
+        }
+    }
+}
+
+__global__ void segsort_huge_scatter(const int64_t* ptr, const int32_t* huge, const int64_t* hoff,
+                                     int32_t nh, const uint64_t* k64, const uint32_t* pos,
+                                     const uint32_t* vals_src, uint32_t* keys, uint32_t* vals)
+{
+    for (int h = blockIdx.x; h < nh; h += gridDim.x) {
+        int64_t b = ptr[huge[h]], len = ptr[huge[h] + 1] - b, o = hoff[h];
+        for (int64_t t = threadIdx.x; t < len; t += blockDim.x) {
+            keys[b + t] = (uint32_t)k64[o + t];
+            vals[b + t] = vals_src[pos[o + t]];
+        }
+    }
+}
+
+__global__ void segsort_huge_sizes(const int64_t* ptr, const int32_t* huge, int32_t nh, int64_t* sz)
+{
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h < nh) sz[h] = ptr[huge[h] + 1] - ptr[huge[h]];
+}
+
+}  // namespace
+
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st)
+{
+    exclusive_scan_impl<int64_t>(in, out, n, st);
+}
+
+void exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t st)
+{
+    exclusive_scan_impl<int32_t>(in, out, n, st);
+}
+
+void radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaStream_t st)
+{
+    if (n <= 1) return;
+    int64_t ntiles = ceil_div(n, kSortTile);
+    DBuf<uint64_t> k2(n, st);
+    DBuf<uint32_t> v2(n, st);
+    DBuf<int64_t> hist(kRadix * ntiles + 1, st);
+    DBuf<int64_t> offs(kRadix * ntiles + 1, st);
+    uint64_t* kin = keys;
+    uint32_t* vin = vals;
+    uint64_t* kout = k2.p;
+    uint32_t* vout = v2.p;
+    int passes = (bits + 7) / 8;
+    for (int p = 0; p < passes; ++p) {
+        int shift = 8 * p;
+        radix_hist<<<(unsigned)ntiles, kSortBlock, 0, st>>>(kin, n, shift, hist.p, ntiles);
+        OBK_CHECK_LAUNCH();
+        exclusive_scan_i64(hist.p, offs.p, kRadix * ntiles, st);
+        radix_scatter<<<(unsigned)ntiles, kSortBlock, 0, st>>>(kin, vin, kout, vout, n, shift, offs.p,
+                                                              ntiles);
+        OBK_CHECK_LAUNCH();
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    if (kin != keys) {
+        OBK_CUDA(cudaMemcpyAsync(keys, kin, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+        OBK_CUDA(cudaMemcpyAsync(vals, vin, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+    }
+}
+
+int coop_grid(const void* kernel, int block, size_t smem, int64_t want_blocks)
+{
+    DevInfo di = dev_info();
+    int per_sm = 0;
+    OBK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem));
+    if (per_sm < 1) throw Error{-5, "kernel cannot be made resident (occupancy 0)"};
+    int64_t cap = (int64_t)per_sm * di.sms;
+    int64_t g = want_blocks < cap ? want_blocks : cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace obk
+
+namespace obk {
+
+void segmented_sort_u32(const int64_t* ptr, int64_t nseg, uint32_t* keys, uint32_t* vals,
+                        cudaStream_t st)
+{
+    if (nseg <= 0) return;
+    DBuf<int32_t> longs(nseg, st), huge(nseg, st), cnt(2, st);
+    OBK_CUDA(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(int32_t), st));
+    segsort_short<<<(unsigned)ceil_div(nseg, 256), 256, 0, st>>>(ptr, nseg, keys, vals, longs.p, cnt.p,
+                                                                 huge.p, cnt.p + 1);
+    OBK_CHECK_LAUNCH();
+    int32_t h_cnt[2];
+    OBK_CUDA(cudaMemcpyAsync(h_cnt, cnt.p, sizeof(h_cnt), cudaMemcpyDeviceToHost, st));
+    OBK_CUDA(cudaStreamSynchronize(st));
+    if (h_cnt[0] > 0) {
+        segsort_medium<<<(unsigned)h_cnt[0], 512, 0, st>>>(ptr, longs.p, keys, vals);
+        OBK_CHECK_LAUNCH();
+    }
+    int32_t nh = h_cnt[1];
+    if (nh > 0) {
+        DBuf<int64_t> sz(nh, st), hoff(nh + 1, st);
+        segsort_huge_sizes<<<(unsigned)ceil_div(nh, 256), 256, 0, st>>>(ptr, huge.p, nh, sz.p);
+        OBK_CHECK_LAUNCH();
+        exclusive_scan_i64(sz.p, hoff.p, nh, st);
+        int64_t tot = read_scalar(hoff.p + nh, st);
+        DBuf<uint64_t> k64(tot, st);
+        DBuf<uint32_t> pos(tot, st);
+        segsort_huge_gather<<<256, 256, 0, st>>>(ptr, huge.p, hoff.p, nh, keys, k64.p, pos.p);
+        OBK_CHECK_LAUNCH();
+        radix_sort_pairs(k64.p, pos.p, tot, 32 + bits_for((uint64_t)nh), st);
+        // the scatter reads values through their source positions: keep a copy
+        int64_t nvals = read_scalar(ptr + nseg, st);
+        DBuf<uint32_t> vsrc(nvals, st);
+        OBK_CUDA(cudaMemcpyAsync(vsrc.p, vals, nvals * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+        segsort_huge_scatter<<<256, 256, 0, st>>>(ptr, huge.p, hoff.p, nh, k64.p, pos.p, vsrc.p, keys,
+                                                  vals);
+        OBK_CHECK_LAUNCH();
+    }
+}
+
+}  // namespace obk

@@ -1,0 +1,646 @@
+// rcm.cu -- Reverse Cuthill-McKee reordering on the GPU (paper Section 3.2,
+// Eq. 3.1-3.2; the paper names RCM without its steps).
+//
+// Reading implemented (and matched bit for bit by the tests):
+//   graph      pattern(A + A^T) without self loops; deg(v) = distinct neighbours
+//   start      per connected component, George-Liu pseudo-peripheral search grown
+//              from the component's minimum-(deg, index) vertex: root v, last BFS
+//              level's minimum-(deg, index) vertex u; move to u while its
+//              eccentricity is larger
+//   order      Cuthill-McKee from the root, children appended in (deg, index)
+//              order; components in order of their minimum-(deg, index) vertex;
+//              the whole list is reversed once.
+//
+// GPU formulation:
+//   * every vertex gets its rank r(v) in (deg, index) order, and every
+//     adjacency list is sorted by r, so "children in (deg, index) order" is a
+//     linear scan;
+//   * components are labelled by min-hooking (label = smallest vertex index);
+//   * all components run their breadth-first searches at the same time
+//     (level-synchronous, cooperative kernels with bounded grid barriers);
+//   * Cuthill-McKee levels: the frontier F_L is kept sorted by (component,
+//     CM position).  A newly reached vertex w takes as parent the frontier
+//     vertex of smallest frontier index (atomicMin), which is the earliest
+//     placed neighbour of sequential Cuthill-McKee; children are then written
+//     contiguously after an exclusive scan of per-parent child counts, in the
+//     r order of the parent's adjacency list.  This reproduces the sequential
+//     queue order exactly.
+#include <cooperative_groups.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace obk {
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int32_t kUnvisited = -1;
+
+// ---- symmetric graph: pattern(A + A^T) minus self loops -----------------------
+
+__global__ void expand_rows(const int64_t* rp, int64_t N, int32_t* row_of)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) row_of[e] = (int32_t)i;
+}
+
+__global__ void col_keys(const int32_t* ci, int64_t nnz, uint64_t* keys, uint32_t* vals,
+                         const int32_t* row_of)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        keys[e] = (uint64_t)(uint32_t)ci[e];
+        vals[e] = (uint32_t)row_of[e];
+    }
+}
+
+__global__ void count_cols(const int32_t* ci, int64_t nnz, int64_t* cnt)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+         e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd((unsigned long long*)&cnt[ci[e]], 1ull);
+}
+
+// Merge row i of A (sorted columns) with row i of A^T (sorted rows of column i):
+// the union without i.  Pass 0 counts, pass 1 writes.
+template <bool kWrite>
+__global__ void merge_sym(int64_t N, const int64_t* rp, const int32_t* ci, const int64_t* tp,
+                          const uint32_t* tr, const int64_t* gp, int64_t* deg, int32_t* adj)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a = rp[i], ae = rp[i + 1], b = tp[i], be = tp[i + 1];
+        int64_t out = kWrite ? gp[i] : 0, cnt = 0;
+        int64_t last = -1;
+        while (a < ae || b < be) {
+            int64_t va = a < ae ? (int64_t)ci[a] : INT64_MAX;
+            int64_t vb = b < be ? (int64_t)tr[b] : INT64_MAX;
+            int64_t v;
+            if (va <= vb) { v = va; ++a; if (va == vb) ++b; }
+            else { v = vb; ++b; }
+            if (v == i || v == last) continue;
+            last = v;
+            if (kWrite) adj[out + cnt] = (int32_t)v;
+            ++cnt;
+        }
+        if (!kWrite) deg[i] = cnt;
+    }
+}
+
+// ---- ranks in (deg, index) order ---------------------------------------------
+
+__global__ void deg_keys(int64_t N, const int64_t* gp, int bN, uint64_t* keys, uint32_t* vals)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        keys[v] = ((uint64_t)(gp[v + 1] - gp[v]) << bN) | (uint64_t)v;
+        vals[v] = (uint32_t)v;
+    }
+}
+
+__global__ void rank_of(int64_t N, const uint32_t* by_rank, int32_t* r)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x)
+        r[by_rank[k]] = (int32_t)k;
+}
+
+__global__ void adj_rank_keys(int64_t M, const int32_t* adj, const int32_t* r, uint32_t* keys,
+                              uint32_t* vals)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < M;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        keys[e] = (uint32_t)r[adj[e]];
+        vals[e] = (uint32_t)adj[e];
+    }
+}
+
+// ---- connected components by min-hooking ---------------------------------------
+
+__device__ __forceinline__ int32_t find_root(const int32_t* parent, int32_t v)
+{
+    int32_t p = ld_volatile_i32(parent + v);
+    while (p != v) {
+        v = p;
+        p = ld_volatile_i32(parent + v);
+    }
+    return v;
+}
+
+__global__ void cc_init(int64_t N, int32_t* parent)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+         v += (int64_t)gridDim.x * blockDim.x)
+        parent[v] = (int32_t)v;
+}
+
+__global__ void cc_hook(int64_t N, const int64_t* gp, const int32_t* adj, int32_t* parent, int* changed)
+{
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < N;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        for (int64_t e = gp[u]; e < gp[u + 1]; ++e) {
+            int32_t w = adj[e];
+            if (w <= u) continue;
+            int32_t ru = find_root(parent, (int32_t)u), rw = find_root(parent, w);
+            if (ru != rw) {
+                int32_t hi = ru > rw ? ru : rw, lo = ru > rw ? rw : ru;
+                atomicMin(parent + hi, lo);
+                *changed = 1;
+            }
+        }
+    }
+}
+
+__global__ void cc_compress(int64_t N, int32_t* parent)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+         v += (int64_t)gridDim.x * blockDim.x)
+        parent[v] = find_root(parent, (int32_t)v);
+}
+
+// per component (indexed by its label): minimum rank, size
+__global__ void comp_stats(int64_t N, const int32_t* label, const int32_t* r, int32_t* cmin_r,
+                           int32_t* csize)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        atomicMin(cmin_r + label[v], r[v]);
+        atomicAdd(csize + label[v], 1);
+    }
+}
+
+// starts[k] = 1 if the vertex of rank k is the minimum-rank vertex of its component
+__global__ void comp_start_flags(int64_t N, const uint32_t* by_rank, const int32_t* label,
+                                 const int32_t* cmin_r, int32_t* flag)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v = (int32_t)by_rank[k];
+        flag[k] = cmin_r[label[v]] == (int32_t)k ? 1 : 0;
+    }
+}
+
+// component order: index = number of component starts of smaller rank
+__global__ void comp_order(int64_t N, const uint32_t* by_rank, const int32_t* label, const int32_t* flag,
+                           const int64_t* flag_scan, int32_t* cidx, int32_t* roots, int64_t* size_by_idx,
+                           const int32_t* csize)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[k]) continue;
+        int32_t v = (int32_t)by_rank[k];
+        int32_t c = (int32_t)flag_scan[k];
+        cidx[label[v]] = c;
+        roots[c] = v;
+        size_by_idx[c] = csize[label[v]];
+    }
+}
+
+// ---- level-synchronous multi-source BFS (distances only) ------------------------
+
+struct BfsParams {
+    int64_t N;
+    const int64_t* gp;
+    const int32_t* adj;
+    const int32_t* sources;
+    int64_t nsrc;
+    int32_t* dist;      // N, pre-set to kUnvisited
+    int32_t* qa;        // N
+    int32_t* qb;        // N
+    int64_t* cnt;       // 3 rotating frontier counters, zeroed
+    int32_t* nlevels;   // out
+    GridBarrier gb;
+};
+
+__global__ void __launch_bounds__(kBlock) bfs_levels(BfsParams p)
+{
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = tid; k < p.nsrc; k += nth) {
+        p.dist[p.sources[k]] = 0;
+        p.qa[k] = p.sources[k];
+    }
+    if (tid == 0) p.cnt[0] = p.nsrc;
+    if (!grid_sync(p.gb)) return;
+    int32_t* cur = p.qa;
+    int32_t* nxt = p.qb;
+    int L = 0;
+    for (;;) {
+        int64_t ncur = *(volatile int64_t*)(p.cnt + (L % 3));
+        if (ncur == 0) break;
+        if (tid == 0) p.cnt[(L + 2) % 3] = 0;
+        int64_t* cnext = p.cnt + ((L + 1) % 3);
+        for (int64_t k = tid; k < ncur; k += nth) {
+            int32_t u = cur[k];
+            for (int64_t e = p.gp[u]; e < p.gp[u + 1]; ++e) {
+                int32_t w = p.adj[e];
+                if (ld_volatile_i32(p.dist + w) != kUnvisited) continue;
+                if (atomicCAS(p.dist + w, kUnvisited, L + 1) == kUnvisited) {
+                    unsigned long long pos = atomicAdd((unsigned long long*)cnext, 1ull);
+                    if ((int64_t)pos < p.N) nxt[pos] = w;
+                    else atomicCAS(p.gb.err, 0, (int)kDevOverflow);
+                }
+            }
+        }
+        if (!grid_sync(p.gb)) return;
+        int32_t* t = cur;
+        cur = nxt;
+        nxt = t;
+        ++L;
+    }
+    if (tid == 0) *p.nlevels = L;
+}
+
+__global__ void ecc_per_comp(int64_t N, const int32_t* dist, const int32_t* label, int32_t* ecc)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+         v += (int64_t)gridDim.x * blockDim.x)
+        if (dist[v] >= 0) atomicMax(ecc + label[v], dist[v]);
+}
+
+__global__ void last_level_min(int64_t N, const int32_t* dist, const int32_t* label, const int32_t* ecc,
+                               const int32_t* r, int32_t* cand_r)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+         v += (int64_t)gridDim.x * blockDim.x)
+        if (dist[v] >= 0 && dist[v] == ecc[label[v]]) atomicMin(cand_r + label[v], r[v]);
+}
+
+// George-Liu step per component (indexed by component order c).  active[c]:
+// 1 while the root may still move.  Phase A (after the BFS from the roots):
+// remember ecc(root) and the candidate u.  Phase B (after the BFS from the
+// candidates): move when ecc(u) > ecc(root).
+__global__ void gl_record_root(int64_t C, const int32_t* roots, const int32_t* label, const int32_t* ecc,
+                               const int32_t* cand_r, const uint32_t* by_rank, int32_t* ecc_root,
+                               int32_t* cand, const int32_t* active)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (!active[c]) continue;
+        int32_t lab = label[roots[c]];
+        ecc_root[c] = ecc[lab];
+        cand[c] = (int32_t)by_rank[cand_r[lab]];
+    }
+}
+
+__global__ void gl_compare(int64_t C, int32_t* roots, const int32_t* label, const int32_t* ecc,
+                           const int32_t* cand_r, const uint32_t* by_rank, int32_t* ecc_root,
+                           int32_t* cand, int32_t* active, int* any_active)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (!active[c]) continue;
+        int32_t lab = label[roots[c]];
+        int32_t e_u = ecc[lab];
+        if (e_u > ecc_root[c]) {
+            roots[c] = cand[c];
+            ecc_root[c] = e_u;
+            cand[c] = (int32_t)by_rank[cand_r[lab]];
+            *any_active = 1;
+        } else {
+            active[c] = 0;
+        }
+    }
+}
+
+__global__ void gather_active_sources(int64_t C, const int32_t* which, const int32_t* active, int32_t* src,
+                                      int64_t* nsrc)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+         c += (int64_t)gridDim.x * blockDim.x)
+        if (active[c]) src[atomicAdd((unsigned long long*)nsrc, 1ull)] = which[c];
+}
+
+// ---- Cuthill-McKee levels (all components at once) ----------------------------
+
+struct CmParams {
+    int64_t N;
+    const int64_t* gp;
+    const int32_t* adj_r;    // adjacency sorted by rank
+    const int32_t* label;
+    const int32_t* cidx;     // component order index by label
+    const int64_t* cbase;    // first CM position of each component (by order index)
+    const int32_t* roots;    // by order index
+    int64_t C;
+    int32_t* vis;            // N, kUnvisited
+    int32_t* claim;          // N, INT32_MAX
+    int32_t* fa;             // N
+    int32_t* fb;             // N
+    int64_t* cnt;            // N child counts / local offsets
+    int64_t* placed;         // 2*C, double buffered by level parity
+    int64_t* seg_start;      // C
+    int64_t* bsum;           // gridDim + 1
+    int32_t* cm_order;       // N, out
+    int64_t* nlevels;        // out
+    GridBarrier gb;
+};
+
+__global__ void __launch_bounds__(kBlock) cm_levels(CmParams p)
+{
+    __shared__ int64_t s_tot;
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = tid; c < p.C; c += nth) {
+        p.fa[c] = p.roots[c];
+        p.vis[p.roots[c]] = 0;
+        p.placed[c] = 0;
+    }
+    if (!grid_sync(p.gb)) return;
+    int32_t* cur = p.fa;
+    int32_t* nxt = p.fb;
+    int64_t F = p.C;
+    int L = 0;
+    while (F > 0) {
+        int64_t* placedA = p.placed + (L & 1) * p.C;
+        int64_t* placedB = p.placed + ((L + 1) & 1) * p.C;
+        // P1: claim children, mark component segment starts
+        for (int64_t k = tid; k < F; k += nth) {
+            int32_t u = cur[k];
+            int32_t c = p.cidx[p.label[u]];
+            if (k == 0 || p.cidx[p.label[cur[k - 1]]] != c) p.seg_start[c] = k;
+            for (int64_t e = p.gp[u]; e < p.gp[u + 1]; ++e) {
+                int32_t w = p.adj_r[e];
+                if (ld_volatile_i32(p.vis + w) == kUnvisited) atomicMin(p.claim + w, (int32_t)k);
+            }
+        }
+        if (!grid_sync(p.gb)) return;
+        // P2: per block, a contiguous chunk of the frontier: child counts and the
+        // block-local exclusive scan
+        int64_t chunk = ceil_div(F, (int64_t)gridDim.x);
+        int64_t c0 = (int64_t)blockIdx.x * chunk, c1 = c0 + chunk < F ? c0 + chunk : F;
+        int64_t carry = 0;
+        for (int64_t base = c0; base < c1; base += blockDim.x) {
+            int64_t k = base + threadIdx.x;
+            int64_t n_child = 0;
+            if (k < c1) {
+                int32_t u = cur[k];
+                for (int64_t e = p.gp[u]; e < p.gp[u + 1]; ++e) {
+                    int32_t w = p.adj_r[e];
+                    if (p.vis[w] == kUnvisited && p.claim[w] == (int32_t)k) ++n_child;
+                }
+            }
+            // block exclusive scan of n_child
+            __shared__ int64_t wsum[kBlock / kWarp];
+            int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+            int64_t inc = n_child;
+            for (int o = 1; o < 32; o <<= 1) {
+                int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t;
+            }
+            if (lane == 31) wsum[wid] = inc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int64_t run = 0;
+                for (int w = 0; w < kBlock / kWarp; ++w) {
+                    int64_t t = wsum[w];
+                    wsum[w] = run;
+                    run += t;
+                }
+                s_tot = run;
+            }
+            __syncthreads();
+            if (k < c1) p.cnt[k] = carry + wsum[wid] + inc - n_child;
+            carry += s_tot;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) p.bsum[blockIdx.x] = carry;
+        if (!grid_sync(p.gb)) return;
+        // P3: exclusive scan of the block sums (block 0)
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            int64_t run = 0;
+            for (unsigned b = 0; b < gridDim.x; ++b) {
+                int64_t t = p.bsum[b];
+                p.bsum[b] = run;
+                run += t;
+            }
+            p.bsum[gridDim.x] = run;
+        }
+        if (!grid_sync(p.gb)) return;
+        // P4: positions of this level, children into the next frontier
+        for (int64_t k = tid; k < F; k += nth) {
+            int32_t u = cur[k];
+            int32_t c = p.cidx[p.label[u]];
+            int64_t s0 = p.seg_start[c];
+            int64_t pos = p.cbase[c] + placedA[c] + (k - s0);
+            if (pos >= 0 && pos < p.N) p.cm_order[pos] = u;
+            else atomicCAS(p.gb.err, 0, (int)kDevOverflow);
+            bool seg_end = (k == F - 1) || p.cidx[p.label[cur[k + 1]]] != c;
+            if (seg_end) placedB[c] = placedA[c] + (k + 1 - s0);
+            int64_t o = p.cnt[k] + p.bsum[k / chunk];
+            for (int64_t e = p.gp[u]; e < p.gp[u + 1]; ++e) {
+                int32_t w = p.adj_r[e];
+                if (p.vis[w] == kUnvisited && p.claim[w] == (int32_t)k) {
+                    if (o >= 0 && o < p.N) nxt[o] = w;
+                    else atomicCAS(p.gb.err, 0, (int)kDevOverflow);
+                    ++o;
+                    p.vis[w] = L + 1;
+                }
+            }
+        }
+        // components absent from this level keep their count
+        if (!grid_sync(p.gb)) return;
+        int64_t Fn = *(volatile int64_t*)(p.bsum + gridDim.x);
+        // carry placed counts of components that had no vertex in this level
+        for (int64_t c = tid; c < p.C; c += nth) {
+            // a component is in F_L iff seg_start[c] points at one of its vertices
+            int64_t s0 = p.seg_start[c];
+            bool present = s0 < F && p.cidx[p.label[cur[s0]]] == (int32_t)c;
+            if (!present) placedB[c] = placedA[c];
+        }
+        if (!grid_sync(p.gb)) return;
+        int32_t* t = cur;
+        cur = nxt;
+        nxt = t;
+        F = Fn;
+        ++L;
+    }
+    if (tid == 0) *p.nlevels = L;
+}
+
+__global__ void reverse_into_perm(int64_t N, const int32_t* cm_order, int32_t* perm)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x)
+        perm[N - 1 - k] = cm_order[k];
+}
+
+inline unsigned grid_for(int64_t n) { return (unsigned)std::min<int64_t>(ceil_div(n, kBlock) + 1, 65535); }
+
+}  // namespace
+
+void build_sym_graph(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, DBuf<int64_t>& gp,
+                     DBuf<int32_t>& adj, cudaStream_t st)
+{
+    DBuf<int32_t> row_of(nnz, st);
+    if (nnz) {
+        expand_rows<<<grid_for(N), kBlock, 0, st>>>(rp, N, row_of.p);
+        OBK_CHECK_LAUNCH();
+    }
+    // transpose pattern: stable sort of (column, row) by column
+    DBuf<uint64_t> keys(nnz, st);
+    DBuf<uint32_t> trow(nnz, st);
+    DBuf<int64_t> ccnt(N + 1, st), tp(N + 1, st);
+    OBK_CUDA(cudaMemsetAsync(ccnt.p, 0, (N + 1) * sizeof(int64_t), st));
+    if (nnz) {
+        col_keys<<<grid_for(nnz), kBlock, 0, st>>>(ci, nnz, keys.p, trow.p, row_of.p);
+        OBK_CHECK_LAUNCH();
+        radix_sort_pairs(keys.p, trow.p, nnz, bits_for((uint64_t)(N - 1)), st);
+        count_cols<<<grid_for(nnz), kBlock, 0, st>>>(ci, nnz, ccnt.p);
+        OBK_CHECK_LAUNCH();
+    }
+    exclusive_scan_i64(ccnt.p, tp.p, N, st);
+    DBuf<int64_t> deg(N + 1, st);
+    merge_sym<false><<<grid_for(N), kBlock, 0, st>>>(N, rp, ci, tp.p, trow.p, nullptr, deg.p, nullptr);
+    OBK_CHECK_LAUNCH();
+    gp.alloc(N + 1, st);
+    exclusive_scan_i64(deg.p, gp.p, N, st);
+    int64_t M = read_scalar(gp.p + N, st);
+    adj.alloc(M > 0 ? M : 1, st);
+    merge_sym<true><<<grid_for(N), kBlock, 0, st>>>(N, rp, ci, tp.p, trow.p, gp.p, nullptr, adj.p);
+    OBK_CHECK_LAUNCH();
+}
+
+void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, int32_t* perm,
+                 long long spin_limit, int* d_err, RcmStats* stats, cudaStream_t st)
+{
+    DevInfo di = dev_info();
+    // 1. symmetric graph
+    DBuf<int64_t> gp;
+    DBuf<int32_t> adj;
+    build_sym_graph(N, rp, ci, nnz, gp, adj, st);
+    int64_t M = read_scalar(gp.p + N, st);
+
+    // 2. ranks in (deg, index) order
+    int bN = bits_for((uint64_t)(N > 1 ? N - 1 : 1));
+    DBuf<uint64_t> dk(N, st);
+    DBuf<uint32_t> by_rank(N, st);
+    deg_keys<<<grid_for(N), kBlock, 0, st>>>(N, gp.p, bN, dk.p, by_rank.p);
+    OBK_CHECK_LAUNCH();
+    int64_t maxdeg_bound = M;  // degrees are at most M
+    radix_sort_pairs(dk.p, by_rank.p, N, bN + bits_for((uint64_t)maxdeg_bound), st);
+    dk.release();
+    DBuf<int32_t> r(N, st);
+    rank_of<<<grid_for(N), kBlock, 0, st>>>(N, by_rank.p, r.p);
+    OBK_CHECK_LAUNCH();
+
+    // 3. adjacency lists sorted by rank
+    DBuf<uint32_t> ak(M, st), av(M, st);
+    if (M) {
+        adj_rank_keys<<<grid_for(M), kBlock, 0, st>>>(M, adj.p, r.p, ak.p, av.p);
+        OBK_CHECK_LAUNCH();
+        segmented_sort_u32(gp.p, N, ak.p, av.p, st);
+    }
+    ak.release();
+    const int32_t* adj_r = reinterpret_cast<const int32_t*>(av.p);
+
+    // 4. connected components (label = smallest vertex index)
+    DBuf<int32_t> label(N, st);
+    DBuf<int> changed(1, st);
+    cc_init<<<grid_for(N), kBlock, 0, st>>>(N, label.p);
+    OBK_CHECK_LAUNCH();
+    for (int it = 0; it < 100000; ++it) {
+        OBK_CUDA(cudaMemsetAsync(changed.p, 0, sizeof(int), st));
+        cc_hook<<<grid_for(N), kBlock, 0, st>>>(N, gp.p, adj.p, label.p, changed.p);
+        OBK_CHECK_LAUNCH();
+        cc_compress<<<grid_for(N), kBlock, 0, st>>>(N, label.p);
+        OBK_CHECK_LAUNCH();
+        if (read_scalar(changed.p, st) == 0) break;
+    }
+    adj.release();
+
+    // 5. component order and bases
+    DBuf<int32_t> cmin_r(N, st), csize(N, st), flag(N, st), cidx(N, st);
+    DBuf<int64_t> fscan(N + 1, st);
+    OBK_CUDA(cudaMemsetAsync(cmin_r.p, 0x7f, N * sizeof(int32_t), st));
+    OBK_CUDA(cudaMemsetAsync(csize.p, 0, N * sizeof(int32_t), st));
+    comp_stats<<<grid_for(N), kBlock, 0, st>>>(N, label.p, r.p, cmin_r.p, csize.p);
+    OBK_CHECK_LAUNCH();
+    comp_start_flags<<<grid_for(N), kBlock, 0, st>>>(N, by_rank.p, label.p, cmin_r.p, flag.p);
+    OBK_CHECK_LAUNCH();
+    exclusive_scan_i32_to_i64(flag.p, fscan.p, N, st);
+    int64_t C = read_scalar(fscan.p + N, st);
+    DBuf<int32_t> roots(C, st);
+    DBuf<int64_t> size_by_idx(C, st), cbase(C + 1, st);
+    comp_order<<<grid_for(N), kBlock, 0, st>>>(N, by_rank.p, label.p, flag.p, fscan.p, cidx.p, roots.p,
+                                               size_by_idx.p, csize.p);
+    OBK_CHECK_LAUNCH();
+    exclusive_scan_i64(size_by_idx.p, cbase.p, C, st);
+
+    // 6. George-Liu pseudo-peripheral roots, all components at once
+    DBuf<int32_t> dist(N, st), qa(N, st), qb(N, st), ecc(N, st), cand_r(N, st);
+    DBuf<int32_t> ecc_root(C, st), cand(C, st), active(C, st), src(C, st);
+    DBuf<int64_t> cnt3(3, st), nsrc(1, st);
+    DBuf<int32_t> nlev(1, st);
+    DBuf<unsigned> bar(2, st);
+    int any_h = 1;
+    DBuf<int> any(1, st);
+    // all components start active (any nonzero word is "active")
+    OBK_CUDA(cudaMemsetAsync(active.p, 1, C * sizeof(int32_t), st));
+    int bfs_grid = coop_grid((const void*)bfs_levels, kBlock, 0, (int64_t)di.sms * 8);
+    auto run_bfs = [&](const int32_t* sources, int64_t ns) {
+        OBK_CUDA(cudaMemsetAsync(dist.p, 0xff, N * sizeof(int32_t), st));
+        OBK_CUDA(cudaMemsetAsync(cnt3.p, 0, 3 * sizeof(int64_t), st));
+        OBK_CUDA(cudaMemsetAsync(bar.p, 0, 2 * sizeof(unsigned), st));
+        BfsParams bp{N, gp.p, adj_r, sources, ns, dist.p, qa.p, qb.p, cnt3.p, nlev.p,
+                     GridBarrier{bar.p, d_err, spin_limit}};
+        void* args[] = {&bp};
+        OBK_COOP_LAUNCH(bfs_levels, bfs_grid, kBlock, args, st);
+        OBK_CUDA(cudaMemsetAsync(ecc.p, 0, N * sizeof(int32_t), st));
+        OBK_CUDA(cudaMemsetAsync(cand_r.p, 0x7f, N * sizeof(int32_t), st));
+        ecc_per_comp<<<grid_for(N), kBlock, 0, st>>>(N, dist.p, label.p, ecc.p);
+        OBK_CHECK_LAUNCH();
+        last_level_min<<<grid_for(N), kBlock, 0, st>>>(N, dist.p, label.p, ecc.p, r.p, cand_r.p);
+        OBK_CHECK_LAUNCH();
+    };
+    run_bfs(roots.p, C);
+    gl_record_root<<<grid_for(C), kBlock, 0, st>>>(C, roots.p, label.p, ecc.p, cand_r.p, by_rank.p,
+                                                    ecc_root.p, cand.p, active.p);
+    OBK_CHECK_LAUNCH();
+    int gl_rounds = 0;
+    while (any_h) {
+        ++gl_rounds;
+        OBK_CUDA(cudaMemsetAsync(nsrc.p, 0, sizeof(int64_t), st));
+        gather_active_sources<<<grid_for(C), kBlock, 0, st>>>(C, cand.p, active.p, src.p, nsrc.p);
+        OBK_CHECK_LAUNCH();
+        int64_t ns = read_scalar(nsrc.p, st);
+        if (ns == 0) break;
+        run_bfs(src.p, ns);
+        OBK_CUDA(cudaMemsetAsync(any.p, 0, sizeof(int), st));
+        gl_compare<<<grid_for(C), kBlock, 0, st>>>(C, roots.p, label.p, ecc.p, cand_r.p, by_rank.p,
+                                                    ecc_root.p, cand.p, active.p, any.p);
+        OBK_CHECK_LAUNCH();
+        any_h = read_scalar(any.p, st);
+        if (read_scalar(d_err, st) != 0) throw Error{-4, "bounded wait expired in RCM search"};
+    }
+    dist.release(); ecc.release(); cand_r.release(); ecc_root.release(); cand.release();
+    active.release(); src.release();
+
+    // 7. Cuthill-McKee levels
+    DBuf<int32_t> vis(N, st), claim(N, st), cm(N, st);
+    DBuf<int64_t> ccnt(N, st), placed(2 * C, st), segs(C, st), nl(1, st);
+    OBK_CUDA(cudaMemsetAsync(vis.p, 0xff, N * sizeof(int32_t), st));
+    OBK_CUDA(cudaMemsetAsync(claim.p, 0x7f, N * sizeof(int32_t), st));
+    OBK_CUDA(cudaMemsetAsync(placed.p, 0, 2 * C * sizeof(int64_t), st));
+    OBK_CUDA(cudaMemsetAsync(segs.p, 0x7f, C * sizeof(int64_t), st));
+    OBK_CUDA(cudaMemsetAsync(bar.p, 0, 2 * sizeof(unsigned), st));
+    int cm_grid = coop_grid((const void*)cm_levels, kBlock, 0, (int64_t)di.sms * 8);
+    DBuf<int64_t> bsum(cm_grid + 1, st);
+    CmParams cp{N, gp.p, adj_r, label.p, cidx.p, cbase.p, roots.p, C, vis.p, claim.p, qa.p, qb.p,
+                ccnt.p, placed.p, segs.p, bsum.p, cm.p, nl.p, GridBarrier{bar.p, d_err, spin_limit}};
+    void* args[] = {&cp};
+    OBK_COOP_LAUNCH(cm_levels, cm_grid, kBlock, args, st);
+    if (read_scalar(d_err, st) != 0) throw Error{-4, "bounded wait expired in Cuthill-McKee levels"};
+    reverse_into_perm<<<grid_for(N), kBlock, 0, st>>>(N, cm.p, perm);
+    OBK_CHECK_LAUNCH();
+    if (stats) {
+        stats->components = C;
+        stats->levels = read_scalar(nl.p, st);
+        stats->gl_rounds = gl_rounds;
+        stats->graph_edges = M;
+    }
+}
+
+}  // namespace obk

@@ -1,0 +1,252 @@
+// server.cu -- request loop with continuous batching (obk_submit / obk_poll).
+//
+// Requests are queued on the host and admitted while the device memory they
+// are estimated to need fits the HBM budget.  Each admitted request runs on
+// one of max_streams worker streams, so requests admitted while others run
+// overlap on the device; a request that does not fit yet stays PENDING until
+// running ones release their memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/obk.h"
+#include "common.cuh"
+
+namespace {
+
+struct Request {
+    uint64_t ticket = 0;
+    int64_t m = 0, n = 0;
+    double thr = 0.1, tol = 1e-8;
+    int64_t maxit = 1000;
+    obk_opts opts{};
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci;
+    std::vector<double> v, f, x0, x;
+    bool has_x0 = false;
+    size_t bytes = 0;
+    std::atomic<int> state{0};  // 0 queued, 1 running, 2 done
+    std::atomic<bool> cancel{false};
+    int status = OBK_PENDING;
+    obk_info info{};
+    std::string err;
+};
+
+// Upper estimate of the device bytes a solve needs at its peak (setup).
+size_t footprint(int64_t m, int64_t n, int64_t nnz)
+{
+    int64_t N = std::max(m, n);
+    return (size_t)(nnz * 96 + N * 160 + (64 << 20));
+}
+
+}  // namespace
+
+struct obk_server {
+    size_t budget = 0, in_use = 0;
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::map<uint64_t, std::shared_ptr<Request>> all;
+    uint64_t next_ticket = 1;
+    bool stopping = false;
+    std::vector<std::thread> workers;
+};
+
+static void worker_loop(obk_server* s)
+{
+    cudaSetDevice(s->device);
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return;
+    for (;;) {
+        std::shared_ptr<Request> r;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            for (;;) {
+                if (s->stopping && s->queue.empty()) {
+                    lk.unlock();
+                    cudaStreamDestroy(st);
+                    return;
+                }
+                // first queued request that fits the remaining budget (arrival order)
+                auto it = std::find_if(s->queue.begin(), s->queue.end(), [&](const std::shared_ptr<Request>& q) {
+                    return q->cancel.load() || s->in_use + q->bytes <= s->budget;
+                });
+                if (it != s->queue.end()) {
+                    r = *it;
+                    s->queue.erase(it);
+                    if (!r->cancel.load()) s->in_use += r->bytes;
+                    break;
+                }
+                s->cv.wait(lk);
+            }
+        }
+        if (r->cancel.load()) {
+            r->status = OBK_ERR_CANCELLED;
+            r->state.store(2);
+            continue;
+        }
+        r->state.store(1);
+        obk_csr A{r->rp.data(), r->ci.data(), r->v.data(), (int64_t)r->ci.size(), 0};
+        obk_handle* h = nullptr;
+        obk_status rc = obk_create_on_stream(&A, r->m, r->n, r->thr, (void*)st, &h);
+        if (rc == OBK_OK) {
+            r->x.assign((size_t)r->n, 0.0);
+            if (r->cancel.load()) rc = OBK_ERR_CANCELLED;
+            else
+                rc = obk_solve_ex(h, &r->opts, r->f.data(), r->has_x0 ? r->x0.data() : nullptr, r->tol, r->maxit,
+                                  r->x.data(), &r->info);
+        }
+        if (rc < 0) r->err = obk_last_error();
+        obk_destroy(h);
+        if (r->cancel.load() && rc >= 0) rc = OBK_ERR_CANCELLED;
+        r->status = rc;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->in_use -= r->bytes;
+        }
+        r->state.store(2);
+        s->cv.notify_all();
+    }
+}
+
+extern "C" {
+
+obk_status obk_server_create(size_t hbm_budget_bytes, int32_t max_streams, obk_server** out)
+{
+    if (!out) return OBK_ERR_INVALID;
+    *out = nullptr;
+    if (max_streams < 0 || max_streams > 256) {
+        obk::set_last_error("max_streams must be in [0, 256]");
+        return OBK_ERR_INVALID;
+    }
+    obk_server* s = new (std::nothrow) obk_server();
+    if (!s) return OBK_ERR_NOMEM;
+    s->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)150 << 30;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        obk::set_last_error("no CUDA device");
+        return OBK_ERR_CUDA;
+    }
+    int nw = max_streams ? max_streams : 8;
+    for (int i = 0; i < nw; ++i) s->workers.emplace_back(worker_loop, s);
+    *out = s;
+    return OBK_OK;
+}
+
+obk_status obk_submit(obk_server* s, const obk_csr* A, int64_t m, int64_t n, double thr, const double* f,
+                      const double* x0, double tol, int64_t maxit, const obk_opts* opts, uint64_t* ticket)
+{
+    if (!s || !A || !f || !ticket || m <= 0 || n <= 0 || A->nnz < 0 || !A->row_ptr ||
+        (A->nnz > 0 && (!A->col_idx || !A->val))) {
+        obk::set_last_error("invalid request arguments");
+        return OBK_ERR_INVALID;
+    }
+    if (!(thr > 0.0 && thr <= 1.0) || !(tol > 0.0) || maxit < 1) {
+        obk::set_last_error("thr must be in (0, 1], tol > 0, maxit >= 1");
+        return OBK_ERR_INVALID;
+    }
+    auto r = std::make_shared<Request>();
+    r->m = m;
+    r->n = n;
+    r->thr = thr;
+    r->tol = tol;
+    r->maxit = maxit;
+    if (opts) r->opts = *opts;
+    r->bytes = footprint(m, n, A->nnz);
+    if (r->bytes > s->budget) {
+        obk::set_last_error("request exceeds the server's HBM budget");
+        return OBK_ERR_BUDGET;
+    }
+    try {
+        r->rp.resize((size_t)m + 1);
+        r->ci.resize((size_t)A->nnz);
+        r->v.resize((size_t)A->nnz);
+        r->f.resize((size_t)m);
+        cudaMemcpyKind k = A->device_ptrs ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+        if (cudaMemcpy(r->rp.data(), A->row_ptr, (m + 1) * sizeof(int64_t), k) != cudaSuccess ||
+            (A->nnz && cudaMemcpy(r->ci.data(), A->col_idx, A->nnz * sizeof(int32_t), k) != cudaSuccess) ||
+            (A->nnz && cudaMemcpy(r->v.data(), A->val, A->nnz * sizeof(double), k) != cudaSuccess)) {
+            obk::set_last_error("copying the request's matrix failed");
+            return OBK_ERR_CUDA;
+        }
+        cudaPointerAttributes pa;
+        auto kind_of = [&](const void* p) {
+            if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) { (void)cudaGetLastError(); return cudaMemcpyHostToHost; }
+            return (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) ? cudaMemcpyDeviceToHost
+                                                                                          : cudaMemcpyHostToHost;
+        };
+        if (cudaMemcpy(r->f.data(), f, m * sizeof(double), kind_of(f)) != cudaSuccess) return OBK_ERR_CUDA;
+        if (x0) {
+            r->x0.resize((size_t)n);
+            r->has_x0 = true;
+            if (cudaMemcpy(r->x0.data(), x0, n * sizeof(double), kind_of(x0)) != cudaSuccess) return OBK_ERR_CUDA;
+        }
+    } catch (const std::bad_alloc&) {
+        return OBK_ERR_NOMEM;
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        r->ticket = s->next_ticket++;
+        *ticket = r->ticket;
+        s->all[r->ticket] = r;
+        s->queue.push_back(r);
+    }
+    s->cv.notify_all();
+    return OBK_OK;
+}
+
+obk_status obk_poll(obk_server* s, uint64_t ticket, double* x_out, obk_info* info)
+{
+    if (!s) return OBK_ERR_INVALID;
+    std::shared_ptr<Request> r;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->all.find(ticket);
+        if (it == s->all.end()) {
+            obk::set_last_error("unknown ticket");
+            return OBK_ERR_NOT_FOUND;
+        }
+        r = it->second;
+        if (r->state.load() != 2) return OBK_PENDING;
+        s->all.erase(it);
+    }
+    if (x_out && r->status >= 0 && !r->x.empty()) std::copy(r->x.begin(), r->x.end(), x_out);
+    if (info) *info = r->info;
+    if (r->status < 0) obk::set_last_error(r->err.empty() ? "request failed" : r->err);
+    return (obk_status)r->status;
+}
+
+obk_status obk_cancel(obk_server* s, uint64_t ticket)
+{
+    if (!s) return OBK_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return OBK_ERR_NOT_FOUND;
+    it->second->cancel.store(true);
+    s->cv.notify_all();
+    return OBK_OK;
+}
+
+void obk_server_destroy(obk_server* s)
+{
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stopping = true;
+    }
+    s->cv.notify_all();
+    for (auto& t : s->workers) t.join();
+    delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,697 @@
+// setup.cu -- validation, symmetric permutation (Eq. 3.1), row norms (Eq. 1.2)
+// and the cosine-threshold row grouping of Section 3.3 taken at one row per
+// block, plus the memory layout used by the sweep.
+//
+// Grouping, as fixed for this library (bit-identical to the CPU reference):
+//   nsq_i   = ((a_1*a_1 + a_2*a_2) + ...) over ascending columns, each product
+//             and sum rounded separately (no fused multiply-add)
+//   dot_ij  = left fold of a_ic*a_jc over the common columns, ascending
+//   cos_ij  = dot_ij / (sqrt(nsq_i) * sqrt(nsq_j)), IEEE division and sqrt
+//   conflict when |cos_ij| >= thr; row i joins the smallest group holding no
+//   conflicting earlier row (greedy first fit in index order); rows with
+//   nsq = 0 join no group.
+//
+// GPU formulation: dot products are accumulated Gustavson style (one warp per
+// row i walks its columns in ascending order and, for each column, adds the
+// products with every earlier row of that column into a per-warp hash table),
+// which keeps the per-pair ascending-column order.  First fit is computed by a
+// cooperative dataflow kernel: a row is coloured as soon as all its
+// conflicting earlier rows are, with the colour = smallest unused by them.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace obk {
+namespace {
+
+constexpr int kBlock = 256;
+inline unsigned grid_for(int64_t n) { return (unsigned)std::min<int64_t>(ceil_div(n, kBlock) + 1, 65535); }
+
+#define GRID_STRIDE(i, n)                                                              \
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); \
+         i += (int64_t)gridDim.x * blockDim.x)
+
+// ---- validation --------------------------------------------------------------
+
+__global__ void validate_rows(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci,
+                              const double* v, int64_t nnz, int* bad)
+{
+    GRID_STRIDE(i, m)
+    {
+        int64_t b = rp[i], e = rp[i + 1];
+        if (b > e || b < 0 || e > nnz) { atomicOr(bad, 1); continue; }
+        for (int64_t k = b; k < e; ++k) {
+            int32_t c = ci[k];
+            if (c < 0 || (int64_t)c >= n) { atomicOr(bad, 2); break; }
+            if (k > b && c <= ci[k - 1]) { atomicOr(bad, 4); break; }
+            if (!isfinite(v[k])) { atomicOr(bad, 8); break; }
+        }
+    }
+}
+
+__global__ void bandwidth_kernel(int64_t N, const int64_t* rp, const int32_t* ci,
+                                 unsigned long long* bw)
+{
+    GRID_STRIDE(i, N)
+    {
+        unsigned long long mx = 0;
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+            long long d = (long long)i - ci[e];
+            unsigned long long a = (unsigned long long)(d < 0 ? -d : d);
+            mx = a > mx ? a : mx;
+        }
+        if (mx) atomicMax(bw, mx);
+    }
+}
+
+// ---- permutation -------------------------------------------------------------
+
+__global__ void inverse_perm(int64_t N, const int32_t* perm, int32_t* iperm)
+{
+    GRID_STRIDE(k, N) iperm[perm[k]] = (int32_t)k;
+}
+
+__global__ void permuted_lengths(int64_t N, const int64_t* rp, const int32_t* perm, int64_t* len)
+{
+    GRID_STRIDE(k, N) len[k] = rp[perm[k] + 1] - rp[perm[k]];
+}
+
+__global__ void permute_gather(int64_t N, const int64_t* rp, const int32_t* ci, const int32_t* perm,
+                               const int32_t* iperm, const int64_t* rp_t, uint32_t* keys,
+                               uint32_t* src)
+{
+    // one warp per new row
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = w; k < N; k += nw) {
+        int64_t o = rp[perm[k]], len = rp[perm[k] + 1] - o, d = rp_t[k];
+        for (int64_t t = lane; t < len; t += 32) {
+            keys[d + t] = (uint32_t)iperm[ci[o + t]];
+            src[d + t] = (uint32_t)(o + t);
+        }
+    }
+}
+
+__global__ void permute_finish(int64_t nnz, const uint32_t* keys, const uint32_t* src, const double* v,
+                               int32_t* ci_t, double* v_t)
+{
+    GRID_STRIDE(e, nnz)
+    {
+        ci_t[e] = (int32_t)keys[e];
+        v_t[e] = v[src[e]];
+    }
+}
+
+// ---- norms and transposition -------------------------------------------------
+
+__global__ void row_norms_exact(int64_t N, const int64_t* rp, const double* v, double* nsq, double* s)
+{
+    GRID_STRIDE(i, N)
+    {
+        double acc = 0.0;
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) acc = __dadd_rn(acc, __dmul_rn(v[e], v[e]));
+        nsq[i] = acc;
+        s[i] = __dsqrt_rn(acc);
+    }
+}
+
+__global__ void expand_rows_k(const int64_t* rp, int64_t N, int32_t* row_of)
+{
+    GRID_STRIDE(i, N)
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) row_of[e] = (int32_t)i;
+}
+
+__global__ void col_key_kernel(int64_t nnz, const int32_t* ci, uint64_t* keys, uint32_t* vals)
+{
+    GRID_STRIDE(e, nnz)
+    {
+        keys[e] = (uint64_t)(uint32_t)ci[e];
+        vals[e] = (uint32_t)e;
+    }
+}
+
+__global__ void count_cols_k(int64_t nnz, const int32_t* ci, int64_t* cnt)
+{
+    GRID_STRIDE(e, nnz) atomicAdd((unsigned long long*)&cnt[ci[e]], 1ull);
+}
+
+// CSC arrays from the sorted entry list; pos_of[e] = CSC position of entry e.
+__global__ void csc_fill(int64_t nnz, const uint32_t* order, const int32_t* row_of, const double* v,
+                         int32_t* crow, double* cval, int64_t* pos_of)
+{
+    GRID_STRIDE(p, nnz)
+    {
+        uint32_t e = order[p];
+        crow[p] = row_of[e];
+        cval[p] = v[e];
+        pos_of[e] = p;
+    }
+}
+
+// ub[i] = number of (earlier row, shared column) incidences of row i; the rank
+// of entry (i, c) in column c counts the earlier rows of that column.
+__global__ void pair_upper_bound(int64_t N, const int64_t* rp, const int32_t* ci, const int64_t* cptr,
+                                 const int64_t* pos_of, int64_t* ub)
+{
+    GRID_STRIDE(i, N)
+    {
+        int64_t s = 0;
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) s += pos_of[e] - cptr[ci[e]];
+        ub[i] = s;
+    }
+}
+
+__host__ __device__ inline int64_t table_cap(int64_t ub)
+{
+    int64_t c = 32;
+    while (c < 2 * ub) c <<= 1;
+    return c;
+}
+
+__global__ void big_table_sizes(int64_t N, const int64_t* ub, int64_t smem_cap, int64_t* sz)
+{
+    GRID_STRIDE(i, N)
+    {
+        int64_t c = table_cap(ub[i]);
+        sz[i] = c > smem_cap ? c : 0;
+    }
+}
+
+// ---- pair cosines and conflict lists ------------------------------------------
+
+constexpr int kPairWarps = 8;
+constexpr int kPairCap = 512;  // hash slots per warp in shared memory
+constexpr int32_t kEmpty = -1;
+
+struct PairParams {
+    int64_t N;
+    const int64_t* rp;
+    const int32_t* ci;
+    const double* v;
+    const int64_t* cptr;
+    const int32_t* crow;
+    const double* cval;
+    const int64_t* pos_of;
+    const double* nsq;
+    const double* s;
+    double thr;
+    const int64_t* ub;
+    const int64_t* big_off;  // offsets into the global tables (rows whose table is too big)
+    int32_t* big_key;
+    double* big_val;
+    int32_t* conf_cnt;       // out
+    int64_t* conf_off;       // out
+    int32_t* pool;
+    int64_t pool_cap;
+    unsigned long long* pool_used;
+    unsigned long long* n_conflicts;
+    int* err;
+};
+
+__device__ __forceinline__ uint32_t hslot(int32_t j, uint32_t mask)
+{
+    return ((uint32_t)j * 0x9E3779B1u) & mask;
+}
+
+__global__ void __launch_bounds__(kPairWarps * 32) pair_conflicts(PairParams p)
+{
+    __shared__ int32_t skey[kPairWarps][kPairCap];
+    __shared__ double sval[kPairWarps][kPairCap];
+    int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    unsigned lt = (1u << lane) - 1u;
+    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = gw; i < p.N; i += nw) {
+        if (p.nsq[i] == 0.0) {
+            if (lane == 0) { p.conf_cnt[i] = 0; p.conf_off[i] = 0; }
+            continue;
+        }
+        int64_t cap = table_cap(p.ub[i]);
+        int32_t* key;
+        double* val;
+        if (cap <= kPairCap) {
+            key = skey[wl];
+            val = sval[wl];
+        } else {
+            key = p.big_key + p.big_off[i];
+            val = p.big_val + p.big_off[i];
+        }
+        uint32_t mask = (uint32_t)cap - 1u;
+        for (int64_t t = lane; t < cap; t += 32) { key[t] = kEmpty; val[t] = 0.0; }
+        __syncwarp();
+        for (int64_t e = p.rp[i]; e < p.rp[i + 1]; ++e) {
+            int32_t c = p.ci[e];
+            double a = p.v[e];
+            int64_t q0 = p.cptr[c], q1 = p.pos_of[e];  // earlier rows of column c
+            for (int64_t q = q0 + lane; q < q1; q += 32) {
+                int32_t j = p.crow[q];
+                if (p.nsq[j] == 0.0) continue;
+                double prod = __dmul_rn(a, p.cval[q]);
+                uint32_t h = hslot(j, mask);
+                int64_t probes = 0;
+                for (;;) {
+                    int32_t k = key[h];
+                    if (k == j) break;
+                    if (k == kEmpty) {
+                        int32_t old = atomicCAS(key + h, kEmpty, j);
+                        if (old == kEmpty || old == j) break;
+                    }
+                    h = (h + 1) & mask;
+                    if (++probes > cap) { h = 0xffffffffu; break; }
+                }
+                if (h == 0xffffffffu) { atomicCAS(p.err, 0, (int)kDevOverflow); continue; }
+                val[h] = __dadd_rn(val[h], prod);
+            }
+            __syncwarp();
+        }
+        // conflicts: count, reserve, write
+        double si = p.s[i];
+        int cnt = 0;
+        for (int64_t t0 = 0; t0 < cap; t0 += 32) {
+            int64_t t = t0 + lane;
+            bool conf = false;
+            if (t < cap) {
+                int32_t j = key[t];
+                if (j != kEmpty) {
+                    double cv = __ddiv_rn(val[t], __dmul_rn(p.s[j], si));
+                    conf = fabs(cv) >= p.thr;
+                }
+            }
+            cnt += __popc(__ballot_sync(0xffffffffu, conf));
+        }
+        unsigned long long base = 0;
+        if (lane == 0) {
+            base = atomicAdd(p.pool_used, (unsigned long long)cnt);
+            atomicAdd(p.n_conflicts, (unsigned long long)cnt);
+            p.conf_cnt[i] = cnt;
+            p.conf_off[i] = (int64_t)base;
+        }
+        base = __shfl_sync(0xffffffffu, base, 0);
+        bool fits = (int64_t)(base + cnt) <= p.pool_cap;
+        int run = 0;
+        if (fits) {
+            for (int64_t t0 = 0; t0 < cap; t0 += 32) {
+                int64_t t = t0 + lane;
+                bool conf = false;
+                int32_t j = kEmpty;
+                if (t < cap) {
+                    j = key[t];
+                    if (j != kEmpty) {
+                        double cv = __ddiv_rn(val[t], __dmul_rn(p.s[j], si));
+                        conf = fabs(cv) >= p.thr;
+                    }
+                }
+                unsigned b = __ballot_sync(0xffffffffu, conf);
+                if (conf) p.pool[base + run + __popc(b & lt)] = j;
+                run += __popc(b);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ---- greedy first-fit colouring (dataflow) ------------------------------------
+
+// colour of a row not coloured yet; equals the byte pattern 0x80 written by memset
+constexpr int32_t kUnset = (int32_t)0x80808080;
+
+struct ColorParams {
+    int64_t N;
+    const double* nsq;
+    const int32_t* conf_cnt;
+    const int64_t* conf_off;
+    const int32_t* pool;
+    int32_t* color;   // pre-set to kUnset
+    int* err;
+    long long limit;
+};
+
+__global__ void __launch_bounds__(kBlock) greedy_color(ColorParams p)
+{
+    int lane = threadIdx.x & 31;
+    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    volatile int32_t* col = p.color;
+    for (int64_t w = gw; w * 32 < p.N; w += nw) {
+        int64_t i = w * 32 + lane;
+        bool done = i >= p.N;
+        if (!done && p.nsq[i] == 0.0) {
+            col[i] = -1;
+            done = true;
+        }
+        long long spins = 0;
+        while (__any_sync(0xffffffffu, !done)) {
+            if (!done) {
+                int64_t o = p.conf_off[i];
+                int n = p.conf_cnt[i];
+                bool ready = true;
+                unsigned long long used = 0;
+                for (int t = 0; t < n; ++t) {
+                    int32_t cj = col[p.pool[o + t]];
+                    if (cj == kUnset) { ready = false; break; }
+                    if (cj < 64) used |= 1ull << cj;
+                }
+                if (ready) {
+                    int32_t g;
+                    if (~used != 0ull) {
+                        g = __ffsll((long long)~used) - 1;
+                    } else {
+                        g = 64;
+                        for (;;) {
+                            bool taken = false;
+                            for (int t = 0; t < n; ++t)
+                                if (col[p.pool[o + t]] == g) { taken = true; break; }
+                            if (!taken) break;
+                            ++g;
+                        }
+                    }
+                    col[i] = g;
+                    done = true;
+                }
+            }
+            if (++spins > p.limit) {
+                if (!done) atomicCAS(p.err, 0, (int)kDevTimeout);
+                break;
+            }
+            if (ld_volatile_i32(p.err) != 0) break;
+        }
+        if (__any_sync(0xffffffffu, ld_volatile_i32(p.err) != 0)) return;
+    }
+}
+
+__global__ void max_color(int64_t N, const int32_t* color, int* gmax)
+{
+    GRID_STRIDE(i, N) if (color[i] >= 0) atomicMax(gmax, color[i]);
+}
+
+// ---- group layout -------------------------------------------------------------
+
+__global__ void color_keys(int64_t N, const int32_t* color, int32_t G, uint64_t* keys, uint32_t* vals)
+{
+    GRID_STRIDE(i, N)
+    {
+        keys[i] = (uint64_t)(color[i] >= 0 ? color[i] : G);
+        vals[i] = (uint32_t)i;
+    }
+}
+
+__global__ void group_hist(int64_t N, const int32_t* color, int64_t* cnt)
+{
+    GRID_STRIDE(i, N) if (color[i] >= 0) atomicAdd((unsigned long long*)&cnt[color[i]], 1ull);
+}
+
+__global__ void gm_rows(int64_t Ngm, const uint32_t* order, const int64_t* rp, const double* nsq,
+                        int32_t* grp_row, int32_t* gm_of_row, int64_t* len, double* inv, float* inv32)
+{
+    GRID_STRIDE(k, Ngm)
+    {
+        int32_t i = (int32_t)order[k];
+        grp_row[k] = i;
+        gm_of_row[i] = (int32_t)k;
+        len[k] = rp[i + 1] - rp[i];
+        double d = 1.0 / nsq[i];
+        inv[k] = d;
+        if (inv32) inv32[k] = (float)d;
+    }
+}
+
+__global__ void gm_copy(int64_t Ngm, const int32_t* grp_row, const int64_t* rp, const int32_t* ci,
+                        const double* v, const int64_t* grp_rp, int32_t* gci, double* gv, float* gv32)
+{
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = w; k < Ngm; k += nw) {
+        int64_t o = rp[grp_row[k]], len = rp[grp_row[k] + 1] - o, d = grp_rp[k];
+        for (int64_t t = lane; t < len; t += 32) {
+            gci[d + t] = ci[o + t];
+            gv[d + t] = v[o + t];
+            if (gv32) gv32[d + t] = (float)v[o + t];
+        }
+    }
+}
+
+__global__ void csc_color_keys(int64_t nnz, const int32_t* crow, const int32_t* color, int32_t G,
+                               uint64_t* keys, uint32_t* vals)
+{
+    GRID_STRIDE(p, nnz)
+    {
+        int32_t c = color[crow[p]];
+        keys[p] = (uint64_t)(c >= 0 ? c : G);
+        vals[p] = (uint32_t)p;
+    }
+}
+
+__global__ void expand_cols(int64_t N, const int64_t* cptr, int32_t* col_of)
+{
+    GRID_STRIDE(c, N)
+    for (int64_t p = cptr[c]; p < cptr[c + 1]; ++p) col_of[p] = (int32_t)c;
+}
+
+// mirror entries in (group, column, row) order; seg flags mark (group, column) starts
+__global__ void mirror_fill(int64_t M, const uint32_t* order, const int32_t* crow, const double* cval,
+                            const int32_t* col_of, const int32_t* color, const int32_t* gm_of_row,
+                            int32_t* mrow, double* mval, float* mval32, int32_t* flag)
+{
+    GRID_STRIDE(q, M)
+    {
+        uint32_t pp = order[q];
+        int32_t i = crow[pp];
+        mrow[q] = gm_of_row[i];
+        mval[q] = cval[pp];
+        if (mval32) mval32[q] = (float)cval[pp];
+        bool start = q == 0;
+        if (!start) {
+            uint32_t pr = order[q - 1];
+            start = col_of[pr] != col_of[pp] || color[crow[pr]] != color[i];
+        }
+        flag[q] = start ? 1 : 0;
+    }
+}
+
+__global__ void mirror_segments(int64_t M, const uint32_t* order, const int32_t* crow, const int32_t* col_of,
+                                const int32_t* color, const int32_t* flag, const int64_t* fscan,
+                                int64_t* seg_ptr, int32_t* seg_col, int64_t* gseg_ptr)
+{
+    GRID_STRIDE(q, M)
+    {
+        if (!flag[q]) continue;
+        int64_t sg = fscan[q];
+        uint32_t pp = order[q];
+        seg_ptr[sg] = q;
+        seg_col[sg] = col_of[pp];
+        int32_t g = color[crow[pp]];
+        if (q == 0 || color[crow[order[q - 1]]] != g) gseg_ptr[g] = sg;
+    }
+}
+
+}  // namespace
+
+void validate_csr(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                  int64_t nnz, int* d_bad, cudaStream_t st)
+{
+    OBK_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+    validate_rows<<<grid_for(m), kBlock, 0, st>>>(m, n, rp, ci, v, nnz, d_bad);
+    OBK_CHECK_LAUNCH();
+}
+
+int64_t half_bandwidth(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, cudaStream_t st)
+{
+    (void)nnz;
+    DBuf<unsigned long long> bw(1, st);
+    OBK_CUDA(cudaMemsetAsync(bw.p, 0, sizeof(unsigned long long), st));
+    bandwidth_kernel<<<grid_for(N), kBlock, 0, st>>>(N, rp, ci, bw.p);
+    OBK_CHECK_LAUNCH();
+    return (int64_t)read_scalar(bw.p, st);
+}
+
+void permute_csr(int64_t N, const int64_t* rp, const int32_t* ci, const double* v, int64_t nnz,
+                 const int32_t* perm, int32_t* iperm, int64_t* rp_t, int32_t* ci_t, double* v_t,
+                 cudaStream_t st)
+{
+    inverse_perm<<<grid_for(N), kBlock, 0, st>>>(N, perm, iperm);
+    OBK_CHECK_LAUNCH();
+    DBuf<int64_t> len(N, st);
+    permuted_lengths<<<grid_for(N), kBlock, 0, st>>>(N, rp, perm, len.p);
+    OBK_CHECK_LAUNCH();
+    exclusive_scan_i64(len.p, rp_t, N, st);
+    if (nnz == 0) return;
+    DBuf<uint32_t> keys(nnz, st), src(nnz, st);
+    permute_gather<<<grid_for(N * 32), kBlock, 0, st>>>(N, rp, ci, perm, iperm, rp_t, keys.p, src.p);
+    OBK_CHECK_LAUNCH();
+    segmented_sort_u32(rp_t, N, keys.p, src.p, st);
+    permute_finish<<<grid_for(nnz), kBlock, 0, st>>>(nnz, keys.p, src.p, v, ci_t, v_t);
+    OBK_CHECK_LAUNCH();
+}
+
+void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* v, int64_t nnz,
+                 double thr, long long spin_limit, int* d_err, SweepLayout& L, bool want_fp32,
+                 cudaStream_t st)
+{
+    DevInfo di = dev_info();
+    L.N = N;
+    L.nnz = nnz;
+    // 1. exact row norms
+    L.nsq.alloc(N, st);
+    DBuf<double> s(N, st);
+    row_norms_exact<<<grid_for(N), kBlock, 0, st>>>(N, rp, v, L.nsq.p, s.p);
+    OBK_CHECK_LAUNCH();
+
+    // 2. transpose (rows ascending inside each column)
+    DBuf<int32_t> row_of(nnz, st);
+    DBuf<int64_t> cptr(N + 1, st), ccnt(N + 1, st), pos_of(nnz, st);
+    DBuf<int32_t> crow(nnz, st);
+    DBuf<double> cval(nnz, st);
+    OBK_CUDA(cudaMemsetAsync(ccnt.p, 0, (N + 1) * sizeof(int64_t), st));
+    if (nnz) {
+        expand_rows_k<<<grid_for(N), kBlock, 0, st>>>(rp, N, row_of.p);
+        OBK_CHECK_LAUNCH();
+        DBuf<uint64_t> keys(nnz, st);
+        DBuf<uint32_t> order(nnz, st);
+        col_key_kernel<<<grid_for(nnz), kBlock, 0, st>>>(nnz, ci, keys.p, order.p);
+        OBK_CHECK_LAUNCH();
+        radix_sort_pairs(keys.p, order.p, nnz, bits_for((uint64_t)(N - 1)), st);
+        count_cols_k<<<grid_for(nnz), kBlock, 0, st>>>(nnz, ci, ccnt.p);
+        OBK_CHECK_LAUNCH();
+        csc_fill<<<grid_for(nnz), kBlock, 0, st>>>(nnz, order.p, row_of.p, v, crow.p, cval.p, pos_of.p);
+        OBK_CHECK_LAUNCH();
+    }
+    exclusive_scan_i64(ccnt.p, cptr.p, N, st);
+
+    // 3. pair cosines -> lower conflict lists
+    DBuf<int64_t> ub(N, st), bigsz(N, st), bigoff(N + 1, st);
+    pair_upper_bound<<<grid_for(N), kBlock, 0, st>>>(N, rp, ci, cptr.p, pos_of.p, ub.p);
+    OBK_CHECK_LAUNCH();
+    big_table_sizes<<<grid_for(N), kBlock, 0, st>>>(N, ub.p, kPairCap, bigsz.p);
+    OBK_CHECK_LAUNCH();
+    exclusive_scan_i64(bigsz.p, bigoff.p, N, st);
+    int64_t big_total = read_scalar(bigoff.p + N, st);
+    DBuf<int32_t> big_key(big_total, st);
+    DBuf<double> big_val(big_total, st);
+    DBuf<int32_t> conf_cnt(N, st);
+    DBuf<int64_t> conf_off(N, st);
+    DBuf<unsigned long long> counters(2, st);
+    int64_t pool_cap = 8 * N + 1024;
+    DBuf<int32_t> pool;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        pool.alloc(pool_cap, st);
+        OBK_CUDA(cudaMemsetAsync(counters.p, 0, 2 * sizeof(unsigned long long), st));
+        PairParams pp{N, rp, ci, v, cptr.p, crow.p, cval.p, pos_of.p, L.nsq.p, s.p, thr, ub.p,
+                      bigoff.p, big_key.p, big_val.p, conf_cnt.p, conf_off.p, pool.p, pool_cap,
+                      counters.p, counters.p + 1, d_err};
+        int blocks = (int)std::min<int64_t>(ceil_div(N, kPairWarps), (int64_t)di.sms * 16);
+        pair_conflicts<<<blocks, kPairWarps * 32, 0, st>>>(pp);
+        OBK_CHECK_LAUNCH();
+        if (read_scalar(d_err, st) != 0) throw Error{-5, "internal error: pair table overflow"};
+        unsigned long long used = read_scalar(counters.p, st);
+        L.n_conflicts = (int64_t)read_scalar(counters.p + 1, st);
+        if ((int64_t)used <= pool_cap) break;
+        pool_cap = (int64_t)used + 1024;
+    }
+    big_key.release();
+    big_val.release();
+
+    // 4. greedy first-fit colouring
+    L.group_of.alloc(N, st);
+    OBK_CUDA(cudaMemsetAsync(L.group_of.p, 0x80, N * sizeof(int32_t), st));  // every entry = kUnset
+    ColorParams cp{N, L.nsq.p, conf_cnt.p, conf_off.p, pool.p, L.group_of.p, d_err, spin_limit};
+    int cgrid = coop_grid((const void*)greedy_color, kBlock, 0, ceil_div(N, kBlock));
+    void* args[] = {&cp};
+    OBK_COOP_LAUNCH(greedy_color, cgrid, kBlock, args, st);
+    if (read_scalar(d_err, st) != 0) throw Error{-4, "bounded wait expired in greedy grouping"};
+    DBuf<int> gmax(1, st);
+    OBK_CUDA(cudaMemsetAsync(gmax.p, 0xff, sizeof(int), st));
+    max_color<<<grid_for(N), kBlock, 0, st>>>(N, L.group_of.p, gmax.p);
+    OBK_CHECK_LAUNCH();
+    int G = read_scalar(gmax.p, st) + 1;
+    L.G = G;
+    pool.release();
+    conf_cnt.release();
+    conf_off.release();
+
+    // 5. group-major rows
+    DBuf<uint64_t> gk(N, st);
+    DBuf<uint32_t> gorder(N, st);
+    color_keys<<<grid_for(N), kBlock, 0, st>>>(N, L.group_of.p, G, gk.p, gorder.p);
+    OBK_CHECK_LAUNCH();
+    radix_sort_pairs(gk.p, gorder.p, N, bits_for((uint64_t)G), st);
+    gk.release();
+    DBuf<int64_t> gcnt(G + 1, st);
+    OBK_CUDA(cudaMemsetAsync(gcnt.p, 0, (G + 1) * sizeof(int64_t), st));
+    group_hist<<<grid_for(N), kBlock, 0, st>>>(N, L.group_of.p, gcnt.p);
+    OBK_CHECK_LAUNCH();
+    L.gptr.alloc(G + 1, st);
+    exclusive_scan_i64(gcnt.p, L.gptr.p, G, st);
+    L.h_gptr.resize(G + 1);
+    OBK_CUDA(cudaMemcpyAsync(L.h_gptr.data(), L.gptr.p, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    OBK_CUDA(cudaStreamSynchronize(st));
+    int64_t Ngm = L.h_gptr[G];
+    L.Ngm = Ngm;
+    DBuf<int32_t> gm_of_row(N, st);
+    OBK_CUDA(cudaMemsetAsync(gm_of_row.p, 0xff, N * sizeof(int32_t), st));
+    L.grp_row.alloc(Ngm, st);
+    L.grp_inv.alloc(Ngm, st);
+    if (want_fp32) L.grp_inv32.alloc(Ngm, st);
+    DBuf<int64_t> glen(Ngm, st);
+    gm_rows<<<grid_for(Ngm), kBlock, 0, st>>>(Ngm, gorder.p, rp, L.nsq.p, L.grp_row.p, gm_of_row.p, glen.p,
+                                              L.grp_inv.p, want_fp32 ? L.grp_inv32.p : nullptr);
+    OBK_CHECK_LAUNCH();
+    L.grp_rp.alloc(Ngm + 1, st);
+    exclusive_scan_i64(glen.p, L.grp_rp.p, Ngm, st);
+    int64_t nnz_gm = read_scalar(L.grp_rp.p + Ngm, st);
+    L.nnz_gm = nnz_gm;
+    L.grp_ci.alloc(nnz_gm, st);
+    L.grp_v.alloc(nnz_gm, st);
+    if (want_fp32) L.grp_v32.alloc(nnz_gm, st);
+    gm_copy<<<grid_for(Ngm * 32), kBlock, 0, st>>>(Ngm, L.grp_row.p, rp, ci, v, L.grp_rp.p, L.grp_ci.p,
+                                                   L.grp_v.p, want_fp32 ? L.grp_v32.p : nullptr);
+    OBK_CHECK_LAUNCH();
+
+    // 6. column mirror: CSC entries stably partitioned by the group of their row
+    DBuf<uint64_t> mk(nnz, st);
+    DBuf<uint32_t> morder(nnz, st);
+    DBuf<int32_t> col_of(nnz, st);
+    if (nnz) {
+        csc_color_keys<<<grid_for(nnz), kBlock, 0, st>>>(nnz, crow.p, L.group_of.p, G, mk.p, morder.p);
+        OBK_CHECK_LAUNCH();
+        radix_sort_pairs(mk.p, morder.p, nnz, bits_for((uint64_t)G), st);
+        expand_cols<<<grid_for(N), kBlock, 0, st>>>(N, cptr.p, col_of.p);
+        OBK_CHECK_LAUNCH();
+    }
+    mk.release();
+    // grouped entries come first (zero rows were keyed G)
+    int64_t M = nnz_gm;
+    L.mir_row.alloc(M, st);
+    L.mir_val.alloc(M, st);
+    if (want_fp32) L.mir_val32.alloc(M, st);
+    DBuf<int32_t> flag(M, st);
+    DBuf<int64_t> fscan(M + 1, st);
+    if (M) {
+        mirror_fill<<<grid_for(M), kBlock, 0, st>>>(M, morder.p, crow.p, cval.p, col_of.p, L.group_of.p,
+                                                   gm_of_row.p, L.mir_row.p, L.mir_val.p,
+                                                   want_fp32 ? L.mir_val32.p : nullptr, flag.p);
+        OBK_CHECK_LAUNCH();
+    }
+    exclusive_scan_i32_to_i64(flag.p, fscan.p, M, st);
+    int64_t nseg = read_scalar(fscan.p + M, st);
+    L.nseg = nseg;
+    L.seg_ptr.alloc(nseg + 1, st);
+    L.seg_col.alloc(nseg, st);
+    L.gseg_ptr.alloc(G + 1, st);
+    OBK_CUDA(cudaMemcpyAsync(L.seg_ptr.p + nseg, &M, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    OBK_CUDA(cudaMemcpyAsync(L.gseg_ptr.p + G, &nseg, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    if (M) {
+        mirror_segments<<<grid_for(M), kBlock, 0, st>>>(M, morder.p, crow.p, col_of.p, L.group_of.p, flag.p,
+                                                       fscan.p, L.seg_ptr.p, L.seg_col.p, L.gseg_ptr.p);
+        OBK_CHECK_LAUNCH();
+    }
+    L.h_gseg_ptr.resize(G + 1);
+    OBK_CUDA(cudaMemcpyAsync(L.h_gseg_ptr.data(), L.gseg_ptr.p, (G + 1) * sizeof(int64_t),
+                             cudaMemcpyDeviceToHost, st));
+    OBK_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace obk

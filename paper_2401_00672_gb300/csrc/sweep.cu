@@ -1,0 +1,400 @@
+// sweep.cu -- the orthogonal-group Kaczmarz sweep (paper Eq. 1.2 / Eq. 1.3 /
+// Eq. 3.3, Algorithm 4), the residual check and the FP32-sweep / FP64
+// refinement form, in one persistent cooperative kernel per solve.
+//
+// One group step (rows of group g are mutually near-orthogonal):
+//   phase 1  y_k = (f_k - A_k . x) / ||A_k||^2 for every row k of the group,
+//            from the x at the start of the group.  A sub-warp of SUB lanes
+//            per row, coalesced loads of the group-major CSR, warp-shuffle
+//            reduction.
+//   phase 2  x_c += sum_k A_kc y_k over the group's rows (ascending), one
+//            thread per (group, column) segment of the column mirror: a
+//            deterministic gather, no floating-point atomics.
+// A grid barrier separates the phases.  For an exactly orthogonal group the
+// update equals x + A_tau^+ (f_tau - A_tau x) (Eq. 1.3).
+//
+// Residual check: ||f - A x|| / ||f|| with a fixed-order two-level reduction
+// (deterministic for a given grid).  Block 0 takes the stop decision and the
+// other blocks read it after a barrier.
+//
+// Precision form: outer FP64 loop r = f - A x, beta = ||r||; FP32 sweeps on
+// A d = r / beta from d = 0 (FP32 values, x and y; row norms and groups from
+// FP64); then x += beta * d in FP64.
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace obk {
+namespace {
+
+constexpr int kBlock = 256;
+
+struct SweepParams {
+    int64_t N, Ngm, G;
+    const int64_t* grp_rp;
+    const int32_t* grp_ci;
+    const double* grp_v;
+    const float* grp_v32;
+    const double* grp_inv;
+    const float* grp_inv32;
+    const int64_t* gptr;
+    const int64_t* gseg_ptr;
+    const int64_t* seg_ptr;
+    const int32_t* seg_col;
+    const int32_t* mir_row;
+    const double* mir_val;
+    const float* mir_val32;
+    const double* f;  // group-major
+    double* x;        // N
+    double* y;        // Ngm
+    double* r64;      // Ngm (precision form)
+    float* b32;       // Ngm
+    float* y32;       // Ngm
+    float* d32;       // N
+    double fnorm, zero_f2, tol, stagnation;
+    int64_t maxit;
+    int check_every, precision, inner_sweeps, max_outer;
+    double* partial;  // gridDim.x
+    double* ctrl;     // [0] rr, [1] beta, [2..11] history
+    int64_t* out;     // [0] sweeps, [1] status, [2] outer, [3] stop, [4] sweep ns, [5] inner
+    GridBarrier gb;
+};
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <int SUB>
+__device__ __forceinline__ unsigned sub_mask()
+{
+    if constexpr (SUB == 32) {
+        return 0xffffffffu;
+    } else {
+        int lane = threadIdx.x & 31;
+        return ((1u << SUB) - 1u) << (lane & ~(SUB - 1));
+    }
+}
+
+template <int SUB, class T>
+__device__ __forceinline__ T sub_reduce(T v)
+{
+    unsigned m = sub_mask<SUB>();
+#pragma unroll
+    for (int o = SUB / 2; o > 0; o >>= 1) v += __shfl_xor_sync(m, v, o);
+    return v;
+}
+
+// phase 1: y_k = (rhs_k - A_k . xv) * inv_k for group-major rows [r0, r1)
+template <int SUB, class T, class TR>
+__device__ __forceinline__ void phase1(const SweepParams& p, int64_t r0, int64_t r1, const T* vals,
+                                       const T* inv, const TR* rhs, const T* xv, T* y)
+{
+    int64_t sw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / SUB;
+    int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / SUB;
+    int sub = threadIdx.x & (SUB - 1);
+    for (int64_t k = r0 + sw; k < r1; k += nsw) {
+        int64_t b = p.grp_rp[k], e = p.grp_rp[k + 1];
+        T acc = 0;
+        for (int64_t q = b + sub; q < e; q += SUB) acc = fma(vals[q], xv[p.grp_ci[q]], acc);
+        acc = sub_reduce<SUB>(acc);
+        if (sub == 0) y[k] = ((T)rhs[k] - acc) * inv[k];
+    }
+}
+
+// phase 2: xv_c += sum over the segment's rows of A_kc y_k, segments [s0, s1)
+template <class T>
+__device__ __forceinline__ void phase2(const SweepParams& p, int64_t s0, int64_t s1, const T* mval,
+                                       const T* y, T* xv)
+{
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = s0 + tid; t < s1; t += nth) {
+        int64_t b = p.seg_ptr[t], e = p.seg_ptr[t + 1];
+        T acc = 0;
+        for (int64_t q = b; q < e; ++q) acc = fma(mval[q], y[p.mir_row[q]], acc);
+        xv[p.seg_col[t]] += acc;
+    }
+}
+
+// deterministic block sum (fixed shuffle tree, warps in order); result in thread 0
+__device__ double block_sum(double v)
+{
+    __shared__ double ws[kBlock / 32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) ws[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += ws[k];
+    __syncthreads();
+    return s;
+}
+
+// sum of squared residuals (FP64) of all group-major rows into partial[block];
+// with store_r the residuals are kept in r64
+template <int SUB>
+__device__ void residual_partial(const SweepParams& p, bool store_r)
+{
+    int64_t sw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / SUB;
+    int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / SUB;
+    int sub = threadIdx.x & (SUB - 1);
+    double local = 0.0;
+    for (int64_t k = sw; k < p.Ngm; k += nsw) {
+        int64_t b = p.grp_rp[k], e = p.grp_rp[k + 1];
+        double acc = 0.0;
+        for (int64_t q = b + sub; q < e; q += SUB) acc = fma(p.grp_v[q], p.x[p.grp_ci[q]], acc);
+        acc = sub_reduce<SUB>(acc);
+        if (sub == 0) {
+            double r = p.f[k] - acc;
+            if (store_r) p.r64[k] = r;
+            local = fma(r, r, local);
+        }
+    }
+    double s = block_sum(local);
+    if (threadIdx.x == 0) p.partial[blockIdx.x] = s;
+}
+
+// block 0 thread 0: total of the partials in block order
+__device__ double total_partials(const SweepParams& p)
+{
+    double s = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) s += p.partial[b];
+    return s + p.zero_f2;
+}
+
+template <int SUB>
+__global__ void __launch_bounds__(kBlock) obk_solve_kernel(SweepParams p)
+{
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    volatile int64_t* vout = p.out;
+    // initial residual
+    residual_partial<SUB>(p, p.precision == 1);
+    if (!grid_sync(p.gb)) return;
+    if (lead) {
+        double tot = total_partials(p);
+        double rr = p.fnorm > 0.0 ? sqrt(tot) / p.fnorm : sqrt(tot);
+        p.ctrl[0] = rr;
+        p.ctrl[1] = sqrt(tot);
+        vout[0] = 0;
+        vout[2] = 0;
+        vout[4] = 0;
+        if (rr <= p.tol) { vout[1] = 0; vout[3] = 1; }
+        else { vout[1] = 1; vout[3] = 0; }
+    }
+    if (!grid_sync(p.gb)) return;
+
+    if (p.precision == 0) {
+        int64_t s = 0;
+        int64_t nchk = 0;
+        while (vout[3] == 0) {
+            unsigned long long t0 = lead ? globaltimer() : 0;
+            for (int64_t g = 0; g < p.G; ++g) {
+                phase1<SUB, double, double>(p, p.gptr[g], p.gptr[g + 1], p.grp_v, p.grp_inv, p.f, p.x, p.y);
+                if (!grid_sync(p.gb)) return;
+                phase2<double>(p, p.gseg_ptr[g], p.gseg_ptr[g + 1], p.mir_val, p.y, p.x);
+                if (!grid_sync(p.gb)) return;
+            }
+            ++s;
+            if (lead) { vout[4] += (int64_t)(globaltimer() - t0); vout[0] = s; }
+            bool check = (s % p.check_every) == 0 || s >= p.maxit;
+            if (check) {
+                residual_partial<SUB>(p, false);
+                if (!grid_sync(p.gb)) return;
+                if (lead) {
+                    double tot = total_partials(p);
+                    double rr = p.fnorm > 0.0 ? sqrt(tot) / p.fnorm : sqrt(tot);
+                    p.ctrl[0] = rr;
+                    int stop = 0;
+                    if (rr <= p.tol) { vout[1] = 0; stop = 1; }
+                    else if (s >= p.maxit) stop = 1;
+                    else if (p.stagnation > 0.0) {
+                        double* hist = p.ctrl + 2;
+                        if (nchk >= 10 && fabs(rr - hist[nchk % 10]) < p.stagnation) stop = 1;
+                        hist[nchk % 10] = rr;
+                    }
+                    ++nchk;
+                    vout[3] = stop;
+                }
+                if (!grid_sync(p.gb)) return;
+            }
+        }
+        return;
+    }
+
+    // precision form: FP32 inner sweeps inside FP64 refinement
+    int64_t sweeps = 0;
+    int64_t outer = 0;
+    int s_in = p.inner_sweeps > 0 ? p.inner_sweeps : 8;
+    double rr_prev = p.ctrl[0];
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    while (vout[3] == 0) {
+        double beta = *(volatile double*)(p.ctrl + 1);
+        for (int64_t k = tid; k < p.Ngm; k += nth) p.b32[k] = (float)(p.r64[k] / beta);
+        for (int64_t c = tid; c < p.N; c += nth) p.d32[c] = 0.0f;
+        if (!grid_sync(p.gb)) return;
+        unsigned long long t0 = lead ? globaltimer() : 0;
+        int nin = s_in;
+        if (sweeps + nin > p.maxit) nin = (int)(p.maxit - sweeps);
+        for (int it = 0; it < nin; ++it) {
+            for (int64_t g = 0; g < p.G; ++g) {
+                phase1<SUB, float, float>(p, p.gptr[g], p.gptr[g + 1], p.grp_v32, p.grp_inv32, p.b32, p.d32,
+                                          p.y32);
+                if (!grid_sync(p.gb)) return;
+                phase2<float>(p, p.gseg_ptr[g], p.gseg_ptr[g + 1], p.mir_val32, p.y32, p.d32);
+                if (!grid_sync(p.gb)) return;
+            }
+        }
+        sweeps += nin;
+        if (lead) { vout[4] += (int64_t)(globaltimer() - t0); vout[0] = sweeps; }
+        for (int64_t c = tid; c < p.N; c += nth) p.x[c] = fma(beta, (double)p.d32[c], p.x[c]);
+        ++outer;
+        if (!grid_sync(p.gb)) return;
+        residual_partial<SUB>(p, true);
+        if (!grid_sync(p.gb)) return;
+        if (lead) {
+            double tot = total_partials(p);
+            double rr = p.fnorm > 0.0 ? sqrt(tot) / p.fnorm : sqrt(tot);
+            p.ctrl[0] = rr;
+            p.ctrl[1] = sqrt(tot);
+            vout[2] = outer;
+            int stop = 0;
+            if (rr <= p.tol) { vout[1] = 0; stop = 1; }
+            else if (sweeps >= p.maxit || outer >= p.max_outer) stop = 1;
+            vout[3] = stop;
+            // inner sweep count for the next step: aim for the reduction that
+            // FP32 can deliver (about 1e-6) or what tol still needs
+            if (p.inner_sweeps <= 0 && rr > 0.0 && rr_prev > 0.0 && rr < rr_prev) {
+                double rate = pow(rr / rr_prev, 1.0 / (double)nin);
+                double target = fmax(1e-6, 0.5 * p.tol / rr);
+                if (rate < 1.0 && rate > 0.0) {
+                    double want = ceil(log(target) / log(rate));
+                    int w = (int)fmin(fmax(want, 2.0), 64.0);
+                    vout[5] = w;
+                } else {
+                    vout[5] = 64;
+                }
+            } else {
+                vout[5] = s_in;
+            }
+            rr_prev = rr;
+        }
+        if (!grid_sync(p.gb)) return;
+        s_in = (int)vout[5];
+        if (p.inner_sweeps > 0) s_in = p.inner_sweeps;
+    }
+}
+
+// ---- launch ---------------------------------------------------------------------
+
+template <int SUB>
+void launch_solve(SweepParams& p, cudaStream_t st)
+{
+    DevInfo di = dev_info();
+    const void* k = (const void*)obk_solve_kernel<SUB>;
+    int grid = coop_grid(k, kBlock, 0, (int64_t)di.sms * 8);
+    DBuf<double> partial(grid, st);
+    p.partial = partial.p;
+    void* args[] = {&p};
+    OBK_COOP_LAUNCH(k, grid, kBlock, args, st);
+    OBK_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace
+
+int choose_sub(double avg_row)
+{
+    if (avg_row <= 6) return 4;
+    if (avg_row <= 12) return 8;
+    if (avg_row <= 40) return 16;
+    return 32;
+}
+
+SolveResult run_solve(const SweepLayout& L, const double* f_gm, double fnorm2, double zero_f2,
+                      double* x, const SolveArgs& a, int* d_err, cudaStream_t st)
+{
+    SolveResult res;
+    DBuf<double> y(std::max<int64_t>(L.Ngm, 1), st), ctrl(16, st);
+    DBuf<int64_t> out(8, st);
+    DBuf<unsigned> bar(2, st);
+    DBuf<double> r64;
+    DBuf<float> b32, y32, d32;
+    if (a.precision == 1) {
+        r64.alloc(std::max<int64_t>(L.Ngm, 1), st);
+        b32.alloc(std::max<int64_t>(L.Ngm, 1), st);
+        y32.alloc(std::max<int64_t>(L.Ngm, 1), st);
+        d32.alloc(std::max<int64_t>(L.N, 1), st);
+        if (!L.grp_v32.p && L.nnz_gm > 0) throw Error{-1, "precision form needs the FP32 layout"};
+    }
+    OBK_CUDA(cudaMemsetAsync(ctrl.p, 0, 16 * sizeof(double), st));
+    OBK_CUDA(cudaMemsetAsync(out.p, 0, 8 * sizeof(int64_t), st));
+    OBK_CUDA(cudaMemsetAsync(bar.p, 0, 2 * sizeof(unsigned), st));
+    OBK_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+    SweepParams p{};
+    p.N = L.N;
+    p.Ngm = L.Ngm;
+    p.G = L.G;
+    p.grp_rp = L.grp_rp.p;
+    p.grp_ci = L.grp_ci.p;
+    p.grp_v = L.grp_v.p;
+    p.grp_v32 = L.grp_v32.p;
+    p.grp_inv = L.grp_inv.p;
+    p.grp_inv32 = L.grp_inv32.p;
+    p.gptr = L.gptr.p;
+    p.gseg_ptr = L.gseg_ptr.p;
+    p.seg_ptr = L.seg_ptr.p;
+    p.seg_col = L.seg_col.p;
+    p.mir_row = L.mir_row.p;
+    p.mir_val = L.mir_val.p;
+    p.mir_val32 = L.mir_val32.p;
+    p.f = f_gm;
+    p.x = x;
+    p.y = y.p;
+    p.r64 = r64.p;
+    p.b32 = b32.p;
+    p.y32 = y32.p;
+    p.d32 = d32.p;
+    p.fnorm = sqrt(fnorm2);
+    p.zero_f2 = zero_f2;
+    p.tol = a.tol;
+    p.stagnation = a.stagnation;
+    p.maxit = a.maxit;
+    p.check_every = a.check_every > 0 ? a.check_every : 1;
+    p.precision = a.precision;
+    p.inner_sweeps = a.inner_sweeps;
+    p.max_outer = a.max_outer > 0 ? a.max_outer : 100;
+    p.ctrl = ctrl.p;
+    p.out = out.p;
+    p.gb = GridBarrier{bar.p, d_err, a.spin_limit};
+    int sub = a.sub;
+    if (sub == 0) sub = choose_sub(L.Ngm ? (double)L.nnz_gm / (double)L.Ngm : 1.0);
+    switch (sub) {
+        case 4: launch_solve<4>(p, st); break;
+        case 8: launch_solve<8>(p, st); break;
+        case 16: launch_solve<16>(p, st); break;
+        default: launch_solve<32>(p, st); break;
+    }
+    int err = read_scalar(d_err, st);
+    if (err != 0) throw Error{-4, "bounded wait expired in the sweep kernel"};
+    int64_t h_out[8];
+    double h_ctrl[2];
+    OBK_CUDA(cudaMemcpyAsync(h_out, out.p, sizeof(h_out), cudaMemcpyDeviceToHost, st));
+    OBK_CUDA(cudaMemcpyAsync(h_ctrl, ctrl.p, sizeof(h_ctrl), cudaMemcpyDeviceToHost, st));
+    OBK_CUDA(cudaStreamSynchronize(st));
+    res.sweeps = h_out[0];
+    res.status = (int)h_out[1];
+    res.outer = h_out[2];
+    res.sweep_ms = (double)h_out[4] * 1e-6;
+    res.rel_res = h_ctrl[0];
+    return res;
+}
+
+}  // namespace obk

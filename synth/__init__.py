@@ -72,7 +72,7 @@ def csr_from_coo(m: int, n: int, rows: np.ndarray, cols: np.ndarray, vals: np.nd
     """Build a CSR with sorted, unique columns from COO triplets (no duplicates allowed)."""
     rows = np.asarray(rows, dtype=np.int64)
     cols = np.asarray(cols, dtype=np.int64)
-    order = np.lexsort((cols, rows))
+    order = np.argsort(rows * np.int64(max(n, 1)) + cols, kind="stable")
     rows, cols, vals = rows[order], cols[order], np.asarray(vals, dtype=np.float64)[order]
     if rows.size > 1:
         dup = (rows[1:] == rows[:-1]) & (cols[1:] == cols[:-1])
@@ -146,7 +146,8 @@ def knn_dominant(n: int, k: int = 12, seed: int = 1001, diag_factor: float = 1.2
     i = np.repeat(np.arange(n, dtype=np.int64), k)
     j = nb.ravel().astype(np.int64)
     key = np.concatenate([i * n + j, j * n + i])
-    key = np.unique(key)
+    key.sort()
+    key = key[np.concatenate(([True], key[1:] != key[:-1]))]
     r, c = key // n, key % n
     offv = rng.standard_normal(key.size)
     diag = diag_factor * np.bincount(r, weights=np.abs(offv), minlength=n)
@@ -159,15 +160,18 @@ def knn_dominant(n: int, k: int = 12, seed: int = 1001, diag_factor: float = 1.2
     return System(A, xstar, A.matvec(xstar), f"knn_dominant(n={n},k={k},seed={seed})")
 
 
-def rect_random(m: int, n: int, k: int = 10, seed: int = 1002, noise: float = 0.0) -> System:
-    """m x n with k distinct uniform random columns per row, N(0,1) values.  Redrawn
-    (next sub-seed) until every column holds a nonzero, which makes full column rank
-    near-certain for m >= 2n.  f = A x* (+ noise * N(0,1) for the inconsistent
-    variant)."""
+def rect_random(m: int, n: int, k: int = 10, seed: int = 1002, noise: float = 0.0,
+                full_columns: bool | None = None) -> System:
+    """m x n with k distinct uniform random columns per row, N(0,1) values.  For
+    m >= n (or full_columns=True) the pattern is redrawn until every column holds a
+    nonzero, which makes full column rank near-certain for m >= 2n.  f = A x*
+    (+ noise * N(0,1) for the inconsistent variant)."""
     rng = np.random.Generator(np.random.PCG64(seed))
+    if full_columns is None:
+        full_columns = m >= n
     for _ in range(64):
         cols = _distinct_columns(rng, m, n, k, skip_diag=False)
-        if np.bincount(cols.ravel(), minlength=n).min() > 0:
+        if not full_columns or np.bincount(cols.ravel(), minlength=n).min() > 0:
             break
     else:  # pragma: no cover - astronomically unlikely for the sizes used
         raise RuntimeError("could not draw a matrix without empty columns")

@@ -1,0 +1,289 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Permutation, row norms and groups must match bit for bit; the FP64 solve must
+match x to ||x_gpu - x_oracle|| / ||x_oracle|| <= 1e-9 after the same number
+of sweeps, and stop within one sweep of the oracle.  Cases span several
+thread blocks and ragged tails, plus the degenerate inputs of the method.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle_helpers import graph_matrix
+
+pytestmark = pytest.mark.gpu
+
+XTOL = 1e-9  # FP64 parity bound on the relative 2-norm difference of x
+
+
+@pytest.fixture(scope="module")
+def obk():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2401_00672_gb300 as m
+
+    return m
+
+
+def _diag(n=777):
+    rng = np.random.default_rng(3)
+    d = rng.uniform(0.5, 2.0, n)
+    A = synth.csr_from_coo(n, n, np.arange(n), np.arange(n), d)
+    xs = rng.standard_normal(n)
+    return synth.System(A, xs, d * xs, "diag")
+
+
+def _components():
+    # two random components, isolated vertices, and a path; diagonal everywhere
+    rng = np.random.default_rng(11)
+    N = 900
+    edges = set()
+    for lo, hi in ((0, 400), (400, 700)):
+        for _ in range(3 * (hi - lo)):
+            a, b = rng.integers(lo, hi, 2)
+            if a != b:
+                edges.add((int(min(a, b)), int(max(a, b))))
+    for k in range(800, 899):
+        edges.add((k, k + 1))
+    lab = rng.permutation(N)
+    A = graph_matrix(N, [(int(lab[a]), int(lab[b])) for a, b in sorted(edges)])
+    vals = rng.standard_normal(A.nnz)
+    rows = np.repeat(np.arange(N), np.diff(A.row_ptr))
+    vals[rows == A.col_idx] = 0.0
+    offs = np.bincount(rows, weights=np.abs(vals), minlength=N)
+    vals[rows == A.col_idx] = 1.0 + offs
+    A.val = vals
+    xs = rng.standard_normal(N)
+    return synth.System(A, xs, A.matvec(xs), "components")
+
+
+def _zero_rows():
+    s = synth.random_dominant(500, 5, seed=77)
+    A = s.A
+    # blank out some rows entirely (explicit zeros) -> they take no part
+    v = A.val.copy()
+    for i in (0, 17, 250, 499):
+        v[A.row_ptr[i]:A.row_ptr[i + 1]] = 0.0
+    A.val = v
+    f = A.matvec(s.xstar)
+    return synth.System(A, s.xstar, f, "zero_rows")
+
+
+CASES = {
+    "random_dominant_2000": lambda: synth.random_dominant(2000, 7, seed=1000),
+    "knn_30000": lambda: synth.knn_dominant(30000, 12, seed=1001),
+    "rect_over_3000x1000": lambda: synth.rect_random(3000, 1000, 10, seed=1002),
+    "rect_under_400x1000": lambda: synth.rect_random(400, 1000, 8, seed=7, full_columns=False),
+    "diag": _diag,
+    "components": _components,
+    "zero_rows": _zero_rows,
+    "tiny_3x3": lambda: synth.random_dominant(3, 1, seed=5),
+}
+
+_cache = {}
+
+
+def _case(name):
+    if name not in _cache:
+        s = CASES[name]()
+        A = s.A
+        su = oracle.setup(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1)
+        _cache[name] = (s, su)
+    return _cache[name]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_setup_bit_exact(obk, name):
+    s, su = _case(name)
+    A = s.A
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
+        assert h.N == su.N and h.G == su.G
+        assert np.array_equal(h.perm(), su.perm)
+        assert np.array_equal(h.row_norms().view(np.uint64), su.nsq.view(np.uint64))
+        assert np.array_equal(h.groups(), su.group_of)
+        info = h.info()
+        assert info.bandwidth_after == su.info.bandwidth_after
+        assert info.bandwidth_before == su.info.bandwidth_before
+        assert info.n_conflicts == su.info.n_conflicts
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_solve_parity(obk, name):
+    s, su = _case(name)
+    A = s.A
+    tol = 1e-8
+    st_o, x_o, io = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1, tol=tol, maxit=20000)
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
+        st, x, info = h.solve(s.f, None, tol=tol, maxit=20000)
+        assert st == st_o
+        assert abs(info.sweeps - io.sweeps) <= 1
+        # same number of sweeps, no early stop: x must agree to XTOL
+        st2, x2, info2 = h.solve(s.f, None, tol=1e-300, maxit=io.sweeps)
+        assert info2.sweeps == io.sweeps
+    nrm = np.linalg.norm(x_o)
+    err = np.linalg.norm(x2 - x_o) / (nrm if nrm > 0 else 1.0)
+    assert err <= XTOL, err
+    if info.sweeps == io.sweeps:
+        assert np.linalg.norm(x - x_o) / (nrm if nrm > 0 else 1.0) <= XTOL
+
+
+def test_fixed_sweeps_with_x0_and_device_buffers(obk):
+    import torch
+
+    s, su = _case("knn_30000")
+    A = s.A
+    rng = np.random.default_rng(5)
+    x0 = rng.standard_normal(A.n)
+    gptr, grows = oracle.group_lists(su.group_of, su.G)
+    x0_t = x0[su.perm]
+    xt = oracle.sweep(su.N, su.rp, su.ci, su.v, su.nsq, su.f, gptr, grows, x0_t, 3)
+    x_o = np.empty_like(xt)
+    x_o[su.perm] = xt
+    dev = torch.device("cuda")
+    with obk.Handle(torch.from_numpy(A.row_ptr).to(dev), torch.from_numpy(A.col_idx).to(dev),
+                    torch.from_numpy(A.val).to(dev), A.m, A.n, thr=0.1) as h:
+        out = torch.empty(A.n, dtype=torch.float64, device=dev)
+        st, _, info = h.solve(torch.from_numpy(s.f).to(dev), torch.from_numpy(x0).to(dev), tol=1e-300,
+                              maxit=3, out=out)
+        assert st == obk.OBK_NOT_CONVERGED and info.sweeps == 3
+        x = out.cpu().numpy()
+    assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) <= XTOL
+
+
+def test_deterministic_repeat(obk):
+    s, _ = _case("random_dominant_2000")
+    A = s.A
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
+        _, x1, _ = h.solve(s.f, tol=1e-10, maxit=500)
+        _, x2, _ = h.solve(s.f, tol=1e-10, maxit=500)
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h2:
+        _, x3, _ = h2.solve(s.f, tol=1e-10, maxit=500)
+    assert np.array_equal(x1, x2) and np.array_equal(x1, x3)
+
+
+def test_precision_form_reaches_1e10(obk):
+    s, _ = _case("knn_30000")
+    A = s.A
+    st_o, x_o, io = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1, tol=1e-10, maxit=20000)
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
+        st, x, info = h.solve(s.f, tol=1e-10, maxit=20000, opts=obk.Opts(precision=1))
+    assert st == obk.OBK_OK and info.rel_res <= 1e-10 and info.outer_iters >= 1
+    err = np.linalg.norm(x - x_o) / np.linalg.norm(x_o)
+    assert err <= 1e-8, err
+
+
+def test_overdetermined_inconsistent_stagnates(obk):
+    s = synth.rect_random(3000, 1000, 10, seed=12, noise=1e-3)
+    A = s.A
+    st_o, x_o, io = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1, tol=1e-8, maxit=5000,
+                                 stagnation=1e-12)
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
+        st, x, info = h.solve(s.f, tol=1e-8, maxit=5000, opts=obk.Opts(stagnation=1e-12))
+    assert st == st_o == obk.OBK_NOT_CONVERGED
+    assert abs(info.sweeps - io.sweeps) <= 10
+    assert abs(info.rel_res - io.rel_res) <= 1e-6 * io.rel_res
+
+
+@pytest.mark.parametrize("name", ["random_dominant_2000", "knn_30000", "rect_over_3000x1000", "zero_rows"])
+def test_residual_entry_point(obk, name):
+    import torch
+
+    s, _ = _case(name)
+    A = s.A
+    x = np.random.default_rng(2).standard_normal(A.n)
+    rr_host = obk.residual(A.row_ptr, A.col_idx, A.val, A.m, A.n, s.f, x)
+    dev = torch.device("cuda")
+    rr_dev = obk.residual(torch.from_numpy(A.row_ptr).to(dev), torch.from_numpy(A.col_idx).to(dev),
+                          torch.from_numpy(A.val).to(dev), A.m, A.n, torch.from_numpy(s.f).to(dev),
+                          torch.from_numpy(x).to(dev))
+    assert rr_host == rr_dev  # deterministic: same bits from host or device inputs
+    import scipy.sparse as sp
+
+    M = sp.csr_matrix((A.val, A.col_idx, A.row_ptr), shape=(A.m, A.n))
+    ref = np.linalg.norm(s.f - M @ x) / np.linalg.norm(s.f)
+    assert abs(rr_host - ref) <= 1e-13 * ref
+
+
+def test_invalid_inputs(obk):
+    rp = np.array([0, 2, 3], np.int64)
+    ci = np.array([1, 0, 1], np.int32)  # unsorted row 0
+    with pytest.raises(obk.ObkError) as e:
+        obk.Handle(rp, ci, np.ones(3), 2, 2)
+    assert e.value.status == obk.OBK_ERR_INVALID
+    with pytest.raises(obk.ObkError) as e:
+        obk.Handle(rp, np.array([0, 1, 1], np.int32), np.array([1.0, np.nan, 1.0]), 2, 2)
+    assert e.value.status == obk.OBK_ERR_INVALID
+    s, _ = _case("tiny_3x3")
+    A = s.A
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n) as h:
+        with pytest.raises(obk.ObkError):
+            h.solve(np.array([1.0, np.inf, 0.0]))
+        with pytest.raises(obk.ObkError):
+            h.solve(s.f, tol=0.0)
+
+
+def test_bounded_wait_times_out_and_context_survives(obk):
+    # a wait limit of a few polls cannot cover the grid barrier: the kernel must
+    # give up, report OBK_ERR_TIMEOUT, and leave the context usable
+    s, _ = _case("random_dominant_2000")
+    A = s.A
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n) as h:
+        with pytest.raises(obk.ObkError) as e:
+            h.solve(s.f, tol=1e-8, maxit=50, opts=obk.Opts(timeout_spins=1))
+        assert e.value.status == obk.OBK_ERR_TIMEOUT
+        st, x, info = h.solve(s.f, tol=1e-8, maxit=500)
+        assert st == obk.OBK_OK
+
+
+def test_request_loop_alone_equals_mixed(obk):
+    systems = [synth.random_dominant(n, 7, seed=900 + k) for k, n in enumerate((1200, 3000, 800, 5000))]
+    systems += [synth.rect_random(2 * n, n, 10, seed=950 + k) for k, n in enumerate((700, 1500))]
+    alone = []
+    for s in systems:
+        A = s.A
+        st, x, info = obk.solve(A.row_ptr, A.col_idx, A.val, A.m, A.n, s.f, tol=1e-8, maxit=5000)
+        alone.append((st, x))
+    srv = obk.Server(hbm_budget_bytes=0, max_streams=4)
+    tickets = []
+    for k, s in enumerate(systems):
+        A = s.A
+        opts = obk.Opts(precision=0)
+        tickets.append(srv.submit(A.row_ptr, A.col_idx, A.val, A.m, A.n, s.f, tol=1e-8, maxit=5000, opts=opts))
+    import time
+
+    results = {}
+    t0 = time.time()
+    while len(results) < len(tickets) and time.time() - t0 < 120:
+        for t, s in zip(tickets, systems):
+            if t in results:
+                continue
+            st, x, info = srv.poll(t, s.A.n)
+            if st != obk.OBK_PENDING:
+                results[t] = (st, x)
+        time.sleep(0.01)
+    srv.close()
+    assert len(results) == len(tickets)
+    for t, (st_a, x_a) in zip(tickets, alone):
+        st_m, x_m = results[t]
+        assert st_m == st_a
+        assert np.linalg.norm(x_m - x_a) <= XTOL * np.linalg.norm(x_a)
+
+
+@pytest.mark.slow
+def test_full_size_knn_1m_parity(obk):
+    """The kNN workload at n = 1,000,000, in the configuration the benchmark
+    times: setup bit-exact and x within 1e-9 at the oracle's stopping sweep."""
+    s = synth.knn_dominant(1_000_000, 12, seed=1001)
+    A = s.A
+    st_o, x_o, io, perm_o, gof_o = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1, tol=1e-8,
+                                                maxit=10000, return_setup=True)
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
+        assert np.array_equal(h.perm(), perm_o)
+        assert np.array_equal(h.groups(), gof_o)
+        st, x, info = h.solve(s.f, tol=1e-8, maxit=10000)
+        assert st == st_o == obk.OBK_OK and abs(info.sweeps - io.sweeps) <= 1
+        st2, x2, _ = h.solve(s.f, tol=1e-300, maxit=io.sweeps)
+    assert np.linalg.norm(x2 - x_o) / np.linalg.norm(x_o) <= XTOL
