@@ -145,6 +145,30 @@ OBK_API obk_status obk_get_info(const obk_handle* h, obk_info* info);
 OBK_API obk_status obk_residual(const obk_csr* A, int64_t m, int64_t n, const double* f, const double* x,
                                 double* rel_res);
 
+/* Allocation-free residual check, for callers that cannot allocate device
+ * memory when they need it (device memory entirely held by another allocator
+ * or pool, or a latency-critical loop that cannot afford an allocation).  The
+ * paper has no counterpart; it is a library convenience.
+ * Same value as obk_residual (same tiles, same summation order), but: every
+ * array -- row_ptr (m+1), col_idx and val (nnz), f (m), x (n) and the output
+ * rel_res (one double) -- must be in device memory of the current device;
+ * the work is queued on `stream` (a cudaStream_t, NULL = default stream) and
+ * the call returns without waiting, so read *rel_res after synchronising it.
+ * Scratch is a fixed 256 KB array in device memory (two doubles per tile of
+ * 4096 rows), present on every device that loads the library until the
+ * process exits: m is limited to 67,108,864 rows (OBK_ERR_INVALID beyond).
+ * Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.
+ * The first call on a device looks up that array's device address (a one-off
+ * set-up); make that first call before any stream capture.  All calls on a
+ * device share the array and each call overwrites the slots it reads, so calls
+ * whose GPU work overlaps (other streams, threads or processes of the same
+ * library instance) race: serialise them.
+ * Errors: OBK_ERR_INVALID (NULL or host pointer, m or n <= 0, m too large),
+ * OBK_ERR_CUDA. */
+OBK_API obk_status obk_residual_noalloc(const int64_t* row_ptr, const int32_t* col_idx, const double* val,
+                                        int64_t m, int64_t n, const double* f, const double* x,
+                                        double* rel_res, void* stream);
+
 /* Release every resource of h (NULL is ignored). */
 OBK_API void obk_destroy(obk_handle* h);
 

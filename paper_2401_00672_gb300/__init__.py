@@ -26,7 +26,7 @@ EXPORTS = [
     "obk_create", "obk_create_on_stream", "obk_solve", "obk_solve_ex", "obk_get_dims", "obk_get_perm",
     "obk_get_groups", "obk_get_row_norms", "obk_get_info", "obk_destroy", "obk_server_create",
     "obk_submit", "obk_poll", "obk_cancel", "obk_server_destroy", "obk_last_error", "obk_version",
-    "obk_kernel_launches", "obk_residual",
+    "obk_kernel_launches", "obk_residual", "obk_residual_noalloc",
 ]
 
 
@@ -101,6 +101,7 @@ def _load() -> ctypes.CDLL:
         "obk_version": ([], ctypes.c_char_p),
         "obk_kernel_launches": ([], ctypes.c_int64),
         "obk_residual": ([vp, i64, i64, vp, vp, vp], ctypes.c_int),
+        "obk_residual_noalloc": ([vp, vp, vp, i64, i64, vp, vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -224,6 +225,20 @@ def residual(row_ptr, col_idx, val, m, n, f, x) -> float:
     out = ctypes.c_double()
     _check(lib.obk_residual(ctypes.byref(csr), m, n, pf, px, ctypes.byref(out)), "obk_residual")
     return out.value
+
+
+def residual_noalloc(row_ptr, col_idx, val, m, n, f, x, out, stream=None) -> int:
+    """obk_residual_noalloc: all arguments are CUDA tensors (out: one float64);
+    queued on `stream` (raw cudaStream_t handle, None = default stream)."""
+    ptrs = []
+    for a, dt in ((row_ptr, np.int64), (col_idx, np.int32), (val, np.float64), (f, np.float64),
+                  (x, np.float64), (out, np.float64)):
+        p, dev, _ = _ptr(a, dt)
+        if not dev:
+            raise TypeError("obk_residual_noalloc takes device arrays only")
+        ptrs.append(p)
+    return _check(lib.obk_residual_noalloc(ptrs[0], ptrs[1], ptrs[2], int(m), int(n), ptrs[3], ptrs[4], ptrs[5],
+                                           ctypes.c_void_p(stream) if stream else None), "obk_residual_noalloc")
 
 
 def solve(row_ptr, col_idx, val, m, n, f, x0=None, thr=0.1, tol=1e-8, maxit=1000, opts=None):
