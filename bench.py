@@ -132,7 +132,7 @@ def run_reference(args, cfg, s):
     for _ in range(nrun):
         t0 = time.perf_counter()
         st, x, info = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=cfg["thr"], tol=cfg["tol"],
-                                   maxit=10000)
+                                   maxit=10000, check_every=-1)
         t_all.append(time.perf_counter() - t0)
     v = float(np.mean(t_all))
     sample = (f"{nrun} full oracle solve(s) of the workload (of {args.steps} requested steps; "
@@ -189,9 +189,11 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     tol = cfg["tol"]
 
+    solve_opts = obk.Opts(check_every=-1)  # adaptive residual-check schedule
+
     def step():
         h = obk.Handle(rp, ci, v, A.m, A.n, thr=cfg["thr"], stream=stream.cuda_stream)
-        st, _, info = h.solve(f, None, tol=tol, maxit=10000, out=x)
+        st, _, info = h.solve(f, None, tol=tol, maxit=10000, out=x, opts=solve_opts)
         h.close()
         return st, info
 
@@ -233,21 +235,26 @@ def main():
     # sweeps with a residual only at start and end; the difference is 50 sweeps
     h = obk.Handle(rp, ci, v, A.m, A.n, thr=cfg["thr"], stream=stream.cuda_stream)
     N, nnz_gm = h.N, A.nnz
-    per = {}
-    for k in (10, 60):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        best = None
-        for _ in range(3):
-            e0.record(stream)
-            h.solve(f, None, tol=1e-300, maxit=k, out=x, opts=obk.Opts(check_every=1 << 30))
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t_ = e0.elapsed_time(e1)
-            best = t_ if best is None else min(best, t_)
-        per[k] = best
+
+    def sweep_time(rpw):
+        per = {}
+        for k in (10, 60):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            best = None
+            for _ in range(3):
+                e0.record(stream)
+                h.solve(f, None, tol=1e-300, maxit=k, out=x, opts=obk.Opts(check_every=1 << 30, rows_per_warp=rpw))
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t_ = e0.elapsed_time(e1)
+                best = t_ if best is None else min(best, t_)
+            per[k] = best
+        return (per[60] - per[10]) / 50.0
+
+    by_rpw = {rpw: round(sweep_time(rpw), 5) for rpw in (32, 16, 8, 4, 2)}
+    sweep_ms = sweep_time(0)  # the default choice, as the timed solve runs it
     h.close()
-    sweep_ms = (per[60] - per[10]) / 50.0
     # algorithmic bytes of one sweep: A read once (8 B value + 4 B column per
     # entry), row pointers (4 B/row as int32), f and 1/||A_i||^2 (8 + 8 B/row),
     # x read and written (16 B/row)
@@ -268,6 +275,7 @@ def main():
                 "frac": round(frac_hbm, 4), "traffic": None, "peak_source": hbm_src,
                 "kernel": "obk_solve_kernel (sweep phases)", "alu_frac_of_nominal_fp64": round(frac_alu, 4)}
     roof["sweep_ms"] = round(sweep_ms, 5)
+    roof["sweep_ms_by_rows_per_warp"] = by_rpw
     roof["bytes_per_sweep"] = bytes_sweep
 
     e2e = None
@@ -282,7 +290,7 @@ def main():
 
         def step_host():
             hh = obk.Handle(rp_h, ci_h, v_h, A.m, A.n, thr=cfg["thr"], stream=stream.cuda_stream)
-            hh.solve(f_h, None, tol=tol, maxit=10000, out=x_h)
+            hh.solve(f_h, None, tol=tol, maxit=10000, out=x_h, opts=solve_opts)
             hh.close()
 
         step_host()
@@ -311,7 +319,7 @@ def main():
         oracle.build()
         t0 = time.perf_counter()
         st_o, x_o, io = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=cfg["thr"], tol=tol,
-                                     maxit=10000)
+                                     maxit=10000, check_every=-1)
         t_cpu = time.perf_counter() - t0
         par = float(np.linalg.norm(xh - x_o) / np.linalg.norm(x_o))
         cpu = {"value": t_cpu, "unit": "s", "cores": 1, "kind": "oracle",

@@ -66,13 +66,17 @@ typedef struct {
     int32_t precision;      /* 0 = FP64 sweeps (default); 1 = FP32 inner sweeps with
                                FP64 iterative refinement (residual, norms, correction) */
     int32_t check_every;    /* FP64: residual checked after every check_every-th sweep
-                               (default 1)                                             */
+                               (0 = default 1); -1 = adaptive: the linear rate seen
+                               between the last two checks predicts the sweep at which
+                               tol is reached, and the next check is placed there (the
+                               gap between checks at most doubles)                    */
     int32_t inner_sweeps;   /* precision 1: FP32 sweeps per refinement step (0 = auto)  */
     int32_t max_outer;      /* precision 1: refinement steps at most (0 = 100)          */
     double stagnation;      /* FP64: stop with OBK_NOT_CONVERGED when the relative
                                residual moved less than this over 10 checks (0 = off)  */
     int64_t timeout_spins;  /* bound on every device-side wait (0 = default, ~seconds) */
-    int32_t rows_per_warp;  /* sweep kernel: rows handled by one warp (0 = autotune)    */
+    int32_t rows_per_warp;  /* sweep kernel: rows one warp handles at a time, 1..32
+                               (0 = chosen from the mean row length)                  */
     int32_t reserved;
 } obk_opts;
 

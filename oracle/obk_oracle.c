@@ -505,6 +505,24 @@ typedef struct {
     double stagnation;     /* stop (not converged) when rr moved less than this over 10 checks */
 } orc_opts;
 
+/* Adaptive residual-check schedule (a stopping-test cadence, not part of the
+ * paper's method): from the last two checks (sweeps s_prev < s, residuals
+ * rr_prev > rr) the linear rate predicts k more sweeps to reach tol; the next
+ * check comes after min(k, s) sweeps, or after one sweep without a rate. */
+static int64_t next_check(int64_t s, double rr, int64_t s_prev, double rr_prev, double tol)
+{
+    int64_t step = 1;
+    if (s_prev > 0 && rr < rr_prev && rr > tol && rr > 0.0) {
+        double rate = pow(rr / rr_prev, 1.0 / (double)(s - s_prev));
+        if (rate > 0.0 && rate < 1.0) {
+            double k = ceil(log(tol / rr) / log(rate));
+            if (k > (double)s) k = (double)s;
+            if (k > 1.0) step = (int64_t)k;
+        }
+    }
+    return s + step;
+}
+
 /* Setup shared by both precisions: extend, RCM, permute, norms, groups. */
 typedef struct {
     int64_t N;
@@ -610,7 +628,8 @@ int orc_solve(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci, const 
     if (!(thr > 0.0 && thr <= 1.0) || !(tol > 0.0) || maxit < 1) return ORC_INVALID;
     for (int64_t i = 0; i < m; ++i)
         if (!isfinite(f[i])) return ORC_INVALID;
-    int32_t check_every = opts && opts->check_every > 0 ? opts->check_every : 1;
+    /* check_every > 0: fixed cadence; < 0: adaptive schedule (next_check) */
+    int32_t check_every = opts && opts->check_every != 0 ? opts->check_every : 1;
     double stag = opts ? opts->stagnation : 0.0;
 
     orc_sys s;
@@ -630,12 +649,15 @@ int orc_solve(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci, const 
         for (int64_t g = 0; g < s.G; ++g)
             if (s.gptr[g + 1] - s.gptr[g] > maxc) maxc = s.gptr[g + 1] - s.gptr[g];
         double* y = malloc((size_t)maxc * sizeof(double));
+        int64_t next = 1, s_prev = 0;
+        double rr_prev = rr;
         for (int64_t sw = 1; sw <= maxit; ++sw) {
             for (int64_t g = 0; g < s.G; ++g)
                 group_step(s.rp, s.ci, s.v, s.nsq, s.f, s.grows + s.gptr[g],
                            s.gptr[g + 1] - s.gptr[g], s.x, y);
             info->sweeps = sw;
-            if (sw % check_every == 0 || sw == maxit) {
+            int check = check_every > 0 ? (sw % check_every == 0 || sw == maxit) : (sw >= next || sw == maxit);
+            if (check) {
                 rr = orc_residual(s.N, s.rp, s.ci, s.v, s.f, s.x);
                 if (rr <= tol) { status = ORC_OK; break; }
                 if (stag > 0.0) {
@@ -643,6 +665,9 @@ int orc_solve(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci, const 
                     hist[nchk % 10] = rr;
                     nchk++;
                 }
+                next = next_check(sw, rr, s_prev, rr_prev, tol);
+                s_prev = sw;
+                rr_prev = rr;
             }
         }
         free(y);

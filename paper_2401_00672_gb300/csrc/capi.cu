@@ -387,11 +387,11 @@ obk_status obk_solve_ex(obk_handle* h, const obk_opts* opts, const double* f, co
     obk_opts o{};
     if (opts) o = *opts;
     if (o.precision != 0 && o.precision != 1) throw Error{-1, "precision must be 0 or 1"};
-    if (o.check_every < 0 || o.inner_sweeps < 0 || o.max_outer < 0 || o.timeout_spins < 0)
+    if (o.check_every < -1 || o.inner_sweeps < 0 || o.max_outer < 0 || o.timeout_spins < 0)
         throw Error{-1, "negative option"};
     if (o.rows_per_warp != 0 && o.rows_per_warp != 1 && o.rows_per_warp != 2 && o.rows_per_warp != 4 &&
-        o.rows_per_warp != 8)
-        throw Error{-1, "rows_per_warp must be 0, 1, 2, 4 or 8"};
+        o.rows_per_warp != 8 && o.rows_per_warp != 16 && o.rows_per_warp != 32)
+        throw Error{-1, "rows_per_warp must be 0, 1, 2, 4, 8, 16 or 32"};
     OBK_CUDA(cudaSetDevice(h->device));
     cudaStream_t st = h->st;
     int64_t m = h->m, n = h->n, N = h->N;
@@ -421,7 +421,7 @@ obk_status obk_solve_ex(obk_handle* h, const obk_opts* opts, const double* f, co
     double zero_f2 = sum_squares(fd.p, h->zero_src.p, h->n_zero, m, st);
     SolveArgs a;
     a.precision = o.precision;
-    a.check_every = o.check_every > 0 ? o.check_every : 1;
+    a.check_every = o.check_every == 0 ? 1 : o.check_every;
     a.inner_sweeps = o.inner_sweeps;
     a.max_outer = o.max_outer > 0 ? o.max_outer : 100;
     a.stagnation = o.stagnation;

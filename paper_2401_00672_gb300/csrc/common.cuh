@@ -91,7 +91,7 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& gb)
                     ok = 0;
                     break;
                 }
-                if (spins > 64) __nanosleep(64);
+                if (spins > 20000) __nanosleep(32);
             }
         }
         __threadfence();

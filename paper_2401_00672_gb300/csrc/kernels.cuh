@@ -76,7 +76,7 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
 
 struct SolveArgs {
     int precision = 0;
-    int check_every = 1;
+    int check_every = 1;  // < 0: adaptive schedule
     int inner_sweeps = 0;
     int max_outer = 100;
     double stagnation = 0.0;

@@ -36,6 +36,8 @@ namespace obk {
 namespace {
 
 constexpr int kBlock = 256;
+constexpr int kCoopBlock = 512;      // cooperative kernels: 512 threads,
+constexpr int kCoopBlocksPerSm = 2;  // two blocks per SM
 constexpr int32_t kUnvisited = -1;
 
 // ---- symmetric graph: pattern(A + A^T) minus self loops -----------------------
@@ -118,6 +120,48 @@ __global__ void adj_rank_keys(int64_t M, const int32_t* adj, const int32_t* r, u
     }
 }
 
+// Warp-aggregated per-component max / min / add: when every lane of the warp
+// holds the same component label one lane issues the atomic.
+__device__ __forceinline__ void agg_max(int32_t* arr, int32_t lab, int32_t val, bool act)
+{
+    unsigned am = __ballot_sync(0xffffffffu, act);
+    if (!am) return;
+    int32_t l0 = __shfl_sync(0xffffffffu, lab, __ffs(am) - 1);
+    bool same = __all_sync(0xffffffffu, !act || lab == l0);
+    if (same) {
+        int32_t m = __reduce_max_sync(0xffffffffu, act ? val : INT32_MIN);
+        if ((threadIdx.x & 31) == __ffs(am) - 1) atomicMax(arr + l0, m);
+    } else if (act) {
+        atomicMax(arr + lab, val);
+    }
+}
+__device__ __forceinline__ void agg_min(int32_t* arr, int32_t lab, int32_t val, bool act)
+{
+    unsigned am = __ballot_sync(0xffffffffu, act);
+    if (!am) return;
+    int32_t l0 = __shfl_sync(0xffffffffu, lab, __ffs(am) - 1);
+    bool same = __all_sync(0xffffffffu, !act || lab == l0);
+    if (same) {
+        int32_t m = __reduce_min_sync(0xffffffffu, act ? val : INT32_MAX);
+        if ((threadIdx.x & 31) == __ffs(am) - 1) atomicMin(arr + l0, m);
+    } else if (act) {
+        atomicMin(arr + lab, val);
+    }
+}
+__device__ __forceinline__ void agg_add(int32_t* arr, int32_t lab, int32_t val, bool act)
+{
+    unsigned am = __ballot_sync(0xffffffffu, act);
+    if (!am) return;
+    int32_t l0 = __shfl_sync(0xffffffffu, lab, __ffs(am) - 1);
+    bool same = __all_sync(0xffffffffu, !act || lab == l0);
+    if (same) {
+        int32_t m = __reduce_add_sync(0xffffffffu, act ? val : 0);
+        if ((threadIdx.x & 31) == __ffs(am) - 1) atomicAdd(arr + l0, m);
+    } else if (act) {
+        atomicAdd(arr + lab, val);
+    }
+}
+
 // ---- connected components by min-hooking ---------------------------------------
 
 __device__ __forceinline__ int32_t find_root(const int32_t* parent, int32_t v)
@@ -165,10 +209,12 @@ __global__ void cc_compress(int64_t N, int32_t* parent)
 __global__ void comp_stats(int64_t N, const int32_t* label, const int32_t* r, int32_t* cmin_r,
                            int32_t* csize)
 {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        atomicMin(cmin_r + label[v], r[v]);
-        atomicAdd(csize + label[v], 1);
+    for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < N; v0 += (int64_t)gridDim.x * blockDim.x) {
+        int64_t v = v0 + threadIdx.x;
+        bool act = v < N;
+        int32_t lab = act ? label[v] : 0;
+        agg_min(cmin_r, lab, act ? r[v] : 0, act);
+        agg_add(csize, lab, 1, act);
     }
 }
 
@@ -210,20 +256,25 @@ struct BfsParams {
     int32_t* dist;      // N, pre-set to kUnvisited
     int32_t* qa;        // N
     int32_t* qb;        // N
-    int64_t* cnt;       // 3 rotating frontier counters, zeroed
+    int64_t* cnt;       // [0..2] rotating frontier counters (zeroed), [3] vertices reached
     int32_t* nlevels;   // out
     GridBarrier gb;
 };
 
-__global__ void __launch_bounds__(kBlock) bfs_levels(BfsParams p)
+// One warp per frontier vertex, lanes over its neighbours; newly reached
+// vertices are appended with one atomic per warp and chunk.
+__global__ void __launch_bounds__(kCoopBlock) bfs_levels(BfsParams p)
 {
+    int lane = threadIdx.x & 31;
+    unsigned lt = (1u << lane) - 1u;
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    int64_t gw = tid >> 5, nw = nth >> 5;
     for (int64_t k = tid; k < p.nsrc; k += nth) {
         p.dist[p.sources[k]] = 0;
         p.qa[k] = p.sources[k];
     }
-    if (tid == 0) p.cnt[0] = p.nsrc;
+    if (tid == 0) { p.cnt[0] = p.nsrc; p.cnt[3] = p.nsrc; }
     if (!grid_sync(p.gb)) return;
     int32_t* cur = p.qa;
     int32_t* nxt = p.qb;
@@ -231,17 +282,33 @@ __global__ void __launch_bounds__(kBlock) bfs_levels(BfsParams p)
     for (;;) {
         int64_t ncur = *(volatile int64_t*)(p.cnt + (L % 3));
         if (ncur == 0) break;
-        if (tid == 0) p.cnt[(L + 2) % 3] = 0;
+        if (tid == 0) {
+            p.cnt[(L + 2) % 3] = 0;
+            if (L > 0) p.cnt[3] += ncur;
+        }
         int64_t* cnext = p.cnt + ((L + 1) % 3);
-        for (int64_t k = tid; k < ncur; k += nth) {
+        for (int64_t k = gw; k < ncur; k += nw) {
             int32_t u = cur[k];
-            for (int64_t e = p.gp[u]; e < p.gp[u + 1]; ++e) {
-                int32_t w = p.adj[e];
-                if (ld_volatile_i32(p.dist + w) != kUnvisited) continue;
-                if (atomicCAS(p.dist + w, kUnvisited, L + 1) == kUnvisited) {
-                    unsigned long long pos = atomicAdd((unsigned long long*)cnext, 1ull);
-                    if ((int64_t)pos < p.N) nxt[pos] = w;
-                    else atomicCAS(p.gb.err, 0, (int)kDevOverflow);
+            int64_t b = p.gp[u], e = p.gp[u + 1];
+            for (int64_t base = b; base < e; base += 32) {
+                int64_t q = base + lane;
+                bool won = false;
+                int32_t w = 0;
+                if (q < e) {
+                    w = p.adj[q];
+                    if (ld_volatile_i32(p.dist + w) == kUnvisited)
+                        won = atomicCAS(p.dist + w, kUnvisited, L + 1) == kUnvisited;
+                }
+                unsigned m = __ballot_sync(0xffffffffu, won);
+                if (m) {
+                    unsigned long long pos0 = 0;
+                    if (lane == __ffs(m) - 1) pos0 = atomicAdd((unsigned long long*)cnext, (unsigned long long)__popc(m));
+                    pos0 = __shfl_sync(0xffffffffu, pos0, __ffs(m) - 1);
+                    if (won) {
+                        int64_t pos = (int64_t)pos0 + __popc(m & lt);
+                        if (pos < p.N) nxt[pos] = w;
+                        else atomicCAS(p.gb.err, 0, (int)kDevOverflow);
+                    }
                 }
             }
         }
@@ -256,9 +323,11 @@ __global__ void __launch_bounds__(kBlock) bfs_levels(BfsParams p)
 
 __global__ void ecc_per_comp(int64_t N, const int32_t* dist, const int32_t* label, int32_t* ecc)
 {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
-         v += (int64_t)gridDim.x * blockDim.x)
-        if (dist[v] >= 0) atomicMax(ecc + label[v], dist[v]);
+    for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < N; v0 += (int64_t)gridDim.x * blockDim.x) {
+        int64_t v = v0 + threadIdx.x;
+        bool act = v < N && dist[v] >= 0;
+        agg_max(ecc, act ? label[v] : 0, act ? dist[v] : 0, act);
+    }
 }
 
 __global__ void last_level_min(int64_t N, const int32_t* dist, const int32_t* label, const int32_t* ecc,
@@ -315,77 +384,86 @@ __global__ void gather_active_sources(int64_t C, const int32_t* which, const int
 }
 
 // ---- Cuthill-McKee levels (all components at once) ----------------------------
+//
+// All levels live back to back in one queue Q: level L is Q[lo, hi).  Level 0
+// holds the component roots in component order; inside every level the
+// vertices are ordered by (component, CM position).  A vertex w reached from
+// level L takes as parent the queue index of its earliest frontier neighbour
+// (atomicMin over queue indices; only same-component vertices compete), and
+// the children of each frontier vertex are appended in rank order after an
+// exclusive scan of the child counts.  So Q lists, level by level, every
+// component's Cuthill-McKee order interleaved; a stable partition of Q by
+// component gives the concatenated order (nothing to do when connected).
 
 struct CmParams {
     int64_t N;
     const int64_t* gp;
     const int32_t* adj_r;    // adjacency sorted by rank
-    const int32_t* label;
-    const int32_t* cidx;     // component order index by label
-    const int64_t* cbase;    // first CM position of each component (by order index)
-    const int32_t* roots;    // by order index
+    const int32_t* roots;    // C roots in component order
     int64_t C;
     int32_t* vis;            // N, kUnvisited
     int32_t* claim;          // N, INT32_MAX
-    int32_t* fa;             // N
-    int32_t* fb;             // N
-    int64_t* cnt;            // N child counts / local offsets
-    int64_t* placed;         // 2*C, double buffered by level parity
-    int64_t* seg_start;      // C
+    int32_t* Q;              // N
+    int64_t* cnt;            // N: per frontier vertex, block-local offset of its children
     int64_t* bsum;           // gridDim + 1
-    int32_t* cm_order;       // N, out
-    int64_t* nlevels;        // out
+    int64_t* nlevels;        // out: [0] levels, [1] vertices placed
     GridBarrier gb;
 };
 
-__global__ void __launch_bounds__(kBlock) cm_levels(CmParams p)
+__global__ void __launch_bounds__(kCoopBlock) cm_levels(CmParams p)
 {
     __shared__ int64_t s_tot;
+    __shared__ int64_t wsum[kCoopBlock / kWarp];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned lt = (1u << lane) - 1u;
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    int64_t gw = tid >> 5, nw = nth >> 5;
+    const int wpb = kCoopBlock / kWarp;
     for (int64_t c = tid; c < p.C; c += nth) {
-        p.fa[c] = p.roots[c];
+        p.Q[c] = p.roots[c];
         p.vis[p.roots[c]] = 0;
-        p.placed[c] = 0;
     }
     if (!grid_sync(p.gb)) return;
-    int32_t* cur = p.fa;
-    int32_t* nxt = p.fb;
-    int64_t F = p.C;
+    int64_t lo = 0, hi = p.C;
     int L = 0;
-    while (F > 0) {
-        int64_t* placedA = p.placed + (L & 1) * p.C;
-        int64_t* placedB = p.placed + ((L + 1) & 1) * p.C;
-        // P1: claim children, mark component segment starts
-        for (int64_t k = tid; k < F; k += nth) {
-            int32_t u = cur[k];
-            int32_t c = p.cidx[p.label[u]];
-            if (k == 0 || p.cidx[p.label[cur[k - 1]]] != c) p.seg_start[c] = k;
-            for (int64_t e = p.gp[u]; e < p.gp[u + 1]; ++e) {
-                int32_t w = p.adj_r[e];
+    while (hi > lo) {
+        int64_t F = hi - lo;
+        // P1: every unvisited neighbour is claimed by its earliest frontier vertex
+        for (int64_t k = lo + gw; k < hi; k += nw) {
+            int32_t u = p.Q[k];
+            int64_t b = p.gp[u], e = p.gp[u + 1];
+            for (int64_t q = b + lane; q < e; q += 32) {
+                int32_t w = p.adj_r[q];
                 if (ld_volatile_i32(p.vis + w) == kUnvisited) atomicMin(p.claim + w, (int32_t)k);
             }
         }
         if (!grid_sync(p.gb)) return;
-        // P2: per block, a contiguous chunk of the frontier: child counts and the
-        // block-local exclusive scan
+        // P2: child counts of this block's chunk of the frontier, block-local scan
         int64_t chunk = ceil_div(F, (int64_t)gridDim.x);
-        int64_t c0 = (int64_t)blockIdx.x * chunk, c1 = c0 + chunk < F ? c0 + chunk : F;
+        int64_t c0 = lo + (int64_t)blockIdx.x * chunk;
+        int64_t c1 = c0 + chunk < hi ? c0 + chunk : hi;
+        for (int64_t k = c0 + wid; k < c1; k += wpb) {
+            int32_t u = p.Q[k];
+            int64_t b = p.gp[u], e = p.gp[u + 1];
+            int64_t n_child = 0;
+            for (int64_t base = b; base < e; base += 32) {
+                int64_t q = base + lane;
+                bool child = false;
+                if (q < e) {
+                    int32_t w = p.adj_r[q];
+                    child = p.vis[w] == kUnvisited && p.claim[w] == (int32_t)k;
+                }
+                n_child += __popc(__ballot_sync(0xffffffffu, child));
+            }
+            if (lane == 0) p.cnt[k] = n_child;
+        }
+        __syncthreads();
         int64_t carry = 0;
         for (int64_t base = c0; base < c1; base += blockDim.x) {
             int64_t k = base + threadIdx.x;
-            int64_t n_child = 0;
-            if (k < c1) {
-                int32_t u = cur[k];
-                for (int64_t e = p.gp[u]; e < p.gp[u + 1]; ++e) {
-                    int32_t w = p.adj_r[e];
-                    if (p.vis[w] == kUnvisited && p.claim[w] == (int32_t)k) ++n_child;
-                }
-            }
-            // block exclusive scan of n_child
-            __shared__ int64_t wsum[kBlock / kWarp];
-            int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-            int64_t inc = n_child;
+            int64_t v = k < c1 ? p.cnt[k] : 0;
+            int64_t inc = v;
             for (int o = 1; o < 32; o <<= 1) {
                 int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
                 if (lane >= o) inc += t;
@@ -394,7 +472,7 @@ __global__ void __launch_bounds__(kBlock) cm_levels(CmParams p)
             __syncthreads();
             if (threadIdx.x == 0) {
                 int64_t run = 0;
-                for (int w = 0; w < kBlock / kWarp; ++w) {
+                for (int w = 0; w < wpb; ++w) {
                     int64_t t = wsum[w];
                     wsum[w] = run;
                     run += t;
@@ -402,13 +480,13 @@ __global__ void __launch_bounds__(kBlock) cm_levels(CmParams p)
                 s_tot = run;
             }
             __syncthreads();
-            if (k < c1) p.cnt[k] = carry + wsum[wid] + inc - n_child;
+            if (k < c1) p.cnt[k] = carry + wsum[wid] + inc - v;
             carry += s_tot;
             __syncthreads();
         }
         if (threadIdx.x == 0) p.bsum[blockIdx.x] = carry;
         if (!grid_sync(p.gb)) return;
-        // P3: exclusive scan of the block sums (block 0)
+        // P3: exclusive scan of the block totals
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             int64_t run = 0;
             for (unsigned b = 0; b < gridDim.x; ++b) {
@@ -419,45 +497,53 @@ __global__ void __launch_bounds__(kBlock) cm_levels(CmParams p)
             p.bsum[gridDim.x] = run;
         }
         if (!grid_sync(p.gb)) return;
-        // P4: positions of this level, children into the next frontier
-        for (int64_t k = tid; k < F; k += nth) {
-            int32_t u = cur[k];
-            int32_t c = p.cidx[p.label[u]];
-            int64_t s0 = p.seg_start[c];
-            int64_t pos = p.cbase[c] + placedA[c] + (k - s0);
-            if (pos >= 0 && pos < p.N) p.cm_order[pos] = u;
-            else atomicCAS(p.gb.err, 0, (int)kDevOverflow);
-            bool seg_end = (k == F - 1) || p.cidx[p.label[cur[k + 1]]] != c;
-            if (seg_end) placedB[c] = placedA[c] + (k + 1 - s0);
-            int64_t o = p.cnt[k] + p.bsum[k / chunk];
-            for (int64_t e = p.gp[u]; e < p.gp[u + 1]; ++e) {
-                int32_t w = p.adj_r[e];
-                if (p.vis[w] == kUnvisited && p.claim[w] == (int32_t)k) {
-                    if (o >= 0 && o < p.N) nxt[o] = w;
+        // P4: append the children of every frontier vertex in rank order
+        for (int64_t k = lo + gw; k < hi; k += nw) {
+            int32_t u = p.Q[k];
+            int64_t b = p.gp[u], e = p.gp[u + 1];
+            int64_t o = hi + p.bsum[(k - lo) / chunk] + p.cnt[k];
+            for (int64_t base = b; base < e; base += 32) {
+                int64_t q = base + lane;
+                bool child = false;
+                int32_t w = 0;
+                if (q < e) {
+                    w = p.adj_r[q];
+                    child = p.vis[w] == kUnvisited && p.claim[w] == (int32_t)k;
+                }
+                unsigned m = __ballot_sync(0xffffffffu, child);
+                if (child) {
+                    int64_t pos = o + __popc(m & lt);
+                    if (pos < p.N) p.Q[pos] = w;
                     else atomicCAS(p.gb.err, 0, (int)kDevOverflow);
-                    ++o;
                     p.vis[w] = L + 1;
                 }
+                o += __popc(m);
             }
         }
-        // components absent from this level keep their count
         if (!grid_sync(p.gb)) return;
-        int64_t Fn = *(volatile int64_t*)(p.bsum + gridDim.x);
-        // carry placed counts of components that had no vertex in this level
-        for (int64_t c = tid; c < p.C; c += nth) {
-            // a component is in F_L iff seg_start[c] points at one of its vertices
-            int64_t s0 = p.seg_start[c];
-            bool present = s0 < F && p.cidx[p.label[cur[s0]]] == (int32_t)c;
-            if (!present) placedB[c] = placedA[c];
+        int64_t nf = *(volatile int64_t*)(p.bsum + gridDim.x);
+        if (nf < 0 || hi + nf > p.N) {  // cannot happen for a valid queue; stop before any overrun
+            if (tid == 0) atomicCAS(p.gb.err, 0, (int)kDevOverflow);
+            return;
         }
-        if (!grid_sync(p.gb)) return;
-        int32_t* t = cur;
-        cur = nxt;
-        nxt = t;
-        F = Fn;
+        lo = hi;
+        hi = hi + nf;
         ++L;
     }
-    if (tid == 0) *p.nlevels = L;
+    if (tid == 0) {
+        p.nlevels[0] = L;
+        p.nlevels[1] = hi;
+    }
+}
+
+__global__ void comp_keys(int64_t N, const int32_t* Q, const int32_t* label, const int32_t* cidx, uint64_t* keys,
+                          uint32_t* vals)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        keys[k] = (uint64_t)(uint32_t)cidx[label[Q[k]]];
+        vals[k] = (uint32_t)Q[k];
+    }
 }
 
 __global__ void reverse_into_perm(int64_t N, const int32_t* cm_order, int32_t* perm)
@@ -536,71 +622,84 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
     ak.release();
     const int32_t* adj_r = reinterpret_cast<const int32_t*>(av.p);
 
-    // 4. connected components (label = smallest vertex index)
-    DBuf<int32_t> label(N, st);
-    DBuf<int> changed(1, st);
-    cc_init<<<grid_for(N), kBlock, 0, st>>>(N, label.p);
-    OBK_CHECK_LAUNCH();
-    for (int it = 0; it < 100000; ++it) {
-        OBK_CUDA(cudaMemsetAsync(changed.p, 0, sizeof(int), st));
-        cc_hook<<<grid_for(N), kBlock, 0, st>>>(N, gp.p, adj.p, label.p, changed.p);
-        OBK_CHECK_LAUNCH();
-        cc_compress<<<grid_for(N), kBlock, 0, st>>>(N, label.p);
-        OBK_CHECK_LAUNCH();
-        if (read_scalar(changed.p, st) == 0) break;
-    }
-    adj.release();
-
-    // 5. component order and bases
-    DBuf<int32_t> cmin_r(N, st), csize(N, st), flag(N, st), cidx(N, st);
-    DBuf<int64_t> fscan(N + 1, st);
-    OBK_CUDA(cudaMemsetAsync(cmin_r.p, 0x7f, N * sizeof(int32_t), st));
-    OBK_CUDA(cudaMemsetAsync(csize.p, 0, N * sizeof(int32_t), st));
-    comp_stats<<<grid_for(N), kBlock, 0, st>>>(N, label.p, r.p, cmin_r.p, csize.p);
-    OBK_CHECK_LAUNCH();
-    comp_start_flags<<<grid_for(N), kBlock, 0, st>>>(N, by_rank.p, label.p, cmin_r.p, flag.p);
-    OBK_CHECK_LAUNCH();
-    exclusive_scan_i32_to_i64(flag.p, fscan.p, N, st);
-    int64_t C = read_scalar(fscan.p + N, st);
-    DBuf<int32_t> roots(C, st);
-    DBuf<int64_t> size_by_idx(C, st), cbase(C + 1, st);
-    comp_order<<<grid_for(N), kBlock, 0, st>>>(N, by_rank.p, label.p, flag.p, fscan.p, cidx.p, roots.p,
-                                               size_by_idx.p, csize.p);
-    OBK_CHECK_LAUNCH();
-    exclusive_scan_i64(size_by_idx.p, cbase.p, C, st);
-
-    // 6. George-Liu pseudo-peripheral roots, all components at once
+    // 4. first search from the global minimum-(deg, index) vertex; if it
+    //    reaches every vertex the graph is connected and no labelling is needed
+    DBuf<int32_t> label(N, st), cidx(N, st);
     DBuf<int32_t> dist(N, st), qa(N, st), qb(N, st), ecc(N, st), cand_r(N, st);
-    DBuf<int32_t> ecc_root(C, st), cand(C, st), active(C, st), src(C, st);
-    DBuf<int64_t> cnt3(3, st), nsrc(1, st);
+    DBuf<int64_t> cnt4(4, st), nsrc(1, st);
     DBuf<int32_t> nlev(1, st);
     DBuf<unsigned> bar(2, st);
-    int any_h = 1;
-    DBuf<int> any(1, st);
-    // all components start active (any nonzero word is "active")
-    OBK_CUDA(cudaMemsetAsync(active.p, 1, C * sizeof(int32_t), st));
-    int bfs_grid = coop_grid((const void*)bfs_levels, kBlock, 0, (int64_t)di.sms * 8);
-    auto run_bfs = [&](const int32_t* sources, int64_t ns) {
+    int bfs_grid = coop_grid((const void*)bfs_levels, kCoopBlock, 0, (int64_t)di.sms * kCoopBlocksPerSm);
+    auto run_bfs = [&](const int32_t* sources, int64_t ns) -> int64_t {
         OBK_CUDA(cudaMemsetAsync(dist.p, 0xff, N * sizeof(int32_t), st));
-        OBK_CUDA(cudaMemsetAsync(cnt3.p, 0, 3 * sizeof(int64_t), st));
+        OBK_CUDA(cudaMemsetAsync(cnt4.p, 0, 4 * sizeof(int64_t), st));
         OBK_CUDA(cudaMemsetAsync(bar.p, 0, 2 * sizeof(unsigned), st));
-        BfsParams bp{N, gp.p, adj_r, sources, ns, dist.p, qa.p, qb.p, cnt3.p, nlev.p,
+        BfsParams bp{N, gp.p, adj_r, sources, ns, dist.p, qa.p, qb.p, cnt4.p, nlev.p,
                      GridBarrier{bar.p, d_err, spin_limit}};
         void* args[] = {&bp};
-        OBK_COOP_LAUNCH(bfs_levels, bfs_grid, kBlock, args, st);
+        OBK_COOP_LAUNCH(bfs_levels, bfs_grid, kCoopBlock, args, st);
         OBK_CUDA(cudaMemsetAsync(ecc.p, 0, N * sizeof(int32_t), st));
         OBK_CUDA(cudaMemsetAsync(cand_r.p, 0x7f, N * sizeof(int32_t), st));
         ecc_per_comp<<<grid_for(N), kBlock, 0, st>>>(N, dist.p, label.p, ecc.p);
         OBK_CHECK_LAUNCH();
         last_level_min<<<grid_for(N), kBlock, 0, st>>>(N, dist.p, label.p, ecc.p, r.p, cand_r.p);
         OBK_CHECK_LAUNCH();
+        int64_t reached = read_scalar(cnt4.p + 3, st);
+        if (read_scalar(d_err, st) != 0) throw Error{-4, "bounded wait expired in RCM search"};
+        return reached;
     };
-    run_bfs(roots.p, C);
+    OBK_CUDA(cudaMemsetAsync(label.p, 0, N * sizeof(int32_t), st));
+    DBuf<int32_t> s0(1, st);
+    OBK_CUDA(cudaMemcpyAsync(s0.p, by_rank.p, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    int64_t reached = run_bfs(s0.p, 1);
+    int64_t C = 1;
+    DBuf<int32_t> roots;
+    if (reached == N) {
+        roots.alloc(1, st);
+        OBK_CUDA(cudaMemcpyAsync(roots.p, s0.p, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        OBK_CUDA(cudaMemsetAsync(cidx.p, 0, sizeof(int32_t), st));  // label 0 -> component 0
+    } else {
+        // connected components (label = smallest vertex index) by min-hooking
+        DBuf<int> changed(1, st);
+        cc_init<<<grid_for(N), kBlock, 0, st>>>(N, label.p);
+        OBK_CHECK_LAUNCH();
+        for (int it = 0; it < 100000; ++it) {
+            OBK_CUDA(cudaMemsetAsync(changed.p, 0, sizeof(int), st));
+            cc_hook<<<grid_for(N), kBlock, 0, st>>>(N, gp.p, adj.p, label.p, changed.p);
+            OBK_CHECK_LAUNCH();
+            cc_compress<<<grid_for(N), kBlock, 0, st>>>(N, label.p);
+            OBK_CHECK_LAUNCH();
+            if (read_scalar(changed.p, st) == 0) break;
+        }
+        // component order (by minimum-(deg, index) vertex) and first positions
+        DBuf<int32_t> cmin_r(N, st), csize(N, st), flag(N, st);
+        DBuf<int64_t> fscan(N + 1, st);
+        OBK_CUDA(cudaMemsetAsync(cmin_r.p, 0x7f, N * sizeof(int32_t), st));
+        OBK_CUDA(cudaMemsetAsync(csize.p, 0, N * sizeof(int32_t), st));
+        comp_stats<<<grid_for(N), kBlock, 0, st>>>(N, label.p, r.p, cmin_r.p, csize.p);
+        OBK_CHECK_LAUNCH();
+        comp_start_flags<<<grid_for(N), kBlock, 0, st>>>(N, by_rank.p, label.p, cmin_r.p, flag.p);
+        OBK_CHECK_LAUNCH();
+        exclusive_scan_i32_to_i64(flag.p, fscan.p, N, st);
+        C = read_scalar(fscan.p + N, st);
+        roots.alloc(C, st);
+        DBuf<int64_t> size_by_idx(C, st);
+        comp_order<<<grid_for(N), kBlock, 0, st>>>(N, by_rank.p, label.p, flag.p, fscan.p, cidx.p, roots.p,
+                                                   size_by_idx.p, csize.p);
+        OBK_CHECK_LAUNCH();
+        run_bfs(roots.p, C);
+    }
+    adj.release();
+
+    // 5. George-Liu pseudo-peripheral roots, all components at once
+    DBuf<int32_t> ecc_root(C, st), cand(C, st), active(C, st), src(C, st);
+    DBuf<int> any(1, st);
+    OBK_CUDA(cudaMemsetAsync(active.p, 1, C * sizeof(int32_t), st));  // nonzero word = active
     gl_record_root<<<grid_for(C), kBlock, 0, st>>>(C, roots.p, label.p, ecc.p, cand_r.p, by_rank.p,
                                                     ecc_root.p, cand.p, active.p);
     OBK_CHECK_LAUNCH();
     int gl_rounds = 0;
-    while (any_h) {
+    for (;;) {
         ++gl_rounds;
         OBK_CUDA(cudaMemsetAsync(nsrc.p, 0, sizeof(int64_t), st));
         gather_active_sources<<<grid_for(C), kBlock, 0, st>>>(C, cand.p, active.p, src.p, nsrc.p);
@@ -612,28 +711,38 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
         gl_compare<<<grid_for(C), kBlock, 0, st>>>(C, roots.p, label.p, ecc.p, cand_r.p, by_rank.p,
                                                     ecc_root.p, cand.p, active.p, any.p);
         OBK_CHECK_LAUNCH();
-        any_h = read_scalar(any.p, st);
-        if (read_scalar(d_err, st) != 0) throw Error{-4, "bounded wait expired in RCM search"};
+        if (read_scalar(any.p, st) == 0) break;
     }
     dist.release(); ecc.release(); cand_r.release(); ecc_root.release(); cand.release();
     active.release(); src.release();
 
-    // 7. Cuthill-McKee levels
-    DBuf<int32_t> vis(N, st), claim(N, st), cm(N, st);
-    DBuf<int64_t> ccnt(N, st), placed(2 * C, st), segs(C, st), nl(1, st);
+    // 6. Cuthill-McKee levels into one queue, then the per-component order
+    DBuf<int32_t> vis(N, st), claim(N, st);
+    DBuf<int64_t> ccnt(N, st), nl(2, st);
+    int32_t* Q = qa.p;
     OBK_CUDA(cudaMemsetAsync(vis.p, 0xff, N * sizeof(int32_t), st));
     OBK_CUDA(cudaMemsetAsync(claim.p, 0x7f, N * sizeof(int32_t), st));
-    OBK_CUDA(cudaMemsetAsync(placed.p, 0, 2 * C * sizeof(int64_t), st));
-    OBK_CUDA(cudaMemsetAsync(segs.p, 0x7f, C * sizeof(int64_t), st));
     OBK_CUDA(cudaMemsetAsync(bar.p, 0, 2 * sizeof(unsigned), st));
-    int cm_grid = coop_grid((const void*)cm_levels, kBlock, 0, (int64_t)di.sms * 8);
+    int cm_grid = coop_grid((const void*)cm_levels, kCoopBlock, 0, (int64_t)di.sms * kCoopBlocksPerSm);
     DBuf<int64_t> bsum(cm_grid + 1, st);
-    CmParams cp{N, gp.p, adj_r, label.p, cidx.p, cbase.p, roots.p, C, vis.p, claim.p, qa.p, qb.p,
-                ccnt.p, placed.p, segs.p, bsum.p, cm.p, nl.p, GridBarrier{bar.p, d_err, spin_limit}};
+    CmParams cp{N, gp.p, adj_r, roots.p, C, vis.p, claim.p, Q, ccnt.p, bsum.p, nl.p,
+                GridBarrier{bar.p, d_err, spin_limit}};
     void* args[] = {&cp};
-    OBK_COOP_LAUNCH(cm_levels, cm_grid, kBlock, args, st);
-    if (read_scalar(d_err, st) != 0) throw Error{-4, "bounded wait expired in Cuthill-McKee levels"};
-    reverse_into_perm<<<grid_for(N), kBlock, 0, st>>>(N, cm.p, perm);
+    OBK_COOP_LAUNCH(cm_levels, cm_grid, kCoopBlock, args, st);
+    if (read_scalar(d_err, st) != 0) throw Error{-4, "bounded wait or bound check failed in Cuthill-McKee levels"};
+    if (read_scalar(nl.p + 1, st) != N) throw Error{-5, "internal error: Cuthill-McKee order does not cover every vertex"};
+    const int32_t* cm = Q;
+    DBuf<uint64_t> ck;
+    DBuf<uint32_t> cv;
+    if (C > 1) {
+        ck.alloc(N, st);
+        cv.alloc(N, st);
+        comp_keys<<<grid_for(N), kBlock, 0, st>>>(N, Q, label.p, cidx.p, ck.p, cv.p);
+        OBK_CHECK_LAUNCH();
+        radix_sort_pairs(ck.p, cv.p, N, bits_for((uint64_t)C), st);
+        cm = reinterpret_cast<const int32_t*>(cv.p);
+    }
+    reverse_into_perm<<<grid_for(N), kBlock, 0, st>>>(N, cm, perm);
     OBK_CHECK_LAUNCH();
     if (stats) {
         stats->components = C;

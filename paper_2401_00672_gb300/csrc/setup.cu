@@ -54,16 +54,20 @@ __global__ void validate_rows(int64_t m, int64_t n, const int64_t* rp, const int
 __global__ void bandwidth_kernel(int64_t N, const int64_t* rp, const int32_t* ci,
                                  unsigned long long* bw)
 {
+    unsigned long long mx = 0;
     GRID_STRIDE(i, N)
     {
-        unsigned long long mx = 0;
         for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
             long long d = (long long)i - ci[e];
             unsigned long long a = (unsigned long long)(d < 0 ? -d : d);
             mx = a > mx ? a : mx;
         }
-        if (mx) atomicMax(bw, mx);
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = t > mx ? t : mx;
+    }
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(bw, mx);
 }
 
 // ---- permutation -------------------------------------------------------------
@@ -216,6 +220,26 @@ __device__ __forceinline__ uint32_t hslot(int32_t j, uint32_t mask)
     return ((uint32_t)j * 0x9E3779B1u) & mask;
 }
 
+// |cos_ij| >= thr with cos_ij = RN(dot / RN(s_j * s_i)), decided exactly.
+// t = RN(RN(thr * s_i) * s_j) is within 3 units of rounding of thr * s_i * s_j,
+// so |dot| above t (1 + 2^-48) proves the quotient exceeds thr, and below
+// t (1 - 2^-48) proves it rounds below thr; only the narrow band in between
+// takes the IEEE division.  The comparisons use the ordered bit patterns of
+// non-negative doubles (integer compares).
+__device__ __forceinline__ bool is_conflict(double dot, double sj, double si, double thr_si, double thr)
+{
+    double a = fabs(dot);
+    double t = thr_si * sj;
+    if (t > 1e-280 && t < 1e280 && a < 1e300) {
+        long long ab = __double_as_longlong(a);
+        long long hi = __double_as_longlong(t * (1.0 + 0x1p-48));
+        long long lo = __double_as_longlong(t * (1.0 - 0x1p-48));
+        if (ab > hi) return true;
+        if (ab < lo) return false;
+    }
+    return fabs(__ddiv_rn(dot, __dmul_rn(sj, si))) >= thr;
+}
+
 __global__ void __launch_bounds__(kPairWarps * 32) pair_conflicts(PairParams p)
 {
     __shared__ int32_t skey[kPairWarps][kPairCap];
@@ -267,19 +291,32 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_conflicts(PairParams p)
             }
             __syncwarp();
         }
-        // conflicts: count, reserve, write
-        double si = p.s[i];
-        int cnt = 0;
+        // compact the occupied slots to the front of the table (in slot order)
+        int nc = 0;
         for (int64_t t0 = 0; t0 < cap; t0 += 32) {
             int64_t t = t0 + lane;
-            bool conf = false;
-            if (t < cap) {
-                int32_t j = key[t];
-                if (j != kEmpty) {
-                    double cv = __ddiv_rn(val[t], __dmul_rn(p.s[j], si));
-                    conf = fabs(cv) >= p.thr;
-                }
+            int32_t j = t < cap ? key[t] : kEmpty;
+            double a = t < cap ? val[t] : 0.0;
+            unsigned m = __ballot_sync(0xffffffffu, j != kEmpty);
+            __syncwarp();
+            if (j != kEmpty) {
+                key[nc + __popc(m & lt)] = j;
+                val[nc + __popc(m & lt)] = a;
             }
+            nc += __popc(m);
+            __syncwarp();
+        }
+        // one conflict decision per candidate, kept as bits (64 candidates per lane)
+        double si = p.s[i];
+        double thr_si = p.thr * si;
+        int cnt = 0;
+        unsigned long long flags = 0;
+        bool many = nc > 32 * 64;
+        for (int t0 = 0, it = 0; t0 < nc; t0 += 32, ++it) {
+            int t = t0 + lane;
+            bool conf = false;
+            if (t < nc) conf = is_conflict(val[t], p.s[key[t]], si, thr_si, p.thr);
+            if (conf && !many) flags |= 1ull << it;
             cnt += __popc(__ballot_sync(0xffffffffu, conf));
         }
         unsigned long long base = 0;
@@ -290,22 +327,15 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_conflicts(PairParams p)
             p.conf_off[i] = (int64_t)base;
         }
         base = __shfl_sync(0xffffffffu, base, 0);
-        bool fits = (int64_t)(base + cnt) <= p.pool_cap;
-        int run = 0;
-        if (fits) {
-            for (int64_t t0 = 0; t0 < cap; t0 += 32) {
-                int64_t t = t0 + lane;
-                bool conf = false;
-                int32_t j = kEmpty;
-                if (t < cap) {
-                    j = key[t];
-                    if (j != kEmpty) {
-                        double cv = __ddiv_rn(val[t], __dmul_rn(p.s[j], si));
-                        conf = fabs(cv) >= p.thr;
-                    }
-                }
+        if ((int64_t)(base + cnt) <= p.pool_cap) {
+            int run = 0;
+            for (int t0 = 0, it = 0; t0 < nc; t0 += 32, ++it) {
+                int t = t0 + lane;
+                bool conf;
+                if (!many) conf = (flags >> it) & 1ull;
+                else conf = t < nc && is_conflict(val[t], p.s[key[t]], si, thr_si, p.thr);
                 unsigned b = __ballot_sync(0xffffffffu, conf);
-                if (conf) p.pool[base + run + __popc(b & lt)] = j;
+                if (conf) p.pool[base + run + __popc(b & lt)] = key[t];
                 run += __popc(b);
             }
         }
@@ -384,7 +414,10 @@ __global__ void __launch_bounds__(kBlock) greedy_color(ColorParams p)
 
 __global__ void max_color(int64_t N, const int32_t* color, int* gmax)
 {
-    GRID_STRIDE(i, N) if (color[i] >= 0) atomicMax(gmax, color[i]);
+    int m = -1;
+    GRID_STRIDE(i, N) m = color[i] > m ? color[i] : m;
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m >= 0) atomicMax(gmax, m);
 }
 
 // ---- group layout -------------------------------------------------------------
@@ -398,9 +431,21 @@ __global__ void color_keys(int64_t N, const int32_t* color, int32_t G, uint64_t*
     }
 }
 
+// histogram of colours; colours below 256 are counted in shared memory first
 __global__ void group_hist(int64_t N, const int32_t* color, int64_t* cnt)
 {
-    GRID_STRIDE(i, N) if (color[i] >= 0) atomicAdd((unsigned long long*)&cnt[color[i]], 1ull);
+    __shared__ unsigned h[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) h[t] = 0;
+    __syncthreads();
+    GRID_STRIDE(i, N)
+    {
+        int32_t c = color[i];
+        if (c >= 0 && c < 256) atomicAdd(&h[c], 1u);
+        else if (c >= 256) atomicAdd((unsigned long long*)&cnt[c], 1ull);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 256; t += blockDim.x)
+        if (h[t]) atomicAdd((unsigned long long*)&cnt[t], (unsigned long long)h[t]);
 }
 
 __global__ void gm_rows(int64_t Ngm, const uint32_t* order, const int64_t* rp, const double* nsq,

@@ -30,7 +30,8 @@
 namespace obk {
 namespace {
 
-constexpr int kBlock = 256;
+constexpr int kBlock = 512;       // threads per block of the persistent kernel
+constexpr int kBlocksPerSm = 2;   // co-resident blocks per SM (barrier arrivals = 2 x SMs)
 
 struct SweepParams {
     int64_t N, Ngm, G;
@@ -56,10 +57,11 @@ struct SweepParams {
     float* d32;       // N
     double fnorm, zero_f2, tol, stagnation;
     int64_t maxit;
-    int check_every, precision, inner_sweeps, max_outer;
+    int check_every, precision, inner_sweeps, max_outer;  // check_every < 0: adaptive schedule
     double* partial;  // gridDim.x
     double* ctrl;     // [0] rr, [1] beta, [2..11] history
-    int64_t* out;     // [0] sweeps, [1] status, [2] outer, [3] stop, [4] sweep ns, [5] inner
+    int64_t* out;     // [0] sweeps, [1] status, [2] outer, [3] stop, [4] sweep ns, [5] inner,
+                      // [6] next checked sweep (adaptive schedule), [7] residual checks done
     GridBarrier gb;
 };
 
@@ -170,8 +172,29 @@ __device__ double total_partials(const SweepParams& p)
     return s + p.zero_f2;
 }
 
+// Adaptive residual-check schedule: from the last two checks (sweeps s_prev < s,
+// residuals rr_prev > rr) the linear rate predicts k more sweeps to reach tol;
+// the next check comes after min(k, s) sweeps (the gap at most doubles), or
+// after one sweep when no rate is available.  The CPU reference applies the
+// same rule.
+__device__ __forceinline__ int64_t next_check(int64_t s, double rr, int64_t s_prev, double rr_prev, double tol)
+{
+    int64_t step = 1;
+    if (s_prev > 0 && rr < rr_prev && rr > tol && rr > 0.0) {
+        double rate = pow(rr / rr_prev, 1.0 / (double)(s - s_prev));
+        if (rate > 0.0 && rate < 1.0) {
+            double k = ceil(log(tol / rr) / log(rate));
+            if (k > (double)s) k = (double)s;
+            if (k > 1.0) step = (int64_t)k;
+        }
+    } else if (s_prev == 0) {
+        step = 1;
+    }
+    return s + step;
+}
+
 template <int SUB>
-__global__ void __launch_bounds__(kBlock) obk_solve_kernel(SweepParams p)
+__global__ void __launch_bounds__(kBlock, kBlocksPerSm) obk_solve_kernel(SweepParams p)
 {
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     volatile int64_t* vout = p.out;
@@ -194,6 +217,11 @@ __global__ void __launch_bounds__(kBlock) obk_solve_kernel(SweepParams p)
     if (p.precision == 0) {
         int64_t s = 0;
         int64_t nchk = 0;
+        // adaptive schedule state (lead thread only): last checked sweep and its residual
+        int64_t s_prev = 0;
+        double rr_prev = p.ctrl[0];
+        if (lead) vout[6] = 1;
+        if (!grid_sync(p.gb)) return;
         while (vout[3] == 0) {
             unsigned long long t0 = lead ? globaltimer() : 0;
             for (int64_t g = 0; g < p.G; ++g) {
@@ -204,7 +232,8 @@ __global__ void __launch_bounds__(kBlock) obk_solve_kernel(SweepParams p)
             }
             ++s;
             if (lead) { vout[4] += (int64_t)(globaltimer() - t0); vout[0] = s; }
-            bool check = (s % p.check_every) == 0 || s >= p.maxit;
+            bool check = p.check_every > 0 ? ((s % p.check_every) == 0 || s >= p.maxit)
+                                           : (s >= vout[6] || s >= p.maxit);
             if (check) {
                 residual_partial<SUB>(p, false);
                 if (!grid_sync(p.gb)) return;
@@ -212,6 +241,7 @@ __global__ void __launch_bounds__(kBlock) obk_solve_kernel(SweepParams p)
                     double tot = total_partials(p);
                     double rr = p.fnorm > 0.0 ? sqrt(tot) / p.fnorm : sqrt(tot);
                     p.ctrl[0] = rr;
+                    vout[7] += 1;
                     int stop = 0;
                     if (rr <= p.tol) { vout[1] = 0; stop = 1; }
                     else if (s >= p.maxit) stop = 1;
@@ -222,6 +252,9 @@ __global__ void __launch_bounds__(kBlock) obk_solve_kernel(SweepParams p)
                     }
                     ++nchk;
                     vout[3] = stop;
+                    vout[6] = next_check(s, rr, s_prev, rr_prev, p.tol);
+                    s_prev = s;
+                    rr_prev = rr;
                 }
                 if (!grid_sync(p.gb)) return;
             }
@@ -300,7 +333,7 @@ void launch_solve(SweepParams& p, cudaStream_t st)
 {
     DevInfo di = dev_info();
     const void* k = (const void*)obk_solve_kernel<SUB>;
-    int grid = coop_grid(k, kBlock, 0, (int64_t)di.sms * 8);
+    int grid = coop_grid(k, kBlock, 0, (int64_t)di.sms * kBlocksPerSm);
     DBuf<double> partial(grid, st);
     p.partial = partial.p;
     void* args[] = {&p};
@@ -310,11 +343,14 @@ void launch_solve(SweepParams& p, cudaStream_t st)
 
 }  // namespace
 
+// Lanes per row in phase 1.  FP64 issue is the scarce resource on this GPU
+// (a warp-wide FP64 instruction occupies the SM's FP64 pipe for many cycles),
+// so short rows get one or two lanes and no shuffle reduction.
 int choose_sub(double avg_row)
 {
-    if (avg_row <= 6) return 4;
-    if (avg_row <= 12) return 8;
-    if (avg_row <= 40) return 16;
+    if (avg_row <= 24) return 1;
+    if (avg_row <= 64) return 2;
+    if (avg_row <= 160) return 8;
     return 32;
 }
 
@@ -367,7 +403,7 @@ SolveResult run_solve(const SweepLayout& L, const double* f_gm, double fnorm2, d
     p.tol = a.tol;
     p.stagnation = a.stagnation;
     p.maxit = a.maxit;
-    p.check_every = a.check_every > 0 ? a.check_every : 1;
+    p.check_every = a.check_every;
     p.precision = a.precision;
     p.inner_sweeps = a.inner_sweeps;
     p.max_outer = a.max_outer > 0 ? a.max_outer : 100;
@@ -377,6 +413,8 @@ SolveResult run_solve(const SweepLayout& L, const double* f_gm, double fnorm2, d
     int sub = a.sub;
     if (sub == 0) sub = choose_sub(L.Ngm ? (double)L.nnz_gm / (double)L.Ngm : 1.0);
     switch (sub) {
+        case 1: launch_solve<1>(p, st); break;
+        case 2: launch_solve<2>(p, st); break;
         case 4: launch_solve<4>(p, st); break;
         case 8: launch_solve<8>(p, st); break;
         case 16: launch_solve<16>(p, st); break;

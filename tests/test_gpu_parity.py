@@ -130,6 +130,31 @@ def test_solve_parity(obk, name):
         assert np.linalg.norm(x - x_o) / (nrm if nrm > 0 else 1.0) <= XTOL
 
 
+@pytest.mark.parametrize("name", ["knn_30000", "random_dominant_2000"])
+def test_adaptive_schedule_parity(obk, name):
+    s, _ = _case(name)
+    A = s.A
+    st_o, x_o, io = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1, tol=1e-8, maxit=5000,
+                                 check_every=-1)
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
+        st, x, info = h.solve(s.f, None, tol=1e-8, maxit=5000, opts=obk.Opts(check_every=-1))
+    assert st == st_o == obk.OBK_OK and info.rel_res <= 1e-8
+    assert abs(info.sweeps - io.sweeps) <= 1
+    if info.sweeps == io.sweeps:
+        assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) <= XTOL
+
+
+@pytest.mark.parametrize("rpw", [1, 2, 4, 8, 16, 32])
+def test_rows_per_warp_variants_agree(obk, rpw):
+    s, su = _case("knn_30000")
+    A = s.A
+    _, x_o, io = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1, tol=1e-300, maxit=4)
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
+        st, x, info = h.solve(s.f, None, tol=1e-300, maxit=4, opts=obk.Opts(rows_per_warp=rpw))
+    assert info.sweeps == 4
+    assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) <= XTOL
+
+
 def test_fixed_sweeps_with_x0_and_device_buffers(obk):
     import torch
 

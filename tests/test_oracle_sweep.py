@@ -222,3 +222,15 @@ def test_validate_rejects_bad_csr():
                            np.array([1.0, np.nan, 1.0])) != 0
     assert oracle.validate(2, 2, np.array([0, 3, 2]), np.array([0, 1, 1], np.int32),
                            np.ones(3)) != 0
+
+
+def test_adaptive_check_schedule_never_stops_early():
+    # the adaptive cadence only moves residual checks; it must never report
+    # convergence before the every-sweep test would, and overshoots little
+    s = synth.knn_dominant(20000, seed=41)
+    A = s.A
+    for tol in (1e-6, 1e-8, 1e-10):
+        _, _, fixed = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, tol=tol, maxit=5000, check_every=1)
+        st, _, ad = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, tol=tol, maxit=5000, check_every=-1)
+        assert st == oracle.OK and ad.rel_res <= tol
+        assert fixed.sweeps <= ad.sweeps <= fixed.sweeps + max(2, fixed.sweeps // 4)
