@@ -145,6 +145,109 @@ def run_reference(args, cfg, s):
     print(json.dumps(line), flush=True)
 
 
+def precision_study(args):
+    """FP64 sweeps vs FP32 sweeps + FP64 refinement, both to rel. residual 1e-10,
+    on the kNN generator at n = args.pn; error of both against the FP64 CPU
+    oracle at n = 200,000 (the oracle run is bounded to that size)."""
+    import torch
+
+    import oracle
+    import paper_2401_00672_gb300 as obk
+    import synth
+
+    out = {"metric": "time_to_solution_1e-10", "unit": "s"}
+    dev = torch.device("cuda")
+    stream = torch.cuda.Stream()
+    for n in (args.pn, 200_000):
+        s = synth.knn_dominant(n, 12, seed=1003)
+        A = s.A
+        rp = torch.from_numpy(A.row_ptr).to(dev)
+        ci = torch.from_numpy(A.col_idx).to(dev)
+        v = torch.from_numpy(A.val).to(dev)
+        f = torch.from_numpy(s.f).to(dev)
+        x = torch.empty(A.n, dtype=torch.float64, device=dev)
+        res = {}
+        for name, opts in (("fp64", obk.Opts(check_every=-1)), ("fp32_ir", obk.Opts(precision=1))):
+            times = []
+            for rep in range(4):
+                h = obk.Handle(rp, ci, v, A.m, A.n, thr=0.1, stream=stream.cuda_stream)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st, _, info = h.solve(f, None, tol=1e-10, maxit=20000, out=x, opts=opts)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                setup_ms = h.info().setup_ms
+                h.close()
+                if rep > 0:
+                    times.append(e0.elapsed_time(e1))
+            xh = x.cpu().numpy()
+            res[name] = {"solve_ms": min(times), "setup_ms": setup_ms, "sweeps": info.sweeps,
+                         "outer": info.outer_iters, "rel_res": info.rel_res, "status": st,
+                         "x_err_vs_xstar": float(np.linalg.norm(xh - s.xstar) / np.linalg.norm(s.xstar)),
+                         "_x": xh}
+        if n == 200_000:
+            st_o, x_o, io = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1, tol=1e-10,
+                                         maxit=20000, check_every=-1)
+            for name in res:
+                res[name]["x_err_vs_fp64_oracle"] = float(np.linalg.norm(res[name]["_x"] - x_o) / np.linalg.norm(x_o))
+        for name in res:
+            res[name].pop("_x")
+        out[f"n{n}"] = res
+    print(json.dumps(out), flush=True)
+
+
+def serving_study(args):
+    """Request loop: Poisson arrivals of independent systems (75 % square
+    random_dominant, 25 % overdetermined m = 2n), n log-uniform in [1e3, 2e5],
+    precision 50/50, tol 1e-8.  First all requests at t = 0 (closed-loop
+    capacity mu), then open-loop Poisson arrivals at 0.8 mu: req/s, p50/p99."""
+    import torch  # noqa: F401  (initialises CUDA for the library)
+
+    import paper_2401_00672_gb300 as obk
+    import synth
+
+    reqs = synth.request_stream(args.requests, rate_per_s=1.0, seed=1004, materialize=True)
+
+    def run(rate):
+        srv = obk.Server(hbm_budget_bytes=150 << 30, max_streams=args.streams)
+        t0 = time.perf_counter()
+        submit_t, done_t, tickets = {}, {}, {}
+        gaps = np.random.default_rng(7).exponential(1.0 / rate, len(reqs)) if rate else np.zeros(len(reqs))
+        arrive = np.cumsum(gaps) - gaps[0]
+        i = 0
+        pending = set()
+        while len(done_t) < len(reqs):
+            now = time.perf_counter() - t0
+            while i < len(reqs) and arrive[i] <= now:
+                r = reqs[i]
+                A = r.system.A
+                opts = obk.Opts(precision=r.precision)
+                tk = srv.submit(A.row_ptr, A.col_idx, A.val, A.m, A.n, r.system.f, tol=1e-8, maxit=20000,
+                                opts=opts)
+                tickets[tk] = i
+                submit_t[i] = time.perf_counter() - t0
+                pending.add(tk)
+                i += 1
+            for tk in list(pending):
+                st, x, info = srv.poll(tk, reqs[tickets[tk]].n)
+                if st != obk.OBK_PENDING:
+                    done_t[tickets[tk]] = time.perf_counter() - t0
+                    pending.discard(tk)
+            time.sleep(0.0005)
+        srv.close()
+        wall = max(done_t.values())
+        lat = np.array([done_t[k] - submit_t[k] for k in done_t])
+        return {"req_per_s": len(reqs) / wall, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3), "wall_s": wall}
+
+    closed = run(None)
+    mu = closed["req_per_s"]
+    opened = run(0.8 * mu)
+    print(json.dumps({"metric": "serving", "requests": len(reqs), "streams": args.streams,
+                      "closed_loop": closed, "open_loop_0.8mu": opened}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -154,7 +257,16 @@ def main():
     ap.add_argument("--workload", default="knn1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision-study", action="store_true", help="FP64 vs FP32+IR to 1e-10 (extra run)")
+    ap.add_argument("--pn", type=int, default=4_000_000, help="n of the precision study")
+    ap.add_argument("--serving", action="store_true", help="request-loop throughput and latency (extra run)")
+    ap.add_argument("--requests", type=int, default=512)
+    ap.add_argument("--streams", type=int, default=8)
     args = ap.parse_args()
+    if args.precision_study:
+        return precision_study(args)
+    if args.serving:
+        return serving_study(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -16,6 +16,8 @@
  * managed memory is used in place, anything else is treated as host memory.
  * A handle or server must not be used from two threads at once.  No call
  * aborts the process; on error a message is available from obk_last_error().
+ * Device memory is taken from a library-owned stream-ordered pool per device;
+ * memory released by obk_destroy stays in that pool for later handles.
  */
 #ifndef OBK_H
 #define OBK_H

@@ -50,12 +50,19 @@ constexpr long long kDefaultSpins = 1LL << 23;
 
 // ---- bounded grid barrier ------------------------------------------------
 //
-// Sense-counting barrier for kernels launched cooperatively (all blocks
-// co-resident).  Every wait is bounded: after `limit` polls the block records
-// kDevTimeout in *err and returns false; callers must then leave the kernel.
-// bar[0] = arrival counter, bar[1] = generation.
+// Barrier for kernels launched cooperatively (all blocks co-resident).
+// Arrival is hierarchical: block b increments sub-counter b % 16 (each on its
+// own 128-byte line); the last arriver of a sub-group increments the top
+// counter; the last of those resets the counters and bumps the generation.
+// The atomics are acquire-release at GPU scope, so every block's writes
+// before the barrier are visible to every block after it.  Every wait is
+// bounded: after `limit` polls the block records kDevTimeout in *err and
+// returns false; callers must then leave the kernel.
+constexpr int kBarrierSub = 16;
+constexpr int kBarrierWords = 64 + 32 * kBarrierSub;  // [0] top, [32] generation, [64 + 32 s] sub s
+
 struct GridBarrier {
-    unsigned int* bar;
+    unsigned int* bar;  // kBarrierWords words, zeroed before the launch
     int* err;
     long long limit;
 };
@@ -68,6 +75,18 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p)
 {
     return *reinterpret_cast<const volatile int*>(p);
 }
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 
 __device__ __forceinline__ bool grid_sync(const GridBarrier& gb)
 {
@@ -76,16 +95,25 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& gb)
     if (threadIdx.x == 0) {
         int ok = 1;
         unsigned nb = gridDim.x * gridDim.y * gridDim.z;
-        unsigned gen = ld_volatile_u32(gb.bar + 1);
-        __threadfence();
-        unsigned arrived = atomicAdd(gb.bar, 1u);
-        if (arrived == nb - 1) {
-            atomicExch(gb.bar, 0u);
-            __threadfence();
-            atomicAdd(gb.bar + 1, 1u);
-        } else {
+        unsigned ngroups = nb < (unsigned)kBarrierSub ? nb : (unsigned)kBarrierSub;
+        unsigned s = blockIdx.x % ngroups;
+        unsigned gsize = (nb - s + ngroups - 1) / ngroups;
+        unsigned* top = gb.bar;
+        unsigned* gen_p = gb.bar + 32;
+        unsigned* sub = gb.bar + 64 + 32 * s;
+        unsigned gen = ld_acquire_gpu(gen_p);
+        bool released = false;
+        if (atom_add_acq_rel_gpu(sub, 1u) == gsize - 1) {
+            *reinterpret_cast<volatile unsigned*>(sub) = 0u;
+            if (atom_add_acq_rel_gpu(top, 1u) == ngroups - 1) {
+                *reinterpret_cast<volatile unsigned*>(top) = 0u;
+                atom_add_acq_rel_gpu(gen_p, 1u);
+                released = true;
+            }
+        }
+        if (!released) {
             long long spins = 0;
-            while (ld_volatile_u32(gb.bar + 1) == gen) {
+            while (ld_acquire_gpu(gen_p) == gen) {
                 if (++spins > gb.limit || ld_volatile_i32(gb.err) != 0) {
                     atomicCAS(gb.err, 0, (int)kDevTimeout);
                     ok = 0;
@@ -94,7 +122,6 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& gb)
                 if (spins > 20000) __nanosleep(32);
             }
         }
-        __threadfence();
         if (ld_volatile_i32(gb.err) != 0) ok = 0;
         s_ok = ok;
     }
@@ -122,7 +149,12 @@ struct DevInfo {
 };
 DevInfo dev_info();
 
-// Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync).
+// Library-owned stream-ordered memory pool of the current device.  Freed
+// blocks stay in the pool (no release threshold), so the many temporary
+// buffers of setup and solve are served without remapping device memory.
+cudaMemPool_t lib_pool();
+
+// Stream-ordered device buffer (pool allocation / cudaFreeAsync).
 template <class T>
 struct DBuf {
     T* p = nullptr;
@@ -136,7 +168,7 @@ struct DBuf {
         s = st;
         n = count;
         if (count) {
-            cudaError_t e = cudaMallocAsync((void**)&p, count * sizeof(T), st);
+            cudaError_t e = cudaMallocFromPoolAsync((void**)&p, count * sizeof(T), lib_pool(), st);
             if (e != cudaSuccess) {
                 p = nullptr;
                 (void)cudaGetLastError();

@@ -486,15 +486,34 @@ __global__ void __launch_bounds__(kCoopBlock) cm_levels(CmParams p)
         }
         if (threadIdx.x == 0) p.bsum[blockIdx.x] = carry;
         if (!grid_sync(p.gb)) return;
-        // P3: exclusive scan of the block totals
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            int64_t run = 0;
-            for (unsigned b = 0; b < gridDim.x; ++b) {
-                int64_t t = p.bsum[b];
-                p.bsum[b] = run;
-                run += t;
+        // P3: exclusive scan of the block totals (block 0, all threads)
+        if (blockIdx.x == 0) {
+            int64_t carry2 = 0;
+            for (unsigned base = 0; base < gridDim.x; base += blockDim.x) {
+                unsigned b = base + threadIdx.x;
+                int64_t v = b < gridDim.x ? p.bsum[b] : 0;
+                int64_t inc = v;
+                for (int o = 1; o < 32; o <<= 1) {
+                    int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += t;
+                }
+                if (lane == 31) wsum[wid] = inc;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int64_t run = 0;
+                    for (int w = 0; w < wpb; ++w) {
+                        int64_t t = wsum[w];
+                        wsum[w] = run;
+                        run += t;
+                    }
+                    s_tot = run;
+                }
+                __syncthreads();
+                if (b < gridDim.x) p.bsum[b] = carry2 + wsum[wid] + inc - v;
+                carry2 += s_tot;
+                __syncthreads();
             }
-            p.bsum[gridDim.x] = run;
+            if (threadIdx.x == 0) p.bsum[gridDim.x] = carry2;
         }
         if (!grid_sync(p.gb)) return;
         // P4: append the children of every frontier vertex in rank order
@@ -628,12 +647,12 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
     DBuf<int32_t> dist(N, st), qa(N, st), qb(N, st), ecc(N, st), cand_r(N, st);
     DBuf<int64_t> cnt4(4, st), nsrc(1, st);
     DBuf<int32_t> nlev(1, st);
-    DBuf<unsigned> bar(2, st);
+    DBuf<unsigned> bar(kBarrierWords, st);
     int bfs_grid = coop_grid((const void*)bfs_levels, kCoopBlock, 0, (int64_t)di.sms * kCoopBlocksPerSm);
     auto run_bfs = [&](const int32_t* sources, int64_t ns) -> int64_t {
         OBK_CUDA(cudaMemsetAsync(dist.p, 0xff, N * sizeof(int32_t), st));
         OBK_CUDA(cudaMemsetAsync(cnt4.p, 0, 4 * sizeof(int64_t), st));
-        OBK_CUDA(cudaMemsetAsync(bar.p, 0, 2 * sizeof(unsigned), st));
+        OBK_CUDA(cudaMemsetAsync(bar.p, 0, kBarrierWords * sizeof(unsigned), st));
         BfsParams bp{N, gp.p, adj_r, sources, ns, dist.p, qa.p, qb.p, cnt4.p, nlev.p,
                      GridBarrier{bar.p, d_err, spin_limit}};
         void* args[] = {&bp};
@@ -722,7 +741,7 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
     int32_t* Q = qa.p;
     OBK_CUDA(cudaMemsetAsync(vis.p, 0xff, N * sizeof(int32_t), st));
     OBK_CUDA(cudaMemsetAsync(claim.p, 0x7f, N * sizeof(int32_t), st));
-    OBK_CUDA(cudaMemsetAsync(bar.p, 0, 2 * sizeof(unsigned), st));
+    OBK_CUDA(cudaMemsetAsync(bar.p, 0, kBarrierWords * sizeof(unsigned), st));
     int cm_grid = coop_grid((const void*)cm_levels, kCoopBlock, 0, (int64_t)di.sms * kCoopBlocksPerSm);
     DBuf<int64_t> bsum(cm_grid + 1, st);
     CmParams cp{N, gp.p, adj_r, roots.p, C, vis.p, claim.p, Q, ccnt.p, bsum.p, nl.p,

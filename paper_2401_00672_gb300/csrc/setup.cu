@@ -244,6 +244,9 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_conflicts(PairParams p)
 {
     __shared__ int32_t skey[kPairWarps][kPairCap];
     __shared__ double sval[kPairWarps][kPairCap];
+    __shared__ int64_t spre[kPairWarps][32];  // incidence prefix of the current 32 entries
+    __shared__ int64_t sq0[kPairWarps][32];   // first column position of each entry
+    __shared__ double sa[kPairWarps][32];     // value of each entry
     int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     unsigned lt = (1u << lane) - 1u;
     int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -266,28 +269,76 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_conflicts(PairParams p)
         uint32_t mask = (uint32_t)cap - 1u;
         for (int64_t t = lane; t < cap; t += 32) { key[t] = kEmpty; val[t] = 0.0; }
         __syncwarp();
-        for (int64_t e = p.rp[i]; e < p.rp[i + 1]; ++e) {
-            int32_t c = p.ci[e];
-            double a = p.v[e];
-            int64_t q0 = p.cptr[c], q1 = p.pos_of[e];  // earlier rows of column c
-            for (int64_t q = q0 + lane; q < q1; q += 32) {
-                int32_t j = p.crow[q];
-                if (p.nsq[j] == 0.0) continue;
-                double prod = __dmul_rn(a, p.cval[q]);
-                uint32_t h = hslot(j, mask);
-                int64_t probes = 0;
-                for (;;) {
-                    int32_t k = key[h];
-                    if (k == j) break;
-                    if (k == kEmpty) {
-                        int32_t old = atomicCAS(key + h, kEmpty, j);
-                        if (old == kEmpty || old == j) break;
+        // The (column, earlier row) incidences of row i, in ascending column
+        // order, are processed 32 at a time: one product per lane, then the
+        // additions into the table in rounds, the r-th round taking each
+        // lane whose row j occurred r times earlier in the chunk.  Every
+        // dot_ij therefore accumulates its products in ascending column order.
+        for (int64_t e0 = p.rp[i]; e0 < p.rp[i + 1]; e0 += 32) {
+            int64_t e = e0 + lane;
+            int64_t cnt = 0, q0 = 0;
+            double a = 0.0;
+            if (e < p.rp[i + 1]) {
+                int32_t c = p.ci[e];
+                a = p.v[e];
+                q0 = p.cptr[c];
+                cnt = p.pos_of[e] - q0;  // earlier rows of column c
+            }
+            int64_t inc = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t;
+            }
+            spre[wl][lane] = inc - cnt;
+            sq0[wl][lane] = q0;
+            sa[wl][lane] = a;
+            int64_t U = __shfl_sync(0xffffffffu, inc, 31);
+            __syncwarp();
+            for (int64_t t0 = 0; t0 < U; t0 += 32) {
+                int64_t t = t0 + lane;
+                bool valid = t < U;
+                int32_t j = -1;
+                double prod = 0.0;
+                if (valid) {
+                    int lo = 0, hi = 31;  // last entry whose incidences start at or before t
+                    while (lo < hi) {
+                        int mid = (lo + hi + 1) >> 1;
+                        if (spre[wl][mid] <= t) lo = mid;
+                        else hi = mid - 1;
                     }
-                    h = (h + 1) & mask;
-                    if (++probes > cap) { h = 0xffffffffu; break; }
+                    int64_t q = sq0[wl][lo] + (t - spre[wl][lo]);
+                    j = p.crow[q];
+                    double w = p.cval[q];
+                    if (p.nsq[j] == 0.0) valid = false;
+                    else prod = __dmul_rn(sa[wl][lo], w);
                 }
-                if (h == 0xffffffffu) { atomicCAS(p.err, 0, (int)kDevOverflow); continue; }
-                val[h] = __dadd_rn(val[h], prod);
+                unsigned peers = __match_any_sync(0xffffffffu, valid ? j : -1 - lane);
+                int rank = __popc(peers & lt);
+                int maxr = __reduce_max_sync(0xffffffffu, valid ? rank : 0);
+                uint32_t h = 0;
+                if (valid && rank == 0) {
+                    h = hslot(j, mask);
+                    int64_t probes = 0;
+                    for (;;) {
+                        int32_t k = key[h];
+                        if (k == j) break;
+                        if (k == kEmpty) {
+                            int32_t old = atomicCAS(key + h, kEmpty, j);
+                            if (old == kEmpty || old == j) break;
+                        }
+                        h = (h + 1) & mask;
+                        if (++probes > cap) { h = 0xffffffffu; break; }
+                    }
+                }
+                h = __shfl_sync(0xffffffffu, h, __ffs(peers) - 1);
+                if (valid && h == 0xffffffffu) {
+                    atomicCAS(p.err, 0, (int)kDevOverflow);
+                    valid = false;
+                }
+                for (int r = 0; r <= maxr; ++r) {
+                    if (valid && rank == r) val[h] = __dadd_rn(val[h], prod);
+                    __syncwarp();
+                }
             }
             __syncwarp();
         }
@@ -372,17 +423,34 @@ __global__ void __launch_bounds__(kBlock) greedy_color(ColorParams p)
             col[i] = -1;
             done = true;
         }
+        // the first kPre earlier conflicting rows are kept in registers; only
+        // their colours are polled
+        constexpr int kPre = 8;
+        int32_t dep[kPre];
+        int n = 0;
+        int64_t o = 0;
+        if (!done) {
+            o = p.conf_off[i];
+            n = p.conf_cnt[i];
+        }
+#pragma unroll
+        for (int t = 0; t < kPre; ++t) dep[t] = t < n ? p.pool[o + t] : -1;
         long long spins = 0;
         while (__any_sync(0xffffffffu, !done)) {
             if (!done) {
-                int64_t o = p.conf_off[i];
-                int n = p.conf_cnt[i];
                 bool ready = true;
                 unsigned long long used = 0;
-                for (int t = 0; t < n; ++t) {
+#pragma unroll
+                for (int t = 0; t < kPre; ++t) {
+                    if (dep[t] < 0) continue;
+                    int32_t cj = col[dep[t]];
+                    if (cj == kUnset) ready = false;
+                    else if (cj < 64) used |= 1ull << cj;
+                }
+                for (int t = kPre; ready && t < n; ++t) {
                     int32_t cj = col[p.pool[o + t]];
-                    if (cj == kUnset) { ready = false; break; }
-                    if (cj < 64) used |= 1ull << cj;
+                    if (cj == kUnset) ready = false;
+                    else if (cj < 64) used |= 1ull << cj;
                 }
                 if (ready) {
                     int32_t g;
@@ -422,12 +490,65 @@ __global__ void max_color(int64_t N, const int32_t* color, int* gmax)
 
 // ---- group layout -------------------------------------------------------------
 
-__global__ void color_keys(int64_t N, const int32_t* color, int32_t G, uint64_t* keys, uint32_t* vals)
+// Row order of the sweep layout: by group, then by row length, then by index
+// (stable sort on (group, length) over rows in index order).  Equal lengths
+// inside a warp keep every lane of every FP64 instruction busy.
+__global__ void color_keys(int64_t N, const int32_t* color, const int64_t* rp, int32_t G, int lbits,
+                           uint64_t* keys, uint32_t* vals)
 {
     GRID_STRIDE(i, N)
     {
-        keys[i] = (uint64_t)(color[i] >= 0 ? color[i] : G);
+        uint64_t g = (uint64_t)(color[i] >= 0 ? color[i] : G);
+        uint64_t len = (uint64_t)(rp[i + 1] - rp[i]);
+        uint64_t lmax = (1ull << lbits) - 1;
+        keys[i] = (g << lbits) | (len < lmax ? len : lmax);
         vals[i] = (uint32_t)i;
+    }
+}
+
+// Segment order inside each group: by length, then by column (stable sort of
+// the (group, column)-ordered segments on (group, length)).
+__global__ void seg_keys(int64_t nseg, const int64_t* seg_ptr, const int64_t* gseg_ptr, int64_t G, int lbits,
+                         uint64_t* keys, uint32_t* vals)
+{
+    GRID_STRIDE(t, nseg)
+    {
+        // group of segment t: gseg_ptr is increasing, binary search
+        int64_t lo = 0, hi = G;
+        while (hi - lo > 1) {
+            int64_t mid = (lo + hi) >> 1;
+            if (gseg_ptr[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        uint64_t len = (uint64_t)(seg_ptr[t + 1] - seg_ptr[t]);
+        uint64_t lmax = (1ull << lbits) - 1;
+        keys[t] = ((uint64_t)lo << lbits) | (len < lmax ? len : lmax);
+        vals[t] = (uint32_t)t;
+    }
+}
+
+__global__ void seg_lengths(int64_t nseg, const uint32_t* order, const int64_t* seg_ptr, int64_t* len)
+{
+    GRID_STRIDE(t, nseg) len[t] = seg_ptr[order[t] + 1] - seg_ptr[order[t]];
+}
+
+// copy the entries of each segment to its new place (one warp per segment)
+template <class T>
+__global__ void seg_move(int64_t nseg, const uint32_t* order, const int64_t* seg_ptr, const int64_t* new_ptr,
+                         const int32_t* seg_col, int32_t* new_col, const int32_t* mrow, const T* mval,
+                         const float* mval32, int32_t* nrow, T* nval, float* nval32)
+{
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = w; t < nseg; t += nw) {
+        int64_t s = order[t], b = seg_ptr[s], e = seg_ptr[s + 1], d = new_ptr[t];
+        if (lane == 0) new_col[t] = seg_col[s];
+        for (int64_t q = lane; q < e - b; q += 32) {
+            nrow[d + q] = mrow[b + q];
+            nval[d + q] = mval[b + q];
+            if (nval32) nval32[d + q] = mval32[b + q];
+        }
     }
 }
 
@@ -660,9 +781,10 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
     // 5. group-major rows
     DBuf<uint64_t> gk(N, st);
     DBuf<uint32_t> gorder(N, st);
-    color_keys<<<grid_for(N), kBlock, 0, st>>>(N, L.group_of.p, G, gk.p, gorder.p);
+    const int lbits = 10;  // row/segment lengths above 1022 share the last class
+    color_keys<<<grid_for(N), kBlock, 0, st>>>(N, L.group_of.p, rp, G, lbits, gk.p, gorder.p);
     OBK_CHECK_LAUNCH();
-    radix_sort_pairs(gk.p, gorder.p, N, bits_for((uint64_t)G), st);
+    radix_sort_pairs(gk.p, gorder.p, N, bits_for((uint64_t)G) + lbits, st);
     gk.release();
     DBuf<int64_t> gcnt(G + 1, st);
     OBK_CUDA(cudaMemsetAsync(gcnt.p, 0, (G + 1) * sizeof(int64_t), st));
@@ -732,6 +854,32 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
         mirror_segments<<<grid_for(M), kBlock, 0, st>>>(M, morder.p, crow.p, col_of.p, L.group_of.p, flag.p,
                                                        fscan.p, L.seg_ptr.p, L.seg_col.p, L.gseg_ptr.p);
         OBK_CHECK_LAUNCH();
+    }
+    // 7. segments of each group ordered by length (then column), entries moved along
+    if (nseg > 1) {
+        DBuf<uint64_t> sk(nseg, st);
+        DBuf<uint32_t> sorder(nseg, st);
+        seg_keys<<<grid_for(nseg), kBlock, 0, st>>>(nseg, L.seg_ptr.p, L.gseg_ptr.p, G, lbits, sk.p, sorder.p);
+        OBK_CHECK_LAUNCH();
+        radix_sort_pairs(sk.p, sorder.p, nseg, bits_for((uint64_t)G) + lbits, st);
+        sk.release();
+        DBuf<int64_t> slen(nseg, st), nptr(nseg + 1, st);
+        seg_lengths<<<grid_for(nseg), kBlock, 0, st>>>(nseg, sorder.p, L.seg_ptr.p, slen.p);
+        OBK_CHECK_LAUNCH();
+        exclusive_scan_i64(slen.p, nptr.p, nseg, st);
+        DBuf<int32_t> ncol(nseg, st), nrow(M, st);
+        DBuf<double> nval(M, st);
+        DBuf<float> nval32;
+        if (want_fp32) nval32.alloc(M, st);
+        seg_move<double><<<grid_for(nseg * 32), kBlock, 0, st>>>(
+            nseg, sorder.p, L.seg_ptr.p, nptr.p, L.seg_col.p, ncol.p, L.mir_row.p, L.mir_val.p,
+            want_fp32 ? L.mir_val32.p : nullptr, nrow.p, nval.p, want_fp32 ? nval32.p : nullptr);
+        OBK_CHECK_LAUNCH();
+        L.seg_ptr = std::move(nptr);
+        L.seg_col = std::move(ncol);
+        L.mir_row = std::move(nrow);
+        L.mir_val = std::move(nval);
+        if (want_fp32) L.mir_val32 = std::move(nval32);
     }
     L.h_gseg_ptr.resize(G + 1);
     OBK_CUDA(cudaMemcpyAsync(L.h_gseg_ptr.data(), L.gseg_ptr.p, (G + 1) * sizeof(int64_t),

@@ -31,7 +31,8 @@ namespace obk {
 namespace {
 
 constexpr int kBlock = 512;       // threads per block of the persistent kernel
-constexpr int kBlocksPerSm = 2;   // co-resident blocks per SM (barrier arrivals = 2 x SMs)
+constexpr int kBlocksPerSm = 2;   // co-resident blocks per SM
+constexpr int kBatch = 8;         // independent loads issued before their uses
 
 struct SweepParams {
     int64_t N, Ngm, G;
@@ -92,6 +93,96 @@ __device__ __forceinline__ T sub_reduce(T v)
     return v;
 }
 
+// ---- exact-length row and segment kernels -------------------------------------
+//
+// A warp-wide FP64 instruction occupies the SM's FP64 pipe for the same time
+// whether 1 or 32 lanes are active, and even when every lane is predicated
+// off.  Rows and column segments are therefore sorted by length inside each
+// group, and the loops below run exactly as many multiply-adds as a row (or
+// segment) has entries: full batches, then a warp-uniform switch on the
+// remainder.  Loads are batched ahead of their uses so that a row costs a few
+// memory round trips, not two per entry.
+
+// acc - sum_{j<B} a[q+j] * xv[ci[q+j]]
+template <int B, class T>
+__device__ __forceinline__ T sub_batch(const int32_t* ci, const T* vals, const T* xv, int64_t q, T acc)
+{
+    int32_t idx[B];
+    T a[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+        idx[j] = ci[q + j];
+        a[j] = vals[q + j];
+    }
+    T xg[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) xg[j] = xv[idx[j]];
+#pragma unroll
+    for (int j = 0; j < B; ++j) acc = fma(-a[j], xg[j], acc);
+    return acc;
+}
+
+// rhs - A_k . xv for row k (one thread)
+template <class T>
+__device__ __forceinline__ T row_residual(const int64_t* rp, const int32_t* ci, const T* vals, const T* xv, int64_t k,
+                                          T rhs)
+{
+    int64_t q = rp[k], e = rp[k + 1];
+    T acc = rhs;
+    for (; q + kBatch <= e; q += kBatch) acc = sub_batch<kBatch, T>(ci, vals, xv, q, acc);
+    switch ((int)(e - q)) {
+        case 7: acc = sub_batch<7, T>(ci, vals, xv, q, acc); break;
+        case 6: acc = sub_batch<6, T>(ci, vals, xv, q, acc); break;
+        case 5: acc = sub_batch<5, T>(ci, vals, xv, q, acc); break;
+        case 4: acc = sub_batch<4, T>(ci, vals, xv, q, acc); break;
+        case 3: acc = sub_batch<3, T>(ci, vals, xv, q, acc); break;
+        case 2: acc = sub_batch<2, T>(ci, vals, xv, q, acc); break;
+        case 1: acc = sub_batch<1, T>(ci, vals, xv, q, acc); break;
+        default: break;
+    }
+    return acc;
+}
+
+// Dot product of one row with xv by a sub-warp of SUB > 1 lanes (long rows):
+// lanes stride by SUB, batched loads, shuffle reduction afterwards.
+template <int SUB, class T>
+__device__ __forceinline__ T row_dot_wide(const int64_t* rp, const int32_t* ci, const T* vals, const T* xv,
+                                          int64_t k, int sub)
+{
+    int64_t b = rp[k], e = rp[k + 1];
+    T acc = 0;
+    for (int64_t q0 = b + sub; q0 < e; q0 += (int64_t)SUB * kBatch) {
+        int32_t idx[kBatch];
+        T a[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            int64_t q = q0 + (int64_t)j * SUB;
+            idx[j] = q < e ? ci[q] : -1;
+            a[j] = q < e ? vals[q] : T(0);
+        }
+        T xg[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) xg[j] = idx[j] >= 0 ? xv[idx[j]] : T(0);
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) acc = fma(a[j], xg[j], acc);
+    }
+    return acc;
+}
+
+// rhs_k - A_k . xv with SUB lanes per row; the result is valid in lane sub == 0
+template <int SUB, class T>
+__device__ __forceinline__ T row_residual_sub(const SweepParams& p, const T* vals, const T* xv, int64_t k, T rhs,
+                                              int sub)
+{
+    if constexpr (SUB == 1) {
+        return row_residual<T>(p.grp_rp, p.grp_ci, vals, xv, k, rhs);
+    } else {
+        T acc = row_dot_wide<SUB, T>(p.grp_rp, p.grp_ci, vals, xv, k, sub);
+        acc = sub_reduce<SUB>(acc);
+        return rhs - acc;
+    }
+}
+
 // phase 1: y_k = (rhs_k - A_k . xv) * inv_k for group-major rows [r0, r1)
 template <int SUB, class T, class TR>
 __device__ __forceinline__ void phase1(const SweepParams& p, int64_t r0, int64_t r1, const T* vals,
@@ -101,15 +192,32 @@ __device__ __forceinline__ void phase1(const SweepParams& p, int64_t r0, int64_t
     int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / SUB;
     int sub = threadIdx.x & (SUB - 1);
     for (int64_t k = r0 + sw; k < r1; k += nsw) {
-        int64_t b = p.grp_rp[k], e = p.grp_rp[k + 1];
-        T acc = 0;
-        for (int64_t q = b + sub; q < e; q += SUB) acc = fma(vals[q], xv[p.grp_ci[q]], acc);
-        acc = sub_reduce<SUB>(acc);
-        if (sub == 0) y[k] = ((T)rhs[k] - acc) * inv[k];
+        T r = row_residual_sub<SUB, T>(p, vals, xv, k, (T)rhs[k], sub);
+        if (sub == 0) y[k] = r * inv[k];
     }
 }
 
-// phase 2: xv_c += sum over the segment's rows of A_kc y_k, segments [s0, s1)
+// xv_c + sum_{j<B} a[q+j] * y[row[q+j]]
+template <int B, class T>
+__device__ __forceinline__ T add_batch(const int32_t* mrow, const T* mval, const T* y, int64_t q, T acc)
+{
+    int32_t r[B];
+    T a[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+        r[j] = mrow[q + j];
+        a[j] = mval[q + j];
+    }
+    T yg[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) yg[j] = y[r[j]];
+#pragma unroll
+    for (int j = 0; j < B; ++j) acc = fma(a[j], yg[j], acc);
+    return acc;
+}
+
+// phase 2: xv_c += sum over the segment's rows (ascending) of A_kc y_k, one
+// thread per (group, column) segment, segments [s0, s1)
 template <class T>
 __device__ __forceinline__ void phase2(const SweepParams& p, int64_t s0, int64_t s1, const T* mval,
                                        const T* y, T* xv)
@@ -117,10 +225,17 @@ __device__ __forceinline__ void phase2(const SweepParams& p, int64_t s0, int64_t
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t nth = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = s0 + tid; t < s1; t += nth) {
-        int64_t b = p.seg_ptr[t], e = p.seg_ptr[t + 1];
-        T acc = 0;
-        for (int64_t q = b; q < e; ++q) acc = fma(mval[q], y[p.mir_row[q]], acc);
-        xv[p.seg_col[t]] += acc;
+        int64_t q = p.seg_ptr[t], e = p.seg_ptr[t + 1];
+        int32_t c = p.seg_col[t];
+        T acc = xv[c];
+        for (; q + 4 <= e; q += 4) acc = add_batch<4, T>(p.mir_row, mval, y, q, acc);
+        switch ((int)(e - q)) {
+            case 3: acc = add_batch<3, T>(p.mir_row, mval, y, q, acc); break;
+            case 2: acc = add_batch<2, T>(p.mir_row, mval, y, q, acc); break;
+            case 1: acc = add_batch<1, T>(p.mir_row, mval, y, q, acc); break;
+            default: break;
+        }
+        xv[c] = acc;
     }
 }
 
@@ -150,12 +265,8 @@ __device__ void residual_partial(const SweepParams& p, bool store_r)
     int sub = threadIdx.x & (SUB - 1);
     double local = 0.0;
     for (int64_t k = sw; k < p.Ngm; k += nsw) {
-        int64_t b = p.grp_rp[k], e = p.grp_rp[k + 1];
-        double acc = 0.0;
-        for (int64_t q = b + sub; q < e; q += SUB) acc = fma(p.grp_v[q], p.x[p.grp_ci[q]], acc);
-        acc = sub_reduce<SUB>(acc);
+        double r = row_residual_sub<SUB, double>(p, p.grp_v, p.x, k, p.f[k], sub);
         if (sub == 0) {
-            double r = p.f[k] - acc;
             if (store_r) p.r64[k] = r;
             local = fma(r, r, local);
         }
@@ -164,11 +275,15 @@ __device__ void residual_partial(const SweepParams& p, bool store_r)
     if (threadIdx.x == 0) p.partial[blockIdx.x] = s;
 }
 
-// block 0 thread 0: total of the partials in block order
+// Total of the per-block partial sums, computed by block 0 with a fixed
+// reduction tree (thread t sums partials t, t + blockDim, ... in order, then
+// the block sum), so the result is the same on every run for a given grid.
+// Called by every thread of block 0; the total is returned to thread 0.
 __device__ double total_partials(const SweepParams& p)
 {
     double s = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) s += p.partial[b];
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += p.partial[b];
+    s = block_sum(s);
     return s + p.zero_f2;
 }
 
@@ -201,8 +316,9 @@ __global__ void __launch_bounds__(kBlock, kBlocksPerSm) obk_solve_kernel(SweepPa
     // initial residual
     residual_partial<SUB>(p, p.precision == 1);
     if (!grid_sync(p.gb)) return;
+    double tot0 = blockIdx.x == 0 ? total_partials(p) : 0.0;
     if (lead) {
-        double tot = total_partials(p);
+        double tot = tot0;
         double rr = p.fnorm > 0.0 ? sqrt(tot) / p.fnorm : sqrt(tot);
         p.ctrl[0] = rr;
         p.ctrl[1] = sqrt(tot);
@@ -237,8 +353,9 @@ __global__ void __launch_bounds__(kBlock, kBlocksPerSm) obk_solve_kernel(SweepPa
             if (check) {
                 residual_partial<SUB>(p, false);
                 if (!grid_sync(p.gb)) return;
+                double totc = blockIdx.x == 0 ? total_partials(p) : 0.0;
                 if (lead) {
-                    double tot = total_partials(p);
+                    double tot = totc;
                     double rr = p.fnorm > 0.0 ? sqrt(tot) / p.fnorm : sqrt(tot);
                     p.ctrl[0] = rr;
                     vout[7] += 1;
@@ -293,8 +410,9 @@ __global__ void __launch_bounds__(kBlock, kBlocksPerSm) obk_solve_kernel(SweepPa
         if (!grid_sync(p.gb)) return;
         residual_partial<SUB>(p, true);
         if (!grid_sync(p.gb)) return;
+        double totr = blockIdx.x == 0 ? total_partials(p) : 0.0;
         if (lead) {
-            double tot = total_partials(p);
+            double tot = totr;
             double rr = p.fnorm > 0.0 ? sqrt(tot) / p.fnorm : sqrt(tot);
             p.ctrl[0] = rr;
             p.ctrl[1] = sqrt(tot);
@@ -343,12 +461,14 @@ void launch_solve(SweepParams& p, cudaStream_t st)
 
 }  // namespace
 
-// Lanes per row in phase 1.  FP64 issue is the scarce resource on this GPU
-// (a warp-wide FP64 instruction occupies the SM's FP64 pipe for many cycles),
-// so short rows get one or two lanes and no shuffle reduction.
+// Lanes per row in phase 1.  FP64 issue is scarce on this GPU (a warp-wide
+// FP64 instruction occupies the FP64 pipe for the same time whatever the
+// number of active lanes), so rows get one or two lanes and at most one
+// shuffle step; two lanes per row measured fastest for rows of ~15 entries
+// (twice as many independent loads in flight per row).
 int choose_sub(double avg_row)
 {
-    if (avg_row <= 24) return 1;
+    if (avg_row <= 6) return 1;
     if (avg_row <= 64) return 2;
     if (avg_row <= 160) return 8;
     return 32;
@@ -360,7 +480,7 @@ SolveResult run_solve(const SweepLayout& L, const double* f_gm, double fnorm2, d
     SolveResult res;
     DBuf<double> y(std::max<int64_t>(L.Ngm, 1), st), ctrl(16, st);
     DBuf<int64_t> out(8, st);
-    DBuf<unsigned> bar(2, st);
+    DBuf<unsigned> bar(kBarrierWords, st);
     DBuf<double> r64;
     DBuf<float> b32, y32, d32;
     if (a.precision == 1) {
@@ -372,7 +492,7 @@ SolveResult run_solve(const SweepLayout& L, const double* f_gm, double fnorm2, d
     }
     OBK_CUDA(cudaMemsetAsync(ctrl.p, 0, 16 * sizeof(double), st));
     OBK_CUDA(cudaMemsetAsync(out.p, 0, 8 * sizeof(int64_t), st));
-    OBK_CUDA(cudaMemsetAsync(bar.p, 0, 2 * sizeof(unsigned), st));
+    OBK_CUDA(cudaMemsetAsync(bar.p, 0, kBarrierWords * sizeof(unsigned), st));
     OBK_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
     SweepParams p{};
     p.N = L.N;
