@@ -91,6 +91,10 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p)
 __device__ __forceinline__ bool grid_sync(const GridBarrier& gb)
 {
     __shared__ int s_ok;
+    if (gridDim.x * gridDim.y * gridDim.z == 1) {  // a one-block grid needs only the block barrier
+        __syncthreads();
+        return true;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;

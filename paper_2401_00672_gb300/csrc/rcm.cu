@@ -27,6 +27,7 @@
 //     queue order exactly.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -648,7 +649,10 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
     DBuf<int64_t> cnt4(4, st), nsrc(1, st);
     DBuf<int32_t> nlev(1, st);
     DBuf<unsigned> bar(kBarrierWords, st);
-    int bfs_grid = coop_grid((const void*)bfs_levels, kCoopBlock, 0, (int64_t)di.sms * kCoopBlocksPerSm);
+    // grids scale with the problem (one block per 2K vertices, at most two per
+    // SM) so that small systems leave the rest of the GPU to other requests
+    int64_t want = std::min<int64_t>((int64_t)di.sms * kCoopBlocksPerSm, ceil_div(N, 2048));
+    int bfs_grid = coop_grid((const void*)bfs_levels, kCoopBlock, 0, want);
     auto run_bfs = [&](const int32_t* sources, int64_t ns) -> int64_t {
         OBK_CUDA(cudaMemsetAsync(dist.p, 0xff, N * sizeof(int32_t), st));
         OBK_CUDA(cudaMemsetAsync(cnt4.p, 0, 4 * sizeof(int64_t), st));
@@ -742,7 +746,7 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
     OBK_CUDA(cudaMemsetAsync(vis.p, 0xff, N * sizeof(int32_t), st));
     OBK_CUDA(cudaMemsetAsync(claim.p, 0x7f, N * sizeof(int32_t), st));
     OBK_CUDA(cudaMemsetAsync(bar.p, 0, kBarrierWords * sizeof(unsigned), st));
-    int cm_grid = coop_grid((const void*)cm_levels, kCoopBlock, 0, (int64_t)di.sms * kCoopBlocksPerSm);
+    int cm_grid = coop_grid((const void*)cm_levels, kCoopBlock, 0, want);
     DBuf<int64_t> bsum(cm_grid + 1, st);
     CmParams cp{N, gp.p, adj_r, roots.p, C, vis.p, claim.p, Q, ccnt.p, bsum.p, nl.p,
                 GridBarrier{bar.p, d_err, spin_limit}};

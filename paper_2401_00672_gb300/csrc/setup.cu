@@ -764,7 +764,7 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
     L.group_of.alloc(N, st);
     OBK_CUDA(cudaMemsetAsync(L.group_of.p, 0x80, N * sizeof(int32_t), st));  // every entry = kUnset
     ColorParams cp{N, L.nsq.p, conf_cnt.p, conf_off.p, pool.p, L.group_of.p, d_err, spin_limit};
-    int cgrid = coop_grid((const void*)greedy_color, kBlock, 0, ceil_div(N, kBlock));
+    int cgrid = coop_grid((const void*)greedy_color, kBlock, 0, ceil_div(N, (int64_t)kBlock * 4));
     void* args[] = {&cp};
     OBK_COOP_LAUNCH(greedy_color, cgrid, kBlock, args, st);
     if (read_scalar(d_err, st) != 0) throw Error{-4, "bounded wait expired in greedy grouping"};

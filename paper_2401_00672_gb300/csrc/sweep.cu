@@ -451,7 +451,10 @@ void launch_solve(SweepParams& p, cudaStream_t st)
 {
     DevInfo di = dev_info();
     const void* k = (const void*)obk_solve_kernel<SUB>;
-    int grid = coop_grid(k, kBlock, 0, (int64_t)di.sms * kBlocksPerSm);
+    // one block per 2K grouped rows, at most kBlocksPerSm per SM: small systems
+    // take a few SMs and leave the others to concurrent requests
+    int64_t want = std::min<int64_t>((int64_t)di.sms * kBlocksPerSm, ceil_div(std::max<int64_t>(p.Ngm, 1), 2048));
+    int grid = coop_grid(k, kBlock, 0, want);
     DBuf<double> partial(grid, st);
     p.partial = partial.p;
     void* args[] = {&p};

@@ -251,15 +251,16 @@ def test_invalid_inputs(obk):
 
 
 def test_bounded_wait_times_out_and_context_survives(obk):
-    # a wait limit of a few polls cannot cover the grid barrier: the kernel must
-    # give up, report OBK_ERR_TIMEOUT, and leave the context usable
-    s, _ = _case("random_dominant_2000")
+    # a wait limit of a few polls cannot cover the grid barrier of a multi-block
+    # sweep: the kernel must give up, report OBK_ERR_TIMEOUT, and leave the
+    # context usable (a one-block grid has no grid barrier, so a larger system)
+    s, _ = _case("knn_30000")
     A = s.A
     with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n) as h:
         with pytest.raises(obk.ObkError) as e:
             h.solve(s.f, tol=1e-8, maxit=50, opts=obk.Opts(timeout_spins=1))
         assert e.value.status == obk.OBK_ERR_TIMEOUT
-        st, x, info = h.solve(s.f, tol=1e-8, maxit=500)
+        st, x, info = h.solve(s.f, tol=1e-8, maxit=5000)
         assert st == obk.OBK_OK
 
 
