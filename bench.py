@@ -64,15 +64,23 @@ def workload(name: str, rank: int):
     import synth
 
     if name == "knn1m":
-        s = synth.knn_dominant(1_000_000, 12, seed=1001 + 100 * rank)
+        s = synth.knn_dominant(1_000_000, 12, seed=replica_seed(1001, rank))
         return s, dict(workload="knn_n1e6_12nn_fp64", n=1_000_000, knn=12, diag_factor=1.2, thr=0.1,
                        tol=1e-8, precision="fp64")
     if name == "dominant2000":
-        s = synth.random_dominant(2000, 7, seed=1000 + 100 * rank)
+        s = synth.random_dominant(2000, 7, seed=replica_seed(1000, rank))
         return s, dict(workload="random_dominant_n2000_fp64", n=2000, thr=0.1, tol=1e-8, precision="fp64")
     if name == "knn200k":
-        s = synth.knn_dominant(200_000, 12, seed=1001 + 100 * rank)
+        s = synth.knn_dominant(200_000, 12, seed=replica_seed(1001, rank))
         return s, dict(workload="knn_n2e5_12nn_fp64", n=200_000, knn=12, thr=0.1, tol=1e-8, precision="fp64")
+    if name == "rect800k":
+        s = synth.rect_random(800_000, 200_000, 10, seed=replica_seed(1002, rank))
+        return s, dict(workload="rect_m8e5_n2e5_10nnz_fp64", m=800_000, n=200_000, nnz_per_row=10, thr=0.1,
+                       tol=1e-8, precision="fp64", variant="consistent (SOBK, Algorithm 5)")
+    if name == "rect800k_noisy":
+        s = synth.rect_random(800_000, 200_000, 10, seed=replica_seed(1002, rank), noise=1e-3)
+        return s, dict(workload="rect_m8e5_n2e5_10nnz_fp64_noise1e-3", m=800_000, n=200_000, nnz_per_row=10,
+                       thr=0.1, tol=1e-8, precision="fp64", variant="inconsistent, stops on stagnation")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -127,6 +135,22 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """Largest value over all ranks (the job's time is its slowest rank)."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(base: int, rank: int) -> int:
+    """Seed of rank's independent system: replicas share no data."""
+    return base + 100 * rank
 
 
 def peaks():
@@ -319,7 +343,8 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     tol = cfg["tol"]
 
-    solve_opts = obk.Opts(check_every=-1)  # adaptive residual-check schedule
+    # adaptive residual-check schedule; stagnation stop for the inconsistent system
+    solve_opts = obk.Opts(check_every=-1, stagnation=1e-12 if "noisy" in args.workload else 0.0)
 
     def step():
         h = obk.Handle(rp, ci, v, A.m, A.n, thr=cfg["thr"], stream=stream.cuda_stream)
@@ -352,11 +377,7 @@ def main():
     torch.cuda.synchronize()
     launches = obk.kernel_launches() - launches0
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, dev)
     st, info = infos[-1]
     xh = x.cpu().numpy()
     err_xstar = float(np.linalg.norm(xh - s.xstar) / np.linalg.norm(s.xstar))
@@ -437,11 +458,7 @@ def main():
             step_host()
         e1.record(stream)
         torch.cuda.synchronize()
-        ems = e0.elapsed_time(e1) / k2
-        if dist is not None:
-            t = torch.tensor([ems], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(e0.elapsed_time(e1) / k2, dist, dev)
         h2d = A.row_ptr.nbytes + A.col_idx.nbytes + A.val.nbytes + s.f.nbytes
         e2e = {"value": ems / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(A.n * 8), "steps": k2}

@@ -175,6 +175,42 @@ OBK_API obk_status obk_residual_noalloc(const int64_t* row_ptr, const int32_t* c
                                         int64_t m, int64_t n, const double* f, const double* x,
                                         double* rel_res, void* stream);
 
+/* Solve `count` prepared systems in one kernel launch, one thread block per
+ * system with x and y in shared memory: for many small systems (the request
+ * loop uses it).  hs[i] are handles of the current device; f[i] (m_i values),
+ * x0[i] (n_i values or NULL) and x_out[i] (n_i values) must be device memory.
+ * Every system must satisfy (N + 2 * grouped rows) * 8 bytes <= the device's
+ * shared memory per block (about N <= 9,000 on GB300), else OBK_ERR_INVALID.
+ * Runs FP64 sweeps (opts->precision must be 0); check_every and stagnation
+ * apply as in obk_solve_ex.  status[i] (and info[i] when not NULL) receive
+ * each system's result; the call returns OBK_OK when all were solved
+ * (converged or not).  Work is issued on hs[0]'s stream and waited for. */
+OBK_API obk_status obk_solve_batch(obk_handle* const* hs, int32_t count, const obk_opts* opts,
+                                   const double* const* f, const double* const* x0, double tol,
+                                   int64_t maxit, double* const* x_out, obk_info* info,
+                                   obk_status* status);
+
+/* Largest N (= max(m, n)) obk_solve_batch accepts on the current device for a
+ * system whose rows all take part (no all-zero rows). */
+OBK_API int64_t obk_batch_max_n(void);
+
+/* Result of obk_autotune. */
+typedef struct {
+    int32_t rows_per_warp;       /* chosen setting (1, 2, 4, 8, 16 or 32) */
+    int32_t reserved;
+    double sweep_ms;             /* device time of one sweep with it */
+    double candidate_ms[6];      /* sweep time for rows_per_warp 32, 16, 8, 4, 2, 1 (0 if skipped) */
+} obk_tune;
+
+/* Autotuner of the sweep kernel for a prepared system: times a few sweeps (on
+ * zero vectors, so the handle's results are unaffected) for each rows-per-warp
+ * setting, keeps the fastest for later solves of h with opts.rows_per_warp = 0
+ * and records it in a process-wide table keyed by (device, size class, mean
+ * row length, precision) that other handles of the same shape use until they
+ * are tuned themselves.  precision: 0 (FP64 sweeps) or 1 (FP32 inner sweeps).
+ * out may be NULL.  Errors: OBK_ERR_INVALID, OBK_ERR_TIMEOUT, OBK_ERR_CUDA. */
+OBK_API obk_status obk_autotune(obk_handle* h, int32_t precision, obk_tune* out);
+
 /* Release every resource of h (NULL is ignored). */
 OBK_API void obk_destroy(obk_handle* h);
 

@@ -26,7 +26,8 @@ EXPORTS = [
     "obk_create", "obk_create_on_stream", "obk_solve", "obk_solve_ex", "obk_get_dims", "obk_get_perm",
     "obk_get_groups", "obk_get_row_norms", "obk_get_info", "obk_destroy", "obk_server_create",
     "obk_submit", "obk_poll", "obk_cancel", "obk_server_destroy", "obk_last_error", "obk_version",
-    "obk_kernel_launches", "obk_residual", "obk_residual_noalloc",
+    "obk_kernel_launches", "obk_residual", "obk_residual_noalloc", "obk_autotune", "obk_solve_batch",
+    "obk_batch_max_n",
 ]
 
 
@@ -47,6 +48,11 @@ class Opts(ctypes.Structure):
                 ("inner_sweeps", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("stagnation", ctypes.c_double), ("timeout_spins", ctypes.c_int64),
                 ("rows_per_warp", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class _Tune(ctypes.Structure):
+    _fields_ = [("rows_per_warp", ctypes.c_int32), ("reserved", ctypes.c_int32), ("sweep_ms", ctypes.c_double),
+                ("candidate_ms", ctypes.c_double * 6)]
 
 
 class _Info(ctypes.Structure):
@@ -102,6 +108,9 @@ def _load() -> ctypes.CDLL:
         "obk_kernel_launches": ([], ctypes.c_int64),
         "obk_residual": ([vp, i64, i64, vp, vp, vp], ctypes.c_int),
         "obk_residual_noalloc": ([vp, vp, vp, i64, i64, vp, vp, vp, vp], ctypes.c_int),
+        "obk_autotune": ([vp, i32, vp], ctypes.c_int),
+        "obk_solve_batch": ([vp, i32, vp, vp, vp, dbl, i64, vp, vp, vp], ctypes.c_int),
+        "obk_batch_max_n": ([], ctypes.c_int64),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -176,6 +185,13 @@ class Handle:
         _check(rc, "obk_solve")
         return rc, ko, _info(info)
 
+    def autotune(self, precision: int = 0) -> dict:
+        """obk_autotune: time the rows-per-warp settings, keep the fastest."""
+        t = _Tune()
+        _check(lib.obk_autotune(self._h, int(precision), ctypes.byref(t)), "obk_autotune")
+        return {"rows_per_warp": t.rows_per_warp, "sweep_ms": t.sweep_ms,
+                "candidate_ms": dict(zip((32, 16, 8, 4, 2, 1), list(t.candidate_ms)))}
+
     def _get(self, fn, dtype):
         a = np.empty(self.N, dtype)
         _check(fn(self._h, a.ctypes.data_as(ctypes.c_void_p)), fn.__name__)
@@ -239,6 +255,23 @@ def residual_noalloc(row_ptr, col_idx, val, m, n, f, x, out, stream=None) -> int
         ptrs.append(p)
     return _check(lib.obk_residual_noalloc(ptrs[0], ptrs[1], ptrs[2], int(m), int(n), ptrs[3], ptrs[4], ptrs[5],
                                            ctypes.c_void_p(stream) if stream else None), "obk_residual_noalloc")
+
+
+def solve_batch(handles, fs, outs, x0s=None, tol=1e-8, maxit=1000, opts=None):
+    """obk_solve_batch: one launch for several prepared systems (device tensors).
+    Returns (statuses, infos)."""
+    n = len(handles)
+    H = (ctypes.c_void_p * n)(*[h._h.value for h in handles])
+    F = (ctypes.c_void_p * n)(*[_ptr(a, np.float64)[0].value for a in fs])
+    X = (ctypes.c_void_p * n)(*[_ptr(a, np.float64)[0].value for a in outs])
+    X0 = None
+    if x0s is not None:
+        X0 = (ctypes.c_void_p * n)(*[(_ptr(a, np.float64)[0].value if a is not None else None) for a in x0s])
+    infos = (_Info * n)()
+    sts = (ctypes.c_int * n)()
+    _check(lib.obk_solve_batch(H, n, ctypes.byref(opts) if opts is not None else None, F, X0, float(tol), int(maxit),
+                               X, infos, sts), "obk_solve_batch")
+    return list(sts), [_info(i) for i in infos]
 
 
 def solve(row_ptr, col_idx, val, m, n, f, x0=None, thr=0.1, tol=1e-8, maxit=1000, opts=None):

@@ -8,11 +8,14 @@
 #include <atomic>
 #include <chrono>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
 #include "../../include/obk.h"
+#include "batch.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -277,7 +280,32 @@ struct obk_handle {
     SweepLayout L;
     obk_info info{};
     RcmStats rcm{};
+    int tuned_sub[2] = {0, 0};  // lanes per row chosen by obk_autotune (0 = not tuned)
 };
+
+namespace {
+// Process-wide autotuning table: (device, log2 size class, mean row length
+// rounded, precision) -> lanes per row.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tune;
+
+std::tuple<int, int, int, int> tune_key(const obk_handle* h, int precision)
+{
+    int szc = 0;
+    while ((int64_t(1) << szc) < h->L.Ngm) ++szc;
+    int avg = h->L.Ngm ? (int)((double)h->L.nnz_gm / (double)h->L.Ngm + 0.5) : 0;
+    return {h->device, szc, avg, precision};
+}
+
+int tuned_or_rule(const obk_handle* h, int precision)
+{
+    if (h->tuned_sub[precision]) return h->tuned_sub[precision];
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tune_key(h, precision));
+    if (it != g_tune.end()) return it->second;
+    return 0;  // the kernel's fixed rule
+}
+}  // namespace
 
 static obk_status fail(const Error& e)
 {
@@ -448,7 +476,7 @@ obk_status obk_solve_ex(obk_handle* h, const obk_opts* opts, const double* f, co
     a.tol = tol;
     a.maxit = maxit;
     a.spin_limit = o.timeout_spins > 0 ? o.timeout_spins : kDefaultSpins;
-    a.sub = o.rows_per_warp > 0 ? 32 / o.rows_per_warp : 0;
+    a.sub = o.rows_per_warp > 0 ? 32 / o.rows_per_warp : tuned_or_rule(h, o.precision);
     SolveResult r = run_solve(h->L, fgm.p, fnorm2, zero_f2, xt.p, a, h->err.p, st);
     // x = P^T x~, then x^(1:n)
     double* xo = x_out;
@@ -477,6 +505,117 @@ obk_status obk_solve(obk_handle* h, const double* f, const double* x0, double to
                      obk_info* info)
 {
     return obk_solve_ex(h, nullptr, f, x0, tol, maxit, x_out, info);
+}
+
+}  // extern "C"
+
+namespace obk {
+bool batch_eligible(const obk_handle* h)
+{
+    return h && batch_smem_bytes(h->N, h->L.Ngm) <= batch_smem_limit();
+}
+}  // namespace obk
+
+extern "C" {
+
+int64_t obk_batch_max_n(void)
+{
+    try {
+        return (int64_t)(batch_smem_limit() / (3 * sizeof(double)));
+    } catch (...) {
+        return 0;
+    }
+}
+
+obk_status obk_solve_batch(obk_handle* const* hs, int32_t count, const obk_opts* opts, const double* const* f,
+                           const double* const* x0, double tol, int64_t maxit, double* const* x_out,
+                           obk_info* info, obk_status* status)
+{
+    OBK_API_BEGIN
+    set_last_error("");
+    if (!hs || count < 0 || !f || !x_out || !status) throw Error{-1, "NULL argument"};
+    if (count == 0) return OBK_OK;
+    if (!(tol > 0.0) || maxit < 1) throw Error{-1, "tol must be > 0 and maxit >= 1"};
+    obk_opts o{};
+    if (opts) o = *opts;
+    if (o.precision != 0) throw Error{-1, "batched solves run FP64 sweeps (precision 0)"};
+    if (o.check_every < -1) throw Error{-1, "check_every must be >= -1"};
+    int dev = hs[0] ? hs[0]->device : -1;
+    OBK_CUDA(cudaSetDevice(dev));
+    size_t limit = batch_smem_limit(), smem = 0;
+    std::vector<BatchSystem> sys((size_t)count);
+    cudaStream_t st = hs[0]->st;
+    DBuf<double> res(3 * (size_t)count, st);
+    for (int32_t i = 0; i < count; ++i) {
+        const obk_handle* h = hs[i];
+        if (!h || h->device != dev) throw Error{-1, "every handle must be non-NULL and on one device"};
+        if (!f[i] || !x_out[i] || !is_device_ptr(f[i]) || !is_device_ptr(x_out[i]) ||
+            (x0 && x0[i] && !is_device_ptr(x0[i])))
+            throw Error{-1, "f, x0 and x_out of a batch must be device memory"};
+        size_t need = batch_smem_bytes(h->N, h->L.Ngm);
+        if (need > limit) throw Error{-1, "system " + std::to_string(i) + " needs more shared memory than a block has"};
+        smem = std::max(smem, need);
+        BatchSystem& d = sys[(size_t)i];
+        d.m = h->m; d.n = h->n; d.N = h->N; d.Ngm = h->L.Ngm; d.G = h->L.G; d.n_zero = h->n_zero;
+        d.perm = h->perm.p; d.src_gm = h->src_gm.p; d.zero_src = h->zero_src.p;
+        d.gptr = h->L.gptr.p; d.gseg_ptr = h->L.gseg_ptr.p; d.grp_rp = h->L.grp_rp.p; d.grp_ci = h->L.grp_ci.p;
+        d.grp_v = h->L.grp_v.p; d.grp_inv = h->L.grp_inv.p; d.seg_ptr = h->L.seg_ptr.p; d.seg_col = h->L.seg_col.p;
+        d.mir_row = h->L.mir_row.p; d.mir_val = h->L.mir_val.p;
+        d.f = f[i]; d.x0 = x0 ? x0[i] : nullptr; d.x_out = x_out[i];
+        d.tol = tol; d.stagnation = o.stagnation; d.maxit = maxit;
+        d.check_every = o.check_every == 0 ? 1 : o.check_every;
+        d.result = res.p + 3 * (size_t)i;
+    }
+    Timer tm(st);
+    DBuf<BatchSystem> dsys((size_t)count, st);
+    OBK_CUDA(cudaMemcpyAsync(dsys.p, sys.data(), sys.size() * sizeof(BatchSystem), cudaMemcpyHostToDevice, st));
+    launch_batch(dsys.p, count, smem, st);
+    std::vector<double> hres(3 * (size_t)count);
+    OBK_CUDA(cudaMemcpyAsync(hres.data(), res.p, hres.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    double ms = tm.stop_ms();
+    OBK_CUDA(cudaStreamSynchronize(st));
+    for (int32_t i = 0; i < count; ++i) {
+        status[i] = hres[3 * (size_t)i] == 0.0 ? OBK_OK : OBK_NOT_CONVERGED;
+        if (info) {
+            info[i] = hs[i]->info;
+            info[i].sweeps = (int64_t)hres[3 * (size_t)i + 1];
+            info[i].rel_res = hres[3 * (size_t)i + 2];
+            info[i].solve_ms = ms;
+            info[i].status = status[i];
+        }
+    }
+    return OBK_OK;
+    OBK_API_END
+}
+
+obk_status obk_autotune(obk_handle* h, int32_t precision, obk_tune* out)
+{
+    OBK_API_BEGIN
+    set_last_error("");
+    if (!h || (precision != 0 && precision != 1)) throw Error{-1, "handle NULL or precision not 0/1"};
+    OBK_CUDA(cudaSetDevice(h->device));
+    obk_tune t{};
+    const int rpw[6] = {32, 16, 8, 4, 2, 1};
+    double best = 1e300;
+    int best_rpw = 16;
+    for (int k = 0; k < 6; ++k) {
+        int sub = 32 / rpw[k];
+        double avg = h->L.Ngm ? (double)h->L.nnz_gm / (double)h->L.Ngm : 1.0;
+        if (sub > 2 * avg + 2) continue;  // more lanes than entries: skip
+        double ms = time_sweep(h->L, sub, precision, h->err.p, h->st);
+        t.candidate_ms[k] = ms;
+        if (ms < best) { best = ms; best_rpw = rpw[k]; }
+    }
+    t.rows_per_warp = best_rpw;
+    t.sweep_ms = best;
+    h->tuned_sub[precision] = 32 / best_rpw;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[tune_key(h, precision)] = 32 / best_rpw;
+    }
+    if (out) *out = t;
+    return OBK_OK;
+    OBK_API_END
 }
 
 obk_status obk_get_dims(const obk_handle* h, int64_t* N, int64_t* nnz, int64_t* G)

@@ -30,6 +30,9 @@ void validate_csr(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci, co
 
 int64_t half_bandwidth(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, cudaStream_t st);
 
+// Longest segment max_i (ptr[i+1] - ptr[i]) of a pointer array of n segments.
+int64_t max_segment_length(int64_t n, const int64_t* ptr, cudaStream_t st);
+
 // A~ = P A P^T with sorted columns.
 void permute_csr(int64_t N, const int64_t* rp, const int32_t* ci, const double* v, int64_t nnz,
                  const int32_t* perm, int32_t* iperm, int64_t* rp_t, int32_t* ci_t, double* v_t,
@@ -93,6 +96,13 @@ struct SolveResult {
     double rel_res = 0.0;
     double sweep_ms = 0.0;
 };
+
+// Device time (ms) of one sweep with `sub` lanes per row (0 = default rule),
+// measured on zero vectors as the difference of 2- and 8-sweep solves.
+double time_sweep(const SweepLayout& L, int sub, int precision, int* d_err, cudaStream_t st);
+
+// Lanes per row chosen by the fixed rule from the mean row length.
+int choose_sub(double avg_row);
 
 // x (N, permuted order) is updated in place; f_gm (Ngm) is f in group-major
 // order; fnorm2 = ||f~||^2 and zero_f2 = sum of f_i^2 over all-zero rows.

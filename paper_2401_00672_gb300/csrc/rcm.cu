@@ -95,13 +95,21 @@ __global__ void merge_sym(int64_t N, const int64_t* rp, const int32_t* ci, const
 
 // ---- ranks in (deg, index) order ---------------------------------------------
 
-__global__ void deg_keys(int64_t N, const int64_t* gp, int bN, uint64_t* keys, uint32_t* vals)
+__global__ void deg_keys(int64_t N, const int64_t* gp, uint64_t* keys, uint32_t* vals, unsigned long long* dmax)
 {
+    unsigned long long mx = 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
          v += (int64_t)gridDim.x * blockDim.x) {
-        keys[v] = ((uint64_t)(gp[v + 1] - gp[v]) << bN) | (uint64_t)v;
+        uint64_t d = (uint64_t)(gp[v + 1] - gp[v]);
+        keys[v] = d;
         vals[v] = (uint32_t)v;
+        mx = d > mx ? d : mx;
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = t > mx ? t : mx;
+    }
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(dmax, mx);
 }
 
 __global__ void rank_of(int64_t N, const uint32_t* by_rank, int32_t* r)
@@ -262,10 +270,17 @@ struct BfsParams {
     GridBarrier gb;
 };
 
-// One warp per frontier vertex, lanes over its neighbours; newly reached
-// vertices are appended with one atomic per warp and chunk.
+// One warp per frontier vertex, lanes over its neighbours.  Newly reached
+// vertices are collected per block in shared memory and appended to the next
+// frontier with one global atomic per block and level (direct appends when the
+// block buffer is full).
+constexpr int kBfsBuf = 2048;
+
 __global__ void __launch_bounds__(kCoopBlock) bfs_levels(BfsParams p)
 {
+    __shared__ int32_t sbuf[kBfsBuf];
+    __shared__ int s_cnt;
+    __shared__ long long s_base;
     int lane = threadIdx.x & 31;
     unsigned lt = (1u << lane) - 1u;
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -288,6 +303,8 @@ __global__ void __launch_bounds__(kCoopBlock) bfs_levels(BfsParams p)
             if (L > 0) p.cnt[3] += ncur;
         }
         int64_t* cnext = p.cnt + ((L + 1) % 3);
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
         for (int64_t k = gw; k < ncur; k += nw) {
             int32_t u = cur[k];
             int64_t b = p.gp[u], e = p.gp[u + 1];
@@ -302,16 +319,38 @@ __global__ void __launch_bounds__(kCoopBlock) bfs_levels(BfsParams p)
                 }
                 unsigned m = __ballot_sync(0xffffffffu, won);
                 if (m) {
-                    unsigned long long pos0 = 0;
-                    if (lane == __ffs(m) - 1) pos0 = atomicAdd((unsigned long long*)cnext, (unsigned long long)__popc(m));
-                    pos0 = __shfl_sync(0xffffffffu, pos0, __ffs(m) - 1);
-                    if (won) {
-                        int64_t pos = (int64_t)pos0 + __popc(m & lt);
-                        if (pos < p.N) nxt[pos] = w;
-                        else atomicCAS(p.gb.err, 0, (int)kDevOverflow);
+                    // slots below kBfsBuf go to the block buffer (each written by
+                    // exactly one lane); the overflow is appended directly
+                    int leader = __ffs(m) - 1;
+                    int sp = 0;
+                    if (lane == leader) sp = atomicAdd(&s_cnt, __popc(m));
+                    sp = __shfl_sync(0xffffffffu, sp, leader);
+                    int slot = sp + __popc(m & lt);
+                    bool in_buf = won && slot < kBfsBuf;
+                    if (in_buf) sbuf[slot] = w;
+                    unsigned over = __ballot_sync(0xffffffffu, won && !in_buf);
+                    if (over) {
+                        int l2 = __ffs(over) - 1;
+                        unsigned long long pos0 = 0;
+                        if (lane == l2) pos0 = atomicAdd((unsigned long long*)cnext, (unsigned long long)__popc(over));
+                        pos0 = __shfl_sync(0xffffffffu, pos0, l2);
+                        if (won && !in_buf) {
+                            int64_t pos = (int64_t)pos0 + __popc(over & lt);
+                            if (pos < p.N) nxt[pos] = w;
+                            else atomicCAS(p.gb.err, 0, (int)kDevOverflow);
+                        }
                     }
                 }
             }
+        }
+        __syncthreads();
+        int nb = s_cnt < kBfsBuf ? s_cnt : kBfsBuf;
+        if (threadIdx.x == 0) s_base = nb ? (long long)atomicAdd((unsigned long long*)cnext, (unsigned long long)nb) : 0;
+        __syncthreads();
+        for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+            int64_t pos = s_base + t;
+            if (pos < p.N) nxt[pos] = sbuf[t];
+            else atomicCAS(p.gb.err, 0, (int)kDevOverflow);
         }
         if (!grid_sync(p.gb)) return;
         int32_t* t = cur;
@@ -411,10 +450,53 @@ struct CmParams {
     GridBarrier gb;
 };
 
+// Sum of the block totals of all blocks (*total) and of the blocks before this
+// one (*before), computed redundantly by every block (thread 0 gets both).
+__device__ __forceinline__ void block_offsets(const int64_t* bsum, int64_t* before, int64_t* total)
+{
+    __shared__ int64_t s_b[kCoopBlock / kWarp], s_t[kCoopBlock / kWarp];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t sb = 0, stot = 0;
+    for (unsigned t = threadIdx.x; t < gridDim.x; t += blockDim.x) {
+        int64_t v = bsum[t];
+        stot += v;
+        if (t < blockIdx.x) sb += v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sb += __shfl_xor_sync(0xffffffffu, sb, o);
+        stot += __shfl_xor_sync(0xffffffffu, stot, o);
+    }
+    if (lane == 0) { s_b[wid] = sb; s_t[wid] = stot; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t x = 0, y = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { x += s_b[w]; y += s_t[w]; }
+        *before = x;
+        *total = y;
+    }
+    __syncthreads();
+}
+
+// Claims of the unvisited neighbours of vertex u placed at queue index k.
+__device__ __forceinline__ void claim_neighbours(const CmParams& p, int32_t u, int64_t k, int lane)
+{
+    int64_t b = p.gp[u], e = p.gp[u + 1];
+    for (int64_t q = b + lane; q < e; q += 32) {
+        int32_t w = p.adj_r[q];
+        if (ld_volatile_i32(p.vis + w) == kUnvisited) atomicMin(p.claim + w, (int32_t)k);
+    }
+}
+
+// Per level two barriers: (1) child counts and block-local offsets,
+// (2) placement of the children, each of which claims its own unvisited
+// neighbours at once.  A claim on a vertex of the same new level is harmless:
+// that vertex is marked visited before the next count, and only unvisited
+// vertices are counted as children.
 __global__ void __launch_bounds__(kCoopBlock) cm_levels(CmParams p)
 {
     __shared__ int64_t s_tot;
     __shared__ int64_t wsum[kCoopBlock / kWarp];
+    __shared__ int64_t s_before, s_total;
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned lt = (1u << lane) - 1u;
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -426,21 +508,13 @@ __global__ void __launch_bounds__(kCoopBlock) cm_levels(CmParams p)
         p.vis[p.roots[c]] = 0;
     }
     if (!grid_sync(p.gb)) return;
+    for (int64_t c = gw; c < p.C; c += nw) claim_neighbours(p, p.roots[c], c, lane);
+    if (!grid_sync(p.gb)) return;
     int64_t lo = 0, hi = p.C;
     int L = 0;
     while (hi > lo) {
         int64_t F = hi - lo;
-        // P1: every unvisited neighbour is claimed by its earliest frontier vertex
-        for (int64_t k = lo + gw; k < hi; k += nw) {
-            int32_t u = p.Q[k];
-            int64_t b = p.gp[u], e = p.gp[u + 1];
-            for (int64_t q = b + lane; q < e; q += 32) {
-                int32_t w = p.adj_r[q];
-                if (ld_volatile_i32(p.vis + w) == kUnvisited) atomicMin(p.claim + w, (int32_t)k);
-            }
-        }
-        if (!grid_sync(p.gb)) return;
-        // P2: child counts of this block's chunk of the frontier, block-local scan
+        // (1) child counts of this block's chunk of the frontier, block-local scan
         int64_t chunk = ceil_div(F, (int64_t)gridDim.x);
         int64_t c0 = lo + (int64_t)blockIdx.x * chunk;
         int64_t c1 = c0 + chunk < hi ? c0 + chunk : hi;
@@ -487,41 +561,18 @@ __global__ void __launch_bounds__(kCoopBlock) cm_levels(CmParams p)
         }
         if (threadIdx.x == 0) p.bsum[blockIdx.x] = carry;
         if (!grid_sync(p.gb)) return;
-        // P3: exclusive scan of the block totals (block 0, all threads)
-        if (blockIdx.x == 0) {
-            int64_t carry2 = 0;
-            for (unsigned base = 0; base < gridDim.x; base += blockDim.x) {
-                unsigned b = base + threadIdx.x;
-                int64_t v = b < gridDim.x ? p.bsum[b] : 0;
-                int64_t inc = v;
-                for (int o = 1; o < 32; o <<= 1) {
-                    int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
-                    if (lane >= o) inc += t;
-                }
-                if (lane == 31) wsum[wid] = inc;
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    int64_t run = 0;
-                    for (int w = 0; w < wpb; ++w) {
-                        int64_t t = wsum[w];
-                        wsum[w] = run;
-                        run += t;
-                    }
-                    s_tot = run;
-                }
-                __syncthreads();
-                if (b < gridDim.x) p.bsum[b] = carry2 + wsum[wid] + inc - v;
-                carry2 += s_tot;
-                __syncthreads();
-            }
-            if (threadIdx.x == 0) p.bsum[gridDim.x] = carry2;
+        block_offsets(p.bsum, &s_before, &s_total);
+        int64_t nf = s_total;
+        if (nf < 0 || hi + nf > p.N) {  // cannot happen for a valid queue; stop before any overrun
+            if (tid == 0) atomicCAS(p.gb.err, 0, (int)kDevOverflow);
+            return;
         }
-        if (!grid_sync(p.gb)) return;
-        // P4: append the children of every frontier vertex in rank order
-        for (int64_t k = lo + gw; k < hi; k += nw) {
+        // (2) children of this block's chunk, in rank order, then their claims
+        int64_t boff = s_before;
+        for (int64_t k = c0 + wid; k < c1; k += wpb) {
             int32_t u = p.Q[k];
             int64_t b = p.gp[u], e = p.gp[u + 1];
-            int64_t o = hi + p.bsum[(k - lo) / chunk] + p.cnt[k];
+            int64_t o = hi + boff + p.cnt[k];
             for (int64_t base = b; base < e; base += 32) {
                 int64_t q = base + lane;
                 bool child = false;
@@ -537,15 +588,19 @@ __global__ void __launch_bounds__(kCoopBlock) cm_levels(CmParams p)
                     else atomicCAS(p.gb.err, 0, (int)kDevOverflow);
                     p.vis[w] = L + 1;
                 }
-                o += __popc(m);
+                // each new vertex claims its unvisited neighbours (the whole warp
+                // walks the new vertices of this chunk one by one)
+                while (m) {
+                    int src = __ffs(m) - 1;
+                    m &= m - 1;
+                    int32_t wn = __shfl_sync(0xffffffffu, w, src);
+                    int64_t posn = o + __popc(__ballot_sync(0xffffffffu, child) & ((1u << src) - 1u));
+                    claim_neighbours(p, wn, posn, lane);
+                }
+                o += __popc(__ballot_sync(0xffffffffu, child));
             }
         }
         if (!grid_sync(p.gb)) return;
-        int64_t nf = *(volatile int64_t*)(p.bsum + gridDim.x);
-        if (nf < 0 || hi + nf > p.N) {  // cannot happen for a valid queue; stop before any overrun
-            if (tid == 0) atomicCAS(p.gb.err, 0, (int)kDevOverflow);
-            return;
-        }
         lo = hi;
         hi = hi + nf;
         ++L;
@@ -620,13 +675,14 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
     int64_t M = read_scalar(gp.p + N, st);
 
     // 2. ranks in (deg, index) order
-    int bN = bits_for((uint64_t)(N > 1 ? N - 1 : 1));
+    // stable sort by degree of the vertices in index order = (degree, index) order
     DBuf<uint64_t> dk(N, st);
     DBuf<uint32_t> by_rank(N, st);
-    deg_keys<<<grid_for(N), kBlock, 0, st>>>(N, gp.p, bN, dk.p, by_rank.p);
+    DBuf<unsigned long long> dmax(1, st);
+    OBK_CUDA(cudaMemsetAsync(dmax.p, 0, sizeof(unsigned long long), st));
+    deg_keys<<<grid_for(N), kBlock, 0, st>>>(N, gp.p, dk.p, by_rank.p, dmax.p);
     OBK_CHECK_LAUNCH();
-    int64_t maxdeg_bound = M;  // degrees are at most M
-    radix_sort_pairs(dk.p, by_rank.p, N, bN + bits_for((uint64_t)maxdeg_bound), st);
+    radix_sort_pairs(dk.p, by_rank.p, N, bits_for((uint64_t)read_scalar(dmax.p, st)), st);
     dk.release();
     DBuf<int32_t> r(N, st);
     rank_of<<<grid_for(N), kBlock, 0, st>>>(N, by_rank.p, r.p);

@@ -1,10 +1,14 @@
 // server.cu -- request loop with continuous batching (obk_submit / obk_poll).
 //
 // Requests are queued on the host and admitted while the device memory they
-// are estimated to need fits the HBM budget.  Each admitted request runs on
-// one of max_streams worker streams, so requests admitted while others run
-// overlap on the device; a request that does not fit yet stays PENDING until
-// running ones release their memory.
+// are estimated to need fits the HBM budget.  Each admitted request is set up
+// (obk_create) on one of max_streams worker streams, so requests admitted
+// while others run overlap on the device; a request that does not fit yet
+// stays PENDING until running ones release their memory.  Large systems are
+// then solved on the cooperative grid of their stream; small FP64 systems join
+// a ready list that is solved many at a time by obk_solve_batch (one thread
+// block per system, x in shared memory), run by whichever worker finds no
+// batch in progress.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,6 +23,7 @@
 #include <vector>
 
 #include "../../include/obk.h"
+#include "batch.cuh"
 #include "common.cuh"
 
 namespace {
@@ -39,6 +44,9 @@ struct Request {
     int status = OBK_PENDING;
     obk_info info{};
     std::string err;
+    // batched path: prepared system and device copies of f, x0 and x
+    obk_handle* h = nullptr;
+    obk::DBuf<double> fdev, x0dev, xdev;
 };
 
 // Upper estimate of the device bytes a solve needs at its peak (setup).
@@ -56,11 +64,95 @@ struct obk_server {
     std::mutex mu;
     std::condition_variable cv;
     std::deque<std::shared_ptr<Request>> queue;
+    std::deque<std::shared_ptr<Request>> ready;  // prepared small systems awaiting a batch
+    bool batch_running = false;
     std::map<uint64_t, std::shared_ptr<Request>> all;
     uint64_t next_ticket = 1;
     bool stopping = false;
     std::vector<std::thread> workers;
 };
+
+// Finish a request: record its result, release its memory and budget.
+static void finish(obk_server* s, const std::shared_ptr<Request>& r, int rc)
+{
+    if (r->h) {
+        obk_destroy(r->h);
+        r->h = nullptr;
+    }
+    r->fdev.release();
+    r->x0dev.release();
+    r->xdev.release();
+    if (r->cancel.load() && rc >= 0) rc = OBK_ERR_CANCELLED;
+    r->status = rc;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->in_use -= r->bytes;
+    }
+    r->state.store(2);
+    s->cv.notify_all();
+}
+
+// Solve the ready small systems in batches (one launch per batch) until the
+// ready list is empty; only one worker runs batches at a time.
+static void run_batches(obk_server* s)
+{
+    constexpr size_t kMaxBatch = 2048;
+    for (;;) {
+        std::vector<std::shared_ptr<Request>> b;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (s->batch_running || s->ready.empty()) return;
+            s->batch_running = true;
+            // same tolerance, iteration limit and stopping options in one batch
+            const Request& f0 = *s->ready.front();
+            for (auto it = s->ready.begin(); it != s->ready.end() && b.size() < kMaxBatch;) {
+                const Request& q = **it;
+                if (q.tol == f0.tol && q.maxit == f0.maxit && q.opts.check_every == f0.opts.check_every &&
+                    q.opts.stagnation == f0.opts.stagnation) {
+                    b.push_back(*it);
+                    it = s->ready.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+        }
+        std::vector<obk_handle*> hs;
+        std::vector<const double*> fs, x0s;
+        std::vector<double*> xs;
+        for (auto& r : b) {
+            hs.push_back(r->h);
+            fs.push_back(r->fdev.p);
+            x0s.push_back(r->has_x0 ? r->x0dev.p : nullptr);
+            xs.push_back(r->xdev.p);
+        }
+        std::vector<obk_status> st(b.size(), OBK_ERR_CUDA);
+        std::vector<obk_info> info(b.size());
+        obk_opts o = b[0]->opts;
+        obk_status rc = obk_solve_batch(hs.data(), (int32_t)hs.size(), &o, fs.data(), x0s.data(), b[0]->tol,
+                                        b[0]->maxit, xs.data(), info.data(), st.data());
+        std::string err = rc < 0 ? obk_last_error() : "";
+        for (size_t i = 0; i < b.size(); ++i) {
+            auto& r = b[i];
+            int ri = rc < 0 ? (int)rc : (int)st[i];
+            if (ri >= 0) {
+                r->x.assign((size_t)r->n, 0.0);
+                if (cudaMemcpy(r->x.data(), r->xdev.p, (size_t)r->n * sizeof(double), cudaMemcpyDeviceToHost) !=
+                    cudaSuccess) {
+                    ri = OBK_ERR_CUDA;
+                    r->err = "copying the result failed";
+                }
+                r->info = info[i];
+            } else {
+                r->err = err;
+            }
+            finish(s, r, ri);
+        }
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->batch_running = false;
+        }
+    }
+}
 
 static void worker_loop(obk_server* s)
 {
@@ -74,6 +166,7 @@ static void worker_loop(obk_server* s)
             for (;;) {
                 if (s->stopping && s->queue.empty()) {
                     lk.unlock();
+                    run_batches(s);
                     cudaStreamDestroy(st);
                     return;
                 }
@@ -99,6 +192,38 @@ static void worker_loop(obk_server* s)
         obk_csr A{r->rp.data(), r->ci.data(), r->v.data(), (int64_t)r->ci.size(), 0};
         obk_handle* h = nullptr;
         obk_status rc = obk_create_on_stream(&A, r->m, r->n, r->thr, (void*)st, &h);
+        if (rc == OBK_OK && r->opts.precision == 0 && obk::batch_eligible(h) && !r->cancel.load()) {
+            // small system: stage f (and x0) on the device, then join the ready list
+            bool ok = true;
+            try {
+                r->fdev.alloc((size_t)r->m, st);
+                r->xdev.alloc((size_t)r->n, st);
+                ok = cudaMemcpyAsync(r->fdev.p, r->f.data(), (size_t)r->m * sizeof(double), cudaMemcpyHostToDevice,
+                                     st) == cudaSuccess;
+                if (ok && r->has_x0) {
+                    r->x0dev.alloc((size_t)r->n, st);
+                    ok = cudaMemcpyAsync(r->x0dev.p, r->x0.data(), (size_t)r->n * sizeof(double),
+                                         cudaMemcpyHostToDevice, st) == cudaSuccess;
+                }
+                ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
+            } catch (const obk::Error& e) {
+                ok = false;
+                r->err = e.msg;
+            }
+            if (ok) {
+                r->h = h;
+                {
+                    std::lock_guard<std::mutex> lk(s->mu);
+                    s->ready.push_back(r);
+                }
+                run_batches(s);
+                continue;
+            }
+            if (r->err.empty()) r->err = "staging a batched request failed";
+            r->h = h;
+            finish(s, r, OBK_ERR_CUDA);
+            continue;
+        }
         if (rc == OBK_OK) {
             r->x.assign((size_t)r->n, 0.0);
             if (r->cancel.load()) rc = OBK_ERR_CANCELLED;
@@ -107,15 +232,9 @@ static void worker_loop(obk_server* s)
                                   r->x.data(), &r->info);
         }
         if (rc < 0) r->err = obk_last_error();
-        obk_destroy(h);
-        if (r->cancel.load() && rc >= 0) rc = OBK_ERR_CANCELLED;
-        r->status = rc;
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            s->in_use -= r->bytes;
-        }
-        r->state.store(2);
-        s->cv.notify_all();
+        r->h = h;
+        finish(s, r, rc);
+        run_batches(s);
     }
 }
 

@@ -532,24 +532,39 @@ __global__ void seg_lengths(int64_t nseg, const uint32_t* order, const int64_t* 
     GRID_STRIDE(t, nseg) len[t] = seg_ptr[order[t] + 1] - seg_ptr[order[t]];
 }
 
-// copy the entries of each segment to its new place (one warp per segment)
+// copy the entries of each segment to its new place (one thread per segment;
+// segments hold a few entries)
 template <class T>
 __global__ void seg_move(int64_t nseg, const uint32_t* order, const int64_t* seg_ptr, const int64_t* new_ptr,
                          const int32_t* seg_col, int32_t* new_col, const int32_t* mrow, const T* mval,
                          const float* mval32, int32_t* nrow, T* nval, float* nval32)
 {
-    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t t = w; t < nseg; t += nw) {
+    GRID_STRIDE(t, nseg)
+    {
         int64_t s = order[t], b = seg_ptr[s], e = seg_ptr[s + 1], d = new_ptr[t];
-        if (lane == 0) new_col[t] = seg_col[s];
-        for (int64_t q = lane; q < e - b; q += 32) {
+        new_col[t] = seg_col[s];
+        for (int64_t q = 0; q < e - b; ++q) {
             nrow[d + q] = mrow[b + q];
             nval[d + q] = mval[b + q];
             if (nval32) nval32[d + q] = mval32[b + q];
         }
     }
+}
+
+// longest row of a CSR (max over i of ptr[i+1] - ptr[i])
+__global__ void max_row_len(int64_t n, const int64_t* ptr, unsigned long long* mx)
+{
+    unsigned long long m = 0;
+    GRID_STRIDE(i, n)
+    {
+        unsigned long long d = (unsigned long long)(ptr[i + 1] - ptr[i]);
+        m = d > m ? d : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+        m = t > m ? t : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(mx, m);
 }
 
 // histogram of colours; colours below 256 are counted in shared memory first
@@ -655,6 +670,15 @@ __global__ void mirror_segments(int64_t M, const uint32_t* order, const int32_t*
 }
 
 }  // namespace
+
+int64_t max_segment_length(int64_t n, const int64_t* ptr, cudaStream_t st)
+{
+    DBuf<unsigned long long> mx(1, st);
+    OBK_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned long long), st));
+    max_row_len<<<grid_for(n), kBlock, 0, st>>>(n, ptr, mx.p);
+    OBK_CHECK_LAUNCH();
+    return (int64_t)read_scalar(mx.p, st);
+}
 
 void validate_csr(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
                   int64_t nnz, int* d_bad, cudaStream_t st)
@@ -781,7 +805,9 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
     // 5. group-major rows
     DBuf<uint64_t> gk(N, st);
     DBuf<uint32_t> gorder(N, st);
-    const int lbits = 10;  // row/segment lengths above 1022 share the last class
+    // length classes: every length up to the longest row (capped at 1023, longer
+    // rows share the last class)
+    int lbits = std::min(10, bits_for((uint64_t)max_segment_length(N, rp, st)));
     color_keys<<<grid_for(N), kBlock, 0, st>>>(N, L.group_of.p, rp, G, lbits, gk.p, gorder.p);
     OBK_CHECK_LAUNCH();
     radix_sort_pairs(gk.p, gorder.p, N, bits_for((uint64_t)G) + lbits, st);
@@ -859,9 +885,10 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
     if (nseg > 1) {
         DBuf<uint64_t> sk(nseg, st);
         DBuf<uint32_t> sorder(nseg, st);
-        seg_keys<<<grid_for(nseg), kBlock, 0, st>>>(nseg, L.seg_ptr.p, L.gseg_ptr.p, G, lbits, sk.p, sorder.p);
+        int sbits = std::min(10, bits_for((uint64_t)max_segment_length(nseg, L.seg_ptr.p, st)));
+        seg_keys<<<grid_for(nseg), kBlock, 0, st>>>(nseg, L.seg_ptr.p, L.gseg_ptr.p, G, sbits, sk.p, sorder.p);
         OBK_CHECK_LAUNCH();
-        radix_sort_pairs(sk.p, sorder.p, nseg, bits_for((uint64_t)G) + lbits, st);
+        radix_sort_pairs(sk.p, sorder.p, nseg, bits_for((uint64_t)G) + sbits, st);
         sk.release();
         DBuf<int64_t> slen(nseg, st), nptr(nseg + 1, st);
         seg_lengths<<<grid_for(nseg), kBlock, 0, st>>>(nseg, sorder.p, L.seg_ptr.p, slen.p);
@@ -871,7 +898,7 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
         DBuf<double> nval(M, st);
         DBuf<float> nval32;
         if (want_fp32) nval32.alloc(M, st);
-        seg_move<double><<<grid_for(nseg * 32), kBlock, 0, st>>>(
+        seg_move<double><<<grid_for(nseg), kBlock, 0, st>>>(
             nseg, sorder.p, L.seg_ptr.p, nptr.p, L.seg_col.p, ncol.p, L.mir_row.p, L.mir_val.p,
             want_fp32 ? L.mir_val32.p : nullptr, nrow.p, nval.p, want_fp32 ? nval32.p : nullptr);
         OBK_CHECK_LAUNCH();

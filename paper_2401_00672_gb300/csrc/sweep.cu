@@ -471,6 +471,7 @@ void launch_solve(SweepParams& p, cudaStream_t st)
 // (twice as many independent loads in flight per row).
 int choose_sub(double avg_row)
 {
+    // (a measured choice from obk_autotune takes precedence, see capi.cu)
     if (avg_row <= 6) return 1;
     if (avg_row <= 64) return 2;
     if (avg_row <= 160) return 8;
@@ -556,6 +557,60 @@ SolveResult run_solve(const SweepLayout& L, const double* f_gm, double fnorm2, d
     res.sweep_ms = (double)h_out[4] * 1e-6;
     res.rel_res = h_ctrl[0];
     return res;
+}
+
+}  // namespace obk
+
+namespace obk {
+namespace {
+__global__ void fill_ones(double* p, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = 1.0;
+}
+}  // namespace
+
+double time_sweep(const SweepLayout& L, int sub, int precision, int* d_err, cudaStream_t st)
+{
+    // scratch system state: x = 0, f = 1 (every sweep does its full work)
+    DBuf<double> x(std::max<int64_t>(L.N, 1), st), f(std::max<int64_t>(L.Ngm, 1), st);
+    OBK_CUDA(cudaMemsetAsync(x.p, 0, x.bytes(), st));
+    fill_ones<<<(unsigned)std::min<int64_t>(ceil_div(f.n, 256), 4096), 256, 0, st>>>(f.p, (int64_t)f.n);
+    OBK_CHECK_LAUNCH();
+    cudaEvent_t e[4];
+    for (auto& ev : e) OBK_CUDA(cudaEventCreate(&ev));
+    double per = 0.0;
+    try {
+        SolveArgs a;
+        a.precision = precision;
+        a.check_every = 1 << 30;
+        a.tol = -1.0;  // never met: exactly maxit sweeps
+        a.sub = sub;
+        a.max_outer = 1;
+        a.inner_sweeps = 0;
+        float t2 = 0.f, t8 = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {  // the first repetition warms up
+            a.maxit = 2;
+            if (precision == 1) a.inner_sweeps = 2;
+            OBK_CUDA(cudaEventRecord(e[0], st));
+            run_solve(L, f.p, (double)L.Ngm, 0.0, x.p, a, d_err, st);
+            OBK_CUDA(cudaEventRecord(e[1], st));
+            a.maxit = 8;
+            if (precision == 1) a.inner_sweeps = 8;
+            OBK_CUDA(cudaEventRecord(e[2], st));
+            run_solve(L, f.p, (double)L.Ngm, 0.0, x.p, a, d_err, st);
+            OBK_CUDA(cudaEventRecord(e[3], st));
+            OBK_CUDA(cudaEventSynchronize(e[3]));
+            OBK_CUDA(cudaEventElapsedTime(&t2, e[0], e[1]));
+            OBK_CUDA(cudaEventElapsedTime(&t8, e[2], e[3]));
+        }
+        per = (double)(t8 - t2) / 6.0;
+    } catch (...) {
+        for (auto& ev : e) cudaEventDestroy(ev);
+        throw;
+    }
+    for (auto& ev : e) cudaEventDestroy(ev);
+    return per;
 }
 
 }  // namespace obk

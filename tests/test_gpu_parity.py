@@ -155,6 +155,54 @@ def test_rows_per_warp_variants_agree(obk, rpw):
     assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) <= XTOL
 
 
+def test_autotune_keeps_results_and_parity(obk):
+    s, _ = _case("knn_30000")
+    A = s.A
+    st_o, x_o, io = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1, tol=1e-300, maxit=5)
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
+        t = h.autotune(0)
+        assert t["rows_per_warp"] in (1, 2, 4, 8, 16, 32) and t["sweep_ms"] > 0
+        assert t["candidate_ms"][t["rows_per_warp"]] == t["sweep_ms"]
+        t1 = h.autotune(1)
+        assert t1["rows_per_warp"] in (1, 2, 4, 8, 16, 32)
+        st, x, info = h.solve(s.f, None, tol=1e-300, maxit=5)
+    assert info.sweeps == 5
+    assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) <= XTOL
+
+
+def test_batched_small_systems_match_single_solves(obk):
+    import torch
+
+    dev = torch.device("cuda")
+    systems = [synth.random_dominant(n, 7, seed=300 + k) for k, n in enumerate((500, 1200, 2000, 3100, 777))]
+    systems += [synth.rect_random(2 * n, n, 10, seed=350 + k) for k, n in enumerate((600, 1300))]
+    systems += [_zero_rows()]
+    handles, fs, outs, ref = [], [], [], []
+    for s in systems:
+        A = s.A
+        h = obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1)
+        handles.append(h)
+        fs.append(torch.from_numpy(s.f).to(dev))
+        outs.append(torch.empty(A.n, dtype=torch.float64, device=dev))
+        st_o, x_o, io = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1, tol=1e-8, maxit=5000)
+        ref.append((st_o, x_o, io))
+    sts, infos = obk.solve_batch(handles, fs, outs, tol=1e-8, maxit=5000)
+    for (st_o, x_o, io), st, info, out in zip(ref, sts, infos, outs):
+        assert st == st_o == obk.OBK_OK
+        assert abs(info.sweeps - io.sweeps) <= 1 and info.rel_res <= 1e-8
+        if info.sweeps == io.sweeps:
+            x = out.cpu().numpy()
+            assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) <= XTOL
+    # too large for one block: refused
+    big = synth.knn_dominant(30000, 12, seed=5)
+    hb = obk.Handle(big.A.row_ptr, big.A.col_idx, big.A.val, big.A.m, big.A.n)
+    with pytest.raises(obk.ObkError):
+        obk.solve_batch([hb], [torch.from_numpy(big.f).to(dev)], [torch.empty(big.A.n, dtype=torch.float64,
+                                                                               device=dev)])
+    for h in handles + [hb]:
+        h.close()
+
+
 def test_fixed_sweeps_with_x0_and_device_buffers(obk):
     import torch
 
@@ -296,6 +344,63 @@ def test_request_loop_alone_equals_mixed(obk):
         st_m, x_m = results[t]
         assert st_m == st_a
         assert np.linalg.norm(x_m - x_a) <= XTOL * np.linalg.norm(x_a)
+
+
+def _wait(srv, ticket, n, limit_s=120):
+    import time
+
+    t0 = time.time()
+    while time.time() - t0 < limit_s:
+        st, x, info = srv.poll(ticket, n)
+        if st != obk_pending():
+            return st, x, info
+        time.sleep(0.005)
+    raise AssertionError("request did not finish")
+
+
+def obk_pending():
+    import paper_2401_00672_gb300 as m
+
+    return m.OBK_PENDING
+
+
+def test_request_loop_budget_cancel_and_unknown_ticket(obk):
+    s, _ = _case("knn_30000")
+    A = s.A
+    # a request that can never fit the budget is refused at submission
+    tiny = obk.Server(hbm_budget_bytes=1 << 20, max_streams=1)
+    with pytest.raises(obk.ObkError) as e:
+        tiny.submit(A.row_ptr, A.col_idx, A.val, A.m, A.n, s.f)
+    assert e.value.status == obk.OBK_ERR_BUDGET
+    tiny.close()
+    # one worker: the second request waits in the queue and can be cancelled there
+    srv = obk.Server(hbm_budget_bytes=0, max_streams=1)
+    t1 = srv.submit(A.row_ptr, A.col_idx, A.val, A.m, A.n, s.f, tol=1e-8, maxit=5000)
+    t2 = srv.submit(A.row_ptr, A.col_idx, A.val, A.m, A.n, s.f, tol=1e-8, maxit=5000)
+    assert srv.cancel(t2) == obk.OBK_OK
+    st1, x1, _ = _wait(srv, t1, A.n)
+    st2, _, _ = _wait(srv, t2, A.n)
+    assert st1 == obk.OBK_OK and st2 == obk.OBK_ERR_CANCELLED
+    # a finished ticket is released by its final poll
+    st, _, _ = srv.poll(t1, A.n)
+    assert st == obk.OBK_ERR_NOT_FOUND
+    assert srv.cancel(123456789) == obk.OBK_ERR_NOT_FOUND
+    srv.close()
+    _, x_alone, _ = obk.solve(A.row_ptr, A.col_idx, A.val, A.m, A.n, s.f, tol=1e-8, maxit=5000)
+    assert np.linalg.norm(x1 - x_alone) <= XTOL * np.linalg.norm(x_alone)
+
+
+def test_request_loop_budget_admits_one_at_a_time(obk):
+    # the budget fits one request at a time: all still finish, in arrival order
+    systems = [synth.random_dominant(3000 + 500 * k, 7, seed=700 + k) for k in range(4)]
+    foot = max(s.A.nnz * 96 + max(s.A.m, s.A.n) * 160 + (64 << 20) for s in systems)
+    srv = obk.Server(hbm_budget_bytes=foot + 1024, max_streams=4)
+    tickets = [srv.submit(s.A.row_ptr, s.A.col_idx, s.A.val, s.A.m, s.A.n, s.f, tol=1e-8, maxit=5000)
+               for s in systems]
+    for t, s in zip(tickets, systems):
+        st, x, info = _wait(srv, t, s.A.n)
+        assert st == obk.OBK_OK and info.rel_res <= 1e-8
+    srv.close()
 
 
 @pytest.mark.slow
