@@ -379,6 +379,9 @@ def main():
     clocks = sampler.stop()
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, dev)
     st, info = infos[-1]
+    hp = obk.Handle(rp, ci, v, A.m, A.n, thr=cfg["thr"], stream=stream.cuda_stream)
+    setup_profile = hp.setup_profile()
+    hp.close()
     xh = x.cpu().numpy()
     err_xstar = float(np.linalg.norm(xh - s.xstar) / np.linalg.norm(s.xstar))
 
@@ -486,6 +489,7 @@ def main():
                            f"{(A.val.nbytes + A.col_idx.nbytes) / 1e6:.0f} MB), no flush"),
             "throughput_solves_per_s": world * 1e3 / ms,
             "sweeps": info.sweeps, "groups": info.groups, "setup_ms": info.setup_ms, "solve_ms": info.solve_ms,
+            "setup_profile_ms": setup_profile,
             "rel_res": info.rel_res, "status": st, "x_err_vs_xstar": err_xstar,
             "bandwidth": [info.bandwidth_before, info.bandwidth_after],
             "gpu_launches": int(launches // max(args.steps, 1)), "gpu_launches_timed_region": int(launches),

@@ -140,6 +140,14 @@ OBK_API obk_status obk_get_groups(const obk_handle* h, int32_t* group_of);
 OBK_API obk_status obk_get_row_norms(const obk_handle* h, double* nsq);
 OBK_API obk_status obk_get_info(const obk_handle* h, obk_info* info);
 
+/* Device time of the stages of obk_create, in order: (0) upload, validation
+ * and extension, (1) bandwidth of the input, (2) Reverse Cuthill-McKee,
+ * (3) permutation and its bandwidth, (4) row norms and transposition,
+ * (5) pair cosines and conflict lists, (6) greedy grouping, (7) group-major
+ * rows, (8) column mirror and segment order, (9) remaining bookkeeping.
+ * Writes at most cap values to ms (host) and returns how many. */
+OBK_API int32_t obk_get_setup_profile(const obk_handle* h, double* ms, int32_t cap);
+
 /* Residual check on its own: *rel_res = ||f - A x||_2 / ||f||_2 (or ||f - A x||_2
  * when f = 0) for A (m x n) in CSR form, in FP64 (the stop rule of the solve).
  * f has m and x has n values; A->device_ptrs says where A lives, f and x are

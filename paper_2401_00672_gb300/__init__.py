@@ -27,7 +27,7 @@ EXPORTS = [
     "obk_get_groups", "obk_get_row_norms", "obk_get_info", "obk_destroy", "obk_server_create",
     "obk_submit", "obk_poll", "obk_cancel", "obk_server_destroy", "obk_last_error", "obk_version",
     "obk_kernel_launches", "obk_residual", "obk_residual_noalloc", "obk_autotune", "obk_solve_batch",
-    "obk_batch_max_n",
+    "obk_batch_max_n", "obk_get_setup_profile",
 ]
 
 
@@ -111,6 +111,7 @@ def _load() -> ctypes.CDLL:
         "obk_autotune": ([vp, i32, vp], ctypes.c_int),
         "obk_solve_batch": ([vp, i32, vp, vp, vp, dbl, i64, vp, vp, vp], ctypes.c_int),
         "obk_batch_max_n": ([], ctypes.c_int64),
+        "obk_get_setup_profile": ([vp, vp, i32], ctypes.c_int32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -184,6 +185,15 @@ class Handle:
                               int(maxit), po, ctypes.byref(info))
         _check(rc, "obk_solve")
         return rc, ko, _info(info)
+
+    SETUP_STAGES = ("upload_validate_extend", "bandwidth_in", "rcm", "permute", "norms_transpose",
+                    "pair_cosines", "grouping", "group_rows", "mirror_segments", "bookkeeping")
+
+    def setup_profile(self) -> dict:
+        """obk_get_setup_profile: device milliseconds per obk_create stage."""
+        ms = (ctypes.c_double * 16)()
+        n = lib.obk_get_setup_profile(self._h, ms, 16)
+        return {name: round(ms[i], 4) for i, name in enumerate(self.SETUP_STAGES[:n])}
 
     def autotune(self, precision: int = 0) -> dict:
         """obk_autotune: time the rows-per-warp settings, keep the fastest."""

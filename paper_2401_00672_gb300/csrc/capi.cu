@@ -281,6 +281,8 @@ struct obk_handle {
     obk_info info{};
     RcmStats rcm{};
     int tuned_sub[2] = {0, 0};  // lanes per row chosen by obk_autotune (0 = not tuned)
+    double stage_ms[16] = {};    // obk_create stages (see obk_get_setup_profile)
+    int n_stage = 0;
 };
 
 namespace {
@@ -350,6 +352,8 @@ obk_status obk_create_on_stream(const obk_csr* A, int64_t m, int64_t n, double t
         }
         cudaStream_t st = h->st;
         Timer tm(st);
+        StageClock clock;
+        clock.mark(st);
         h->m = m;
         h->n = n;
         h->N = std::max(m, n);
@@ -378,10 +382,13 @@ obk_status obk_create_on_stream(const obk_csr* A, int64_t m, int64_t n, double t
             extend_rowptr<<<grid_for(N - m), kBlock, 0, st>>>(m, N, nnz, rp.p);
             OBK_CHECK_LAUNCH();
         }
+        clock.mark(st);  // upload, validation, extension
         h->info.bandwidth_before = half_bandwidth(N, rp.p, ci.p, nnz, st);
+        clock.mark(st);  // bandwidth of the input
         // Reverse Cuthill-McKee (Section 3.2) and A~ = P A^ P^T (Eq. 3.1)
         h->perm.alloc(N, st);
         rcm_reorder(N, rp.p, ci.p, nnz, h->perm.p, kDefaultSpins, h->err.p, &h->rcm, st);
+        clock.mark(st);  // Reverse Cuthill-McKee
         DBuf<int32_t> iperm(N, st);
         DBuf<int64_t> rpt(N + 1, st);
         DBuf<int32_t> cit(std::max<int64_t>(nnz, 1), st);
@@ -391,8 +398,9 @@ obk_status obk_create_on_stream(const obk_csr* A, int64_t m, int64_t n, double t
         ci.release();
         v.release();
         h->info.bandwidth_after = half_bandwidth(N, rpt.p, cit.p, nnz, st);
+        clock.mark(st);  // permutation and its bandwidth
         // norms, groups and sweep layout (Section 3.3)
-        group_build(N, rpt.p, cit.p, vt.p, nnz, thr, kDefaultSpins, h->err.p, h->L, true, st);
+        group_build(N, rpt.p, cit.p, vt.p, nnz, thr, kDefaultSpins, h->err.p, h->L, true, st, &clock);
         h->info.groups = h->L.G;
         h->info.n_conflicts = h->L.n_conflicts;
         h->src_gm.alloc(std::max<int64_t>(h->L.Ngm, 1), st);
@@ -409,6 +417,8 @@ obk_status obk_create_on_stream(const obk_csr* A, int64_t m, int64_t n, double t
         h->zero_src.alloc(std::max<int64_t>(h->n_zero, 1), st);
         zero_row_list<<<grid_for(N), kBlock, 0, st>>>(N, zf.p, zs.p, h->perm.p, h->zero_src.p);
         OBK_CHECK_LAUNCH();
+        clock.mark(st);  // group bookkeeping
+        h->n_stage = clock.read(h->stage_ms, 16);
         h->info.setup_ms = tm.stop_ms();
         OBK_CUDA(cudaStreamSynchronize(st));
     } catch (...) {
@@ -655,6 +665,14 @@ obk_status obk_get_row_norms(const obk_handle* h, double* nsq)
 {
     if (!h) { set_last_error("handle is NULL"); return OBK_ERR_INVALID; }
     return copy_out(h, nsq, h->L.nsq.p, h->N * sizeof(double));
+}
+
+int32_t obk_get_setup_profile(const obk_handle* h, double* ms, int32_t cap)
+{
+    if (!h || !ms || cap <= 0) return 0;
+    int n = std::min<int>(h->n_stage, cap);
+    for (int i = 0; i < n; ++i) ms[i] = h->stage_ms[i];
+    return n;
 }
 
 obk_status obk_get_info(const obk_handle* h, obk_info* info)

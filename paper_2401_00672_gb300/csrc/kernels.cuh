@@ -7,6 +7,40 @@
 
 namespace obk {
 
+// Stage clock of obk_create: CUDA events recorded on the setup stream.
+struct StageClock {
+    static constexpr int kMax = 16;
+    cudaEvent_t ev[kMax] = {};
+    int n = 0;
+    cudaStream_t st = nullptr;
+    void mark(cudaStream_t s)
+    {
+        if (n >= kMax) return;
+        st = s;
+        if (!ev[n]) cudaEventCreate(&ev[n]);
+        cudaEventRecord(ev[n], s);
+        ++n;
+    }
+    // milliseconds between consecutive marks (n - 1 values)
+    int read(double* ms, int cap)
+    {
+        if (n < 2) return 0;
+        cudaEventSynchronize(ev[n - 1]);
+        int k = 0;
+        for (int i = 1; i < n && k < cap; ++i, ++k) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ev[i - 1], ev[i]);
+            ms[k] = t;
+        }
+        return k;
+    }
+    ~StageClock()
+    {
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
 struct RcmStats {
     int64_t components = 0;
     int64_t levels = 0;
@@ -73,7 +107,7 @@ struct SweepLayout {
 // (paper Section 3.3 at one row per block).
 void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* v, int64_t nnz,
                  double thr, long long spin_limit, int* d_err, SweepLayout& L, bool want_fp32,
-                 cudaStream_t st);
+                 cudaStream_t st, StageClock* clock = nullptr);
 
 // ---- sweep.cu -----------------------------------------------------------------
 

@@ -719,8 +719,11 @@ void permute_csr(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
 
 void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* v, int64_t nnz,
                  double thr, long long spin_limit, int* d_err, SweepLayout& L, bool want_fp32,
-                 cudaStream_t st)
+                 cudaStream_t st, StageClock* clock)
 {
+    auto mark = [&]() {
+        if (clock) clock->mark(st);
+    };
     DevInfo di = dev_info();
     L.N = N;
     L.nnz = nnz;
@@ -751,6 +754,7 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
     }
     exclusive_scan_i64(ccnt.p, cptr.p, N, st);
 
+    mark();
     // 3. pair cosines -> lower conflict lists
     DBuf<int64_t> ub(N, st), bigsz(N, st), bigoff(N + 1, st);
     pair_upper_bound<<<grid_for(N), kBlock, 0, st>>>(N, rp, ci, cptr.p, pos_of.p, ub.p);
@@ -784,6 +788,7 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
     big_key.release();
     big_val.release();
 
+    mark();
     // 4. greedy first-fit colouring
     L.group_of.alloc(N, st);
     OBK_CUDA(cudaMemsetAsync(L.group_of.p, 0x80, N * sizeof(int32_t), st));  // every entry = kUnset
@@ -802,6 +807,7 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
     conf_cnt.release();
     conf_off.release();
 
+    mark();
     // 5. group-major rows
     DBuf<uint64_t> gk(N, st);
     DBuf<uint32_t> gorder(N, st);
@@ -843,6 +849,7 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
                                                    L.grp_v.p, want_fp32 ? L.grp_v32.p : nullptr);
     OBK_CHECK_LAUNCH();
 
+    mark();
     // 6. column mirror: CSC entries stably partitioned by the group of their row
     DBuf<uint64_t> mk(nnz, st);
     DBuf<uint32_t> morder(nnz, st);
@@ -908,6 +915,7 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
         L.mir_val = std::move(nval);
         if (want_fp32) L.mir_val32 = std::move(nval32);
     }
+    mark();
     L.h_gseg_ptr.resize(G + 1);
     OBK_CUDA(cudaMemcpyAsync(L.h_gseg_ptr.data(), L.gseg_ptr.p, (G + 1) * sizeof(int64_t),
                              cudaMemcpyDeviceToHost, st));
