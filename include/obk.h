@@ -141,10 +141,13 @@ OBK_API obk_status obk_get_row_norms(const obk_handle* h, double* nsq);
 OBK_API obk_status obk_get_info(const obk_handle* h, obk_info* info);
 
 /* Device time of the stages of obk_create, in order: (0) upload, validation
- * and extension, (1) bandwidth of the input, (2) Reverse Cuthill-McKee,
- * (3) permutation and its bandwidth, (4) row norms and transposition,
- * (5) pair cosines and conflict lists, (6) greedy grouping, (7) group-major
- * rows, (8) column mirror and segment order, (9) remaining bookkeeping.
+ * and extension, (1) bandwidth of the input, Reverse Cuthill-McKee in four
+ * parts: (2) the graph pattern(A^ + A^T), (3) the (degree, index) ranks and
+ * rank-sorted neighbour lists, (4) the pseudo-peripheral search, (5) the
+ * Cuthill-McKee order and its reversal; then (6) permutation and its
+ * bandwidth, (7) row norms and transposition, (8) pair cosines and conflict
+ * lists, (9) greedy grouping, (10) group-major rows, (11) column mirror and
+ * segment order, (12) remaining bookkeeping.
  * Writes at most cap values to ms (host) and returns how many. */
 OBK_API int32_t obk_get_setup_profile(const obk_handle* h, double* ms, int32_t cap);
 

@@ -186,7 +186,8 @@ class Handle:
         _check(rc, "obk_solve")
         return rc, ko, _info(info)
 
-    SETUP_STAGES = ("upload_validate_extend", "bandwidth_in", "rcm", "permute", "norms_transpose",
+    SETUP_STAGES = ("upload_validate_extend", "bandwidth_in", "rcm_graph", "rcm_ranks", "rcm_search",
+                    "rcm_cuthill_mckee", "permute", "norms_transpose",
                     "pair_cosines", "grouping", "group_rows", "mirror_segments", "bookkeeping")
 
     def setup_profile(self) -> dict:

@@ -387,8 +387,8 @@ obk_status obk_create_on_stream(const obk_csr* A, int64_t m, int64_t n, double t
         clock.mark(st);  // bandwidth of the input
         // Reverse Cuthill-McKee (Section 3.2) and A~ = P A^ P^T (Eq. 3.1)
         h->perm.alloc(N, st);
-        rcm_reorder(N, rp.p, ci.p, nnz, h->perm.p, kDefaultSpins, h->err.p, &h->rcm, st);
-        clock.mark(st);  // Reverse Cuthill-McKee
+        rcm_reorder(N, rp.p, ci.p, nnz, h->perm.p, kDefaultSpins, h->err.p, &h->rcm, st, &clock);
+        clock.mark(st);  // Cuthill-McKee order, reversed
         DBuf<int32_t> iperm(N, st);
         DBuf<int64_t> rpt(N + 1, st);
         DBuf<int32_t> cit(std::max<int64_t>(nnz, 1), st);

@@ -50,19 +50,20 @@ constexpr long long kDefaultSpins = 1LL << 23;
 
 // ---- bounded grid barrier ------------------------------------------------
 //
-// Barrier for kernels launched cooperatively (all blocks co-resident).
-// Arrival is hierarchical: block b increments sub-counter b % 16 (each on its
-// own 128-byte line); the last arriver of a sub-group increments the top
-// counter; the last of those resets the counters and bumps the generation.
-// The atomics are acquire-release at GPU scope, so every block's writes
-// before the barrier are visible to every block after it.  Every wait is
-// bounded: after `limit` polls the block records kDevTimeout in *err and
-// returns false; callers must then leave the kernel.
-constexpr int kBarrierSub = 16;
-constexpr int kBarrierWords = 64 + 32 * kBarrierSub;  // [0] top, [32] generation, [64 + 32 s] sub s
+// Barrier for kernels launched cooperatively (all blocks co-resident).  One
+// 64-bit counter that only grows: thread 0 of each block adds 1 with an
+// acquire-release atomic at GPU scope; the value it gets back tells which
+// barrier episode it joined (old / blocks), and it waits with acquire loads
+// until the counter reaches the end of that episode.  The release/acquire
+// pair makes every block's writes before the barrier visible to every block
+// after it.  No reset and no generation word: one atomic per block on the
+// critical path.  Every wait is bounded: after `limit` polls the block
+// records kDevTimeout in *err and returns false; callers must then leave the
+// kernel.
+constexpr int kBarrierWords = 64;  // [0..1] the counter; the rest unused padding
 
 struct GridBarrier {
-    unsigned int* bar;  // kBarrierWords words, zeroed before the launch
+    unsigned int* bar;  // kBarrierWords words, zeroed before the launch (8-byte aligned)
     int* err;
     long long limit;
 };
@@ -87,6 +88,19 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p)
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ unsigned long long atom_add_acq_rel_gpu_u64(unsigned long long* p,
+                                                                      unsigned long long v)
+{
+    unsigned long long old;
+    asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_gpu_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 
 __device__ __forceinline__ bool grid_sync(const GridBarrier& gb)
 {
@@ -98,33 +112,18 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& gb)
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned nb = gridDim.x * gridDim.y * gridDim.z;
-        unsigned ngroups = nb < (unsigned)kBarrierSub ? nb : (unsigned)kBarrierSub;
-        unsigned s = blockIdx.x % ngroups;
-        unsigned gsize = (nb - s + ngroups - 1) / ngroups;
-        unsigned* top = gb.bar;
-        unsigned* gen_p = gb.bar + 32;
-        unsigned* sub = gb.bar + 64 + 32 * s;
-        unsigned gen = ld_acquire_gpu(gen_p);
-        bool released = false;
-        if (atom_add_acq_rel_gpu(sub, 1u) == gsize - 1) {
-            *reinterpret_cast<volatile unsigned*>(sub) = 0u;
-            if (atom_add_acq_rel_gpu(top, 1u) == ngroups - 1) {
-                *reinterpret_cast<volatile unsigned*>(top) = 0u;
-                atom_add_acq_rel_gpu(gen_p, 1u);
-                released = true;
+        unsigned long long nb = (unsigned long long)gridDim.x * gridDim.y * gridDim.z;
+        unsigned long long* ctr = reinterpret_cast<unsigned long long*>(gb.bar);
+        unsigned long long old = atom_add_acq_rel_gpu_u64(ctr, 1ull);
+        unsigned long long target = (old / nb + 1ull) * nb;
+        long long spins = 0;
+        while (ld_acquire_gpu_u64(ctr) < target) {
+            if (++spins > gb.limit || ((spins & 63) == 0 && ld_volatile_i32(gb.err) != 0)) {
+                atomicCAS(gb.err, 0, (int)kDevTimeout);
+                ok = 0;
+                break;
             }
-        }
-        if (!released) {
-            long long spins = 0;
-            while (ld_acquire_gpu(gen_p) == gen) {
-                if (++spins > gb.limit || ld_volatile_i32(gb.err) != 0) {
-                    atomicCAS(gb.err, 0, (int)kDevTimeout);
-                    ok = 0;
-                    break;
-                }
-                if (spins > 20000) __nanosleep(32);
-            }
+            if (spins > 20000) __nanosleep(32);
         }
         if (ld_volatile_i32(gb.err) != 0) ok = 0;
         s_ok = ok;

@@ -49,8 +49,11 @@ struct RcmStats {
 };
 
 // perm[k] = vertex placed at position k by Reverse Cuthill-McKee (rcm.cu).
+// With a clock, marks the end of: the symmetric graph, the rank orders, the
+// pseudo-peripheral search and the Cuthill-McKee order.
 void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, int32_t* perm,
-                 long long spin_limit, int* d_err, RcmStats* stats, cudaStream_t st);
+                 long long spin_limit, int* d_err, RcmStats* stats, cudaStream_t st,
+                 StageClock* clock = nullptr);
 
 // Sorted neighbour lists of pattern(A + A^T) without self loops (rcm.cu).
 void build_sym_graph(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, DBuf<int64_t>& gp,

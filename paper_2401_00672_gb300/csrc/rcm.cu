@@ -665,14 +665,18 @@ void build_sym_graph(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nn
 }
 
 void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, int32_t* perm,
-                 long long spin_limit, int* d_err, RcmStats* stats, cudaStream_t st)
+                 long long spin_limit, int* d_err, RcmStats* stats, cudaStream_t st, StageClock* clock)
 {
+    auto mark = [&]() {
+        if (clock) clock->mark(st);
+    };
     DevInfo di = dev_info();
     // 1. symmetric graph
     DBuf<int64_t> gp;
     DBuf<int32_t> adj;
     build_sym_graph(N, rp, ci, nnz, gp, adj, st);
     int64_t M = read_scalar(gp.p + N, st);
+    mark();
 
     // 2. ranks in (deg, index) order
     // stable sort by degree of the vertices in index order = (degree, index) order
@@ -697,6 +701,7 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
     }
     ak.release();
     const int32_t* adj_r = reinterpret_cast<const int32_t*>(av.p);
+    mark();
 
     // 4. first search from the global minimum-(deg, index) vertex; if it
     //    reaches every vertex the graph is connected and no labelling is needed
@@ -794,6 +799,7 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
     }
     dist.release(); ecc.release(); cand_r.release(); ecc_root.release(); cand.release();
     active.release(); src.release();
+    mark();
 
     // 6. Cuthill-McKee levels into one queue, then the per-component order
     DBuf<int32_t> vis(N, st), claim(N, st);
