@@ -270,22 +270,76 @@ struct BfsParams {
     GridBarrier gb;
 };
 
-// One warp per frontier vertex, lanes over its neighbours.  Newly reached
-// vertices are collected per block in shared memory and appended to the next
-// frontier with one global atomic per block and level (direct appends when the
-// block buffer is full).
+// Frontier vertices are split into contiguous chunks, one per block, so the
+// scattered loads of a small frontier still spread over every SM.  Inside a
+// block a group of G lanes takes one vertex, G the largest power of two up to
+// 32 with chunk * G <= block size, and every lane loads kNbRound neighbours
+// per round (independent loads): a level then costs a few dependent L2 round
+// trips.  Vertices with more than kHeavyDeg neighbours that a small group
+// would need several rounds for go to a per-block list that whole warps
+// process afterwards.  Nothing inside the group loops is warp-collective.
+// Newly reached vertices are collected per block in shared memory and
+// appended to the next frontier with one global atomic per block and level
+// (direct appends when the block buffer is full).
 constexpr int kBfsBuf = 2048;
+constexpr int kHeavyDeg = 32;
+constexpr int kHeavyBuf = 512;
+constexpr int kNbRound = 4;
+
+__device__ __forceinline__ int group_lanes(int64_t items)
+{
+    int G = 32;
+    while (G > 1 && (int64_t)G * items > (int64_t)blockDim.x) G >>= 1;
+    return G;
+}
+
+// deferred to a warp: many neighbours for a group of G lanes
+__device__ __forceinline__ bool heavy_for(int64_t deg, int G)
+{
+    return deg > kHeavyDeg && deg > 2 * kNbRound * G;
+}
+
+__device__ __forceinline__ void bfs_reach(const BfsParams& p, int32_t w, int L, int32_t* sbuf, int* s_cnt,
+                                          int64_t* cnext, int32_t* nxt)
+{
+    if (atomicCAS(p.dist + w, kUnvisited, L + 1) != kUnvisited) return;
+    int slot = atomicAdd(s_cnt, 1);
+    if (slot < kBfsBuf) {
+        sbuf[slot] = w;
+    } else {
+        unsigned long long pos = atomicAdd((unsigned long long*)cnext, 1ull);
+        if ((int64_t)pos < p.N) nxt[pos] = w;
+        else atomicCAS(p.gb.err, 0, (int)kDevOverflow);
+    }
+}
+
+// lanes lg, lg + G, ... of a group of G over the neighbours [b, e) of a vertex
+__device__ __forceinline__ void bfs_expand(const BfsParams& p, int64_t b, int64_t e, int G, int lg, int L,
+                                           int32_t* sbuf, int* s_cnt, int64_t* cnext, int32_t* nxt)
+{
+    for (int64_t q0 = b + lg; q0 < e; q0 += (int64_t)kNbRound * G) {
+        int32_t w[kNbRound];
+        int32_t d[kNbRound];
+#pragma unroll
+        for (int t = 0; t < kNbRound; ++t) w[t] = q0 + (int64_t)t * G < e ? p.adj[q0 + (int64_t)t * G] : -1;
+#pragma unroll
+        for (int t = 0; t < kNbRound; ++t) d[t] = w[t] >= 0 ? ld_volatile_i32(p.dist + w[t]) : 0;
+#pragma unroll
+        for (int t = 0; t < kNbRound; ++t)
+            if (w[t] >= 0 && d[t] == kUnvisited) bfs_reach(p, w[t], L, sbuf, s_cnt, cnext, nxt);
+    }
+}
 
 __global__ void __launch_bounds__(kCoopBlock) bfs_levels(BfsParams p)
 {
     __shared__ int32_t sbuf[kBfsBuf];
-    __shared__ int s_cnt;
+    __shared__ int32_t heavy[kHeavyBuf];
+    __shared__ int s_cnt, s_nheavy;
     __shared__ long long s_base;
-    int lane = threadIdx.x & 31;
-    unsigned lt = (1u << lane) - 1u;
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int wpb = kCoopBlock / kWarp;
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t nth = (int64_t)gridDim.x * blockDim.x;
-    int64_t gw = tid >> 5, nw = nth >> 5;
     for (int64_t k = tid; k < p.nsrc; k += nth) {
         p.dist[p.sources[k]] = 0;
         p.qa[k] = p.sources[k];
@@ -303,45 +357,27 @@ __global__ void __launch_bounds__(kCoopBlock) bfs_levels(BfsParams p)
             if (L > 0) p.cnt[3] += ncur;
         }
         int64_t* cnext = p.cnt + ((L + 1) % 3);
-        if (threadIdx.x == 0) s_cnt = 0;
+        if (threadIdx.x == 0) { s_cnt = 0; s_nheavy = 0; }
         __syncthreads();
-        for (int64_t k = gw; k < ncur; k += nw) {
+        int64_t chunk = ceil_div(ncur, (int64_t)gridDim.x);
+        int64_t c0 = (int64_t)blockIdx.x * chunk;
+        int64_t c1 = c0 + chunk < ncur ? c0 + chunk : ncur;
+        const int G = group_lanes(c1 - c0);
+        const int lg = threadIdx.x & (G - 1);
+        const int ipp = blockDim.x / G;
+        for (int64_t k = c0 + threadIdx.x / G; k < c1; k += ipp) {
             int32_t u = cur[k];
             int64_t b = p.gp[u], e = p.gp[u + 1];
-            for (int64_t base = b; base < e; base += 32) {
-                int64_t q = base + lane;
-                bool won = false;
-                int32_t w = 0;
-                if (q < e) {
-                    w = p.adj[q];
-                    if (ld_volatile_i32(p.dist + w) == kUnvisited)
-                        won = atomicCAS(p.dist + w, kUnvisited, L + 1) == kUnvisited;
-                }
-                unsigned m = __ballot_sync(0xffffffffu, won);
-                if (m) {
-                    // slots below kBfsBuf go to the block buffer (each written by
-                    // exactly one lane); the overflow is appended directly
-                    int leader = __ffs(m) - 1;
-                    int sp = 0;
-                    if (lane == leader) sp = atomicAdd(&s_cnt, __popc(m));
-                    sp = __shfl_sync(0xffffffffu, sp, leader);
-                    int slot = sp + __popc(m & lt);
-                    bool in_buf = won && slot < kBfsBuf;
-                    if (in_buf) sbuf[slot] = w;
-                    unsigned over = __ballot_sync(0xffffffffu, won && !in_buf);
-                    if (over) {
-                        int l2 = __ffs(over) - 1;
-                        unsigned long long pos0 = 0;
-                        if (lane == l2) pos0 = atomicAdd((unsigned long long*)cnext, (unsigned long long)__popc(over));
-                        pos0 = __shfl_sync(0xffffffffu, pos0, l2);
-                        if (won && !in_buf) {
-                            int64_t pos = (int64_t)pos0 + __popc(over & lt);
-                            if (pos < p.N) nxt[pos] = w;
-                            else atomicCAS(p.gb.err, 0, (int)kDevOverflow);
-                        }
-                    }
-                }
+            if (heavy_for(e - b, G) && k - c0 < kHeavyBuf) {  // at most kHeavyBuf such vertices
+                if (lg == 0) heavy[atomicAdd(&s_nheavy, 1)] = u;
+                continue;
             }
+            bfs_expand(p, b, e, G, lg, L, sbuf, &s_cnt, cnext, nxt);
+        }
+        __syncthreads();
+        for (int h = wid; h < s_nheavy; h += wpb) {
+            int32_t u = heavy[h];
+            bfs_expand(p, p.gp[u], p.gp[u + 1], 32, lane, L, sbuf, &s_cnt, cnext, nxt);
         }
         __syncthreads();
         int nb = s_cnt < kBfsBuf ? s_cnt : kBfsBuf;
@@ -427,180 +463,376 @@ __global__ void gather_active_sources(int64_t C, const int32_t* which, const int
 //
 // All levels live back to back in one queue Q: level L is Q[lo, hi).  Level 0
 // holds the component roots in component order; inside every level the
-// vertices are ordered by (component, CM position).  A vertex w reached from
-// level L takes as parent the queue index of its earliest frontier neighbour
-// (atomicMin over queue indices; only same-component vertices compete), and
-// the children of each frontier vertex are appended in rank order after an
-// exclusive scan of the child counts.  So Q lists, level by level, every
-// component's Cuthill-McKee order interleaved; a stable partition of Q by
-// component gives the concatenated order (nothing to do when connected).
+// vertices are ordered by (component, CM position).  So Q lists, level by
+// level, every component's Cuthill-McKee order interleaved; a stable partition
+// of Q by component gives the concatenated order (nothing to do when
+// connected).
+//
+// Priorities.  Every placed vertex v carries a 64-bit priority P(v) that
+// orders vertices exactly as their queue positions do: a root gets its
+// component index c (< 2^32) and the idx-th child (in rank order) of the
+// vertex at queue position k gets ((k + 1) << 32) | idx.  Within a level this
+// is (parent position, rank) order, the CM rule; every priority of level L+1
+// exceeds every priority of level L because parents of level L+1 sit after
+// those of level L.  claim[w] = min P over the vertices that have reached w,
+// so after the vertices of level L have claimed, claim[w] = P(parent of w)
+// for every w of level L+1 (later claims are larger and change nothing).
+//
+// Per level: (A) each frontier vertex u counts its children {w : claim[w] ==
+// P(u)} -- all its neighbours lie in levels L-1..L+1, whose claims no longer
+// change -- gives each child its priority and lets it claim its own
+// neighbours at once; (B) a look-back over the per-block child totals of
+// this level (tagged with the level) gives the block's offset, and the
+// children are written to Q in order; then one grid barrier.
 
 struct CmParams {
     int64_t N;
     const int64_t* gp;
-    const int32_t* adj_r;    // adjacency sorted by rank
-    const int32_t* roots;    // C roots in component order
+    const int32_t* adj_r;            // adjacency sorted by rank
+    const int32_t* roots;            // C roots in component order
     int64_t C;
-    int32_t* vis;            // N, kUnvisited
-    int32_t* claim;          // N, INT32_MAX
-    int32_t* Q;              // N
-    int64_t* cnt;            // N: per frontier vertex, block-local offset of its children
-    int64_t* bsum;           // gridDim + 1
-    int64_t* nlevels;        // out: [0] levels, [1] vertices placed
+    unsigned long long* claim;       // N, all ones
+    unsigned long long* prio;        // N
+    int32_t* Q;                      // N
+    int64_t* cnt;                    // N: per frontier vertex, block-local offset of its children
+    unsigned long long* agg;         // gridDim: ((level + 1) << 40) | block total, zeroed
+    int64_t* ntot;                   // 2: size of the next level (alternating slots)
+    int64_t* nlevels;                // out: [0] levels, [1] vertices placed
     GridBarrier gb;
 };
 
-// Sum of the block totals of all blocks (*total) and of the blocks before this
-// one (*before), computed redundantly by every block (thread 0 gets both).
-__device__ __forceinline__ void block_offsets(const int64_t* bsum, int64_t* before, int64_t* total)
+constexpr int kAggShift = 40;  // a block total is below 2^31; the tag is (level + 1) mod 2^24
+constexpr unsigned long long kAggTagMask = (1ull << (64 - kAggShift)) - 1ull;
+
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v)
 {
-    __shared__ int64_t s_b[kCoopBlock / kWarp], s_t[kCoopBlock / kWarp];
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int64_t sb = 0, stot = 0;
-    for (unsigned t = threadIdx.x; t < gridDim.x; t += blockDim.x) {
-        int64_t v = bsum[t];
-        stot += v;
-        if (t < blockIdx.x) sb += v;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        sb += __shfl_xor_sync(0xffffffffu, sb, o);
-        stot += __shfl_xor_sync(0xffffffffu, stot, o);
-    }
-    if (lane == 0) { s_b[wid] = sb; s_t[wid] = stot; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int64_t x = 0, y = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { x += s_b[w]; y += s_t[w]; }
-        *before = x;
-        *total = y;
-    }
-    __syncthreads();
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// Claims of the unvisited neighbours of vertex u placed at queue index k.
-__device__ __forceinline__ void claim_neighbours(const CmParams& p, int32_t u, int64_t k, int lane)
+// Vertex w with priority pw claims its neighbours: lanes lg, lg + G, ... of
+// a group of G, kNbRound independent loads per lane and round; neighbours
+// already claimed lower are skipped without an atomic.
+__device__ __forceinline__ void claim_group(const CmParams& p, int64_t b, int64_t e, int G, int lg,
+                                            unsigned long long pw)
 {
+    for (int64_t q0 = b + lg; q0 < e; q0 += (int64_t)kNbRound * G) {
+        int32_t x[kNbRound];
+        unsigned long long c[kNbRound];
+#pragma unroll
+        for (int t = 0; t < kNbRound; ++t) x[t] = q0 + (int64_t)t * G < e ? p.adj_r[q0 + (int64_t)t * G] : -1;
+#pragma unroll
+        for (int t = 0; t < kNbRound; ++t) c[t] = x[t] >= 0 ? ld_relaxed_u64(p.claim + x[t]) : 0ull;
+#pragma unroll
+        for (int t = 0; t < kNbRound; ++t)
+            if (x[t] >= 0 && c[t] > pw) atomicMin(p.claim + x[t], pw);
+    }
+}
+
+constexpr int kStage = 8;  // children of one frontier vertex kept in shared memory
+
+struct CmShared {
+    int32_t sj[kStage][kCoopBlock];  // adjacency offset of a staged child
+    int32_t sw[kStage][kCoopBlock];  // the child
+    int32_t scnt[kCoopBlock];        // children per frontier vertex of the chunk
+    int64_t soff[kCoopBlock];        // their block-local offsets
+    int32_t heavy[kHeavyBuf];
+    int64_t wsum[kCoopBlock / kWarp];
+    int64_t s_tot, s_before;
+    int s_fail, s_nheavy;
+};
+
+// Children of frontier vertex k (priority pu, neighbours [b, e)) counted by a
+// group of G lanes; staged mode records (offset, child) pairs per vertex in
+// shared memory, otherwise counts go to p.cnt[k].
+__device__ __forceinline__ void cm_count(const CmParams& p, CmShared& sh, int64_t b, int64_t e, int G, int lg,
+                                         unsigned long long pu, int64_t k, int kl, bool staged)
+{
+    for (int64_t q0 = b + lg; q0 < e; q0 += (int64_t)kNbRound * G) {
+        int32_t w[kNbRound];
+        unsigned long long c[kNbRound];
+#pragma unroll
+        for (int t = 0; t < kNbRound; ++t) w[t] = q0 + (int64_t)t * G < e ? p.adj_r[q0 + (int64_t)t * G] : -1;
+#pragma unroll
+        for (int t = 0; t < kNbRound; ++t) c[t] = w[t] >= 0 ? ld_relaxed_u64(p.claim + w[t]) : ~0ull;
+#pragma unroll
+        for (int t = 0; t < kNbRound; ++t) {
+            if (w[t] < 0 || c[t] != pu) continue;
+            if (staged) {
+                int slot = atomicAdd(&sh.scnt[kl], 1);
+                if (slot < kStage) {
+                    sh.sj[slot][kl] = (int32_t)(q0 + (int64_t)t * G - b);
+                    sh.sw[slot][kl] = w[t];
+                }
+            } else {
+                atomicAdd((unsigned long long*)(p.cnt + k), 1ull);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void cm_place(const CmParams& p, int64_t pos, int32_t w, int64_t k, int64_t idx)
+{
+    if (pos < p.N) p.Q[pos] = w;
+    else atomicCAS(p.gb.err, 0, (int)kDevOverflow);
+    p.prio[w] = ((unsigned long long)(k + 1) << 32) | (unsigned long long)idx;
+}
+
+// Children of frontier vertex k in rank (adjacency) order, found again from
+// the claims by one thread.
+__device__ void cm_rescan_thread(const CmParams& p, int64_t k, int32_t u, int64_t o)
+{
+    unsigned long long pu = p.prio[u];
     int64_t b = p.gp[u], e = p.gp[u + 1];
-    for (int64_t q = b + lane; q < e; q += 32) {
-        int32_t w = p.adj_r[q];
-        if (ld_volatile_i32(p.vis + w) == kUnvisited) atomicMin(p.claim + w, (int32_t)k);
+    int64_t i = 0;
+    for (int64_t q0 = b; q0 < e; q0 += 2 * kNbRound) {
+        int32_t w[2 * kNbRound];
+        unsigned long long c[2 * kNbRound];
+#pragma unroll
+        for (int t = 0; t < 2 * kNbRound; ++t) w[t] = q0 + t < e ? p.adj_r[q0 + t] : -1;
+#pragma unroll
+        for (int t = 0; t < 2 * kNbRound; ++t) c[t] = w[t] >= 0 ? ld_relaxed_u64(p.claim + w[t]) : ~0ull;
+#pragma unroll
+        for (int t = 0; t < 2 * kNbRound; ++t)
+            if (w[t] >= 0 && c[t] == pu) {
+                cm_place(p, o + i, w[t], k, i);
+                ++i;
+            }
     }
 }
 
-// Per level two barriers: (1) child counts and block-local offsets,
-// (2) placement of the children, each of which claims its own unvisited
-// neighbours at once.  A claim on a vertex of the same new level is harmless:
-// that vertex is marked visited before the next count, and only unvisited
-// vertices are counted as children.
+// The same by a whole warp (ballots keep the order).
+__device__ void cm_rescan_warp(const CmParams& p, int64_t k, int32_t u, int64_t o, int lane)
+{
+    unsigned lt = (1u << lane) - 1u;
+    unsigned long long pu = p.prio[u];
+    int64_t b = p.gp[u], e = p.gp[u + 1];
+    int64_t i = 0;
+    for (int64_t base = b; base < e; base += 32) {
+        int64_t q = base + lane;
+        int32_t w = 0;
+        bool child = false;
+        if (q < e) {
+            w = p.adj_r[q];
+            child = ld_relaxed_u64(p.claim + w) == pu;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, child);
+        if (child) cm_place(p, o + i + __popc(m & lt), w, k, i + __popc(m & lt));
+        i += __popc(m);
+    }
+}
+
+__device__ __forceinline__ void cswap(int32_t& ja, int32_t& wa, int32_t& jb, int32_t& wb)
+{
+    if (jb < ja) {
+        int32_t t = ja; ja = jb; jb = t;
+        t = wa; wa = wb; wb = t;
+    }
+}
+
 __global__ void __launch_bounds__(kCoopBlock) cm_levels(CmParams p)
 {
-    __shared__ int64_t s_tot;
-    __shared__ int64_t wsum[kCoopBlock / kWarp];
-    __shared__ int64_t s_before, s_total;
+    __shared__ CmShared sh;
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned lt = (1u << lane) - 1u;
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t nth = (int64_t)gridDim.x * blockDim.x;
     int64_t gw = tid >> 5, nw = nth >> 5;
     const int wpb = kCoopBlock / kWarp;
     for (int64_t c = tid; c < p.C; c += nth) {
-        p.Q[c] = p.roots[c];
-        p.vis[p.roots[c]] = 0;
+        int32_t r = p.roots[c];
+        p.Q[c] = r;
+        p.prio[r] = (unsigned long long)c;
+        p.claim[r] = (unsigned long long)c;
     }
     if (!grid_sync(p.gb)) return;
-    for (int64_t c = gw; c < p.C; c += nw) claim_neighbours(p, p.roots[c], c, lane);
+    for (int64_t c = gw; c < p.C; c += nw) {
+        int32_t r = p.roots[c];
+        claim_group(p, p.gp[r], p.gp[r + 1], 32, lane, (unsigned long long)c);
+    }
     if (!grid_sync(p.gb)) return;
     int64_t lo = 0, hi = p.C;
     int L = 0;
     while (hi > lo) {
         int64_t F = hi - lo;
-        // (1) child counts of this block's chunk of the frontier, block-local scan
         int64_t chunk = ceil_div(F, (int64_t)gridDim.x);
         int64_t c0 = lo + (int64_t)blockIdx.x * chunk;
         int64_t c1 = c0 + chunk < hi ? c0 + chunk : hi;
-        for (int64_t k = c0 + wid; k < c1; k += wpb) {
-            int32_t u = p.Q[k];
-            int64_t b = p.gp[u], e = p.gp[u + 1];
-            int64_t n_child = 0;
-            for (int64_t base = b; base < e; base += 32) {
-                int64_t q = base + lane;
-                bool child = false;
-                if (q < e) {
-                    int32_t w = p.adj_r[q];
-                    child = p.vis[w] == kUnvisited && p.claim[w] == (int32_t)k;
+        int64_t nit = c1 > c0 ? c1 - c0 : 0;
+        const bool staged = nit <= (int64_t)blockDim.x;  // then chunk vertex kl has slot kl
+        if (threadIdx.x == 0) sh.s_nheavy = 0;
+        if (staged) sh.scnt[threadIdx.x] = 0;
+        else
+            for (int64_t k = c0 + threadIdx.x; k < c1; k += blockDim.x) p.cnt[k] = 0;
+        __syncthreads();
+        // (A) child counts: children of u are the w with claim[w] == P(u)
+        {
+            const int G = group_lanes(nit);
+            const int lg = threadIdx.x & (G - 1);
+            const int ipp = blockDim.x / G;
+            for (int64_t k = c0 + threadIdx.x / G; k < c1; k += ipp) {
+                int kl = (int)(k - c0);
+                int32_t u = p.Q[k];
+                unsigned long long pu = p.prio[u];
+                int64_t b = p.gp[u], e = p.gp[u + 1];
+                if (heavy_for(e - b, G) && kl < kHeavyBuf) {
+                    if (lg == 0) sh.heavy[atomicAdd(&sh.s_nheavy, 1)] = kl;
+                    continue;
                 }
-                n_child += __popc(__ballot_sync(0xffffffffu, child));
+                cm_count(p, sh, b, e, G, lg, pu, k, kl, staged);
             }
-            if (lane == 0) p.cnt[k] = n_child;
         }
         __syncthreads();
+        for (int h = wid; h < sh.s_nheavy; h += wpb) {
+            int kl = sh.heavy[h];
+            int64_t k = c0 + kl;
+            int32_t u = p.Q[k];
+            cm_count(p, sh, p.gp[u], p.gp[u + 1], 32, lane, p.prio[u], k, kl, staged);
+        }
+        __syncthreads();
+        // block-local exclusive scan of the child counts
         int64_t carry = 0;
         for (int64_t base = c0; base < c1; base += blockDim.x) {
             int64_t k = base + threadIdx.x;
-            int64_t v = k < c1 ? p.cnt[k] : 0;
+            int64_t v = k < c1 ? (staged ? (int64_t)sh.scnt[k - c0] : p.cnt[k]) : 0;
             int64_t inc = v;
             for (int o = 1; o < 32; o <<= 1) {
                 int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
                 if (lane >= o) inc += t;
             }
-            if (lane == 31) wsum[wid] = inc;
+            if (lane == 31) sh.wsum[wid] = inc;
             __syncthreads();
             if (threadIdx.x == 0) {
                 int64_t run = 0;
                 for (int w = 0; w < wpb; ++w) {
-                    int64_t t = wsum[w];
-                    wsum[w] = run;
+                    int64_t t = sh.wsum[w];
+                    sh.wsum[w] = run;
                     run += t;
                 }
-                s_tot = run;
+                sh.s_tot = run;
             }
             __syncthreads();
-            if (k < c1) p.cnt[k] = carry + wsum[wid] + inc - v;
-            carry += s_tot;
+            if (k < c1) {
+                int64_t off = carry + sh.wsum[wid] + inc - v;
+                if (staged) sh.soff[k - c0] = off;
+                else p.cnt[k] = off;
+            }
+            carry += sh.s_tot;
             __syncthreads();
         }
-        if (threadIdx.x == 0) p.bsum[blockIdx.x] = carry;
+        // look-back: publish this block's total, add up the earlier blocks'
+        const unsigned long long ltag = (unsigned long long)(L + 1) & kAggTagMask;
+        if (threadIdx.x == 0) {
+            sh.s_fail = 0;
+            sh.s_nheavy = 0;
+            st_release_u64(p.agg + blockIdx.x, (ltag << kAggShift) | (unsigned long long)carry);
+        }
+        __syncthreads();
+        int64_t before = 0;
+        for (unsigned j = threadIdx.x; j < blockIdx.x; j += blockDim.x) {
+            long long spins = 0;
+            unsigned long long a;
+            for (;;) {
+                asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(a) : "l"(p.agg + j) : "memory");
+                if ((a >> kAggShift) == ltag) break;
+                if (++spins > p.gb.limit || ((spins & 63) == 0 && ld_volatile_i32(p.gb.err) != 0)) {
+                    atomicCAS(p.gb.err, 0, (int)kDevTimeout);
+                    sh.s_fail = 1;
+                    break;
+                }
+                if (spins > 20000) __nanosleep(32);
+            }
+            before += (int64_t)(a & ((1ull << kAggShift) - 1ull));
+        }
+        for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
+        if (lane == 0) sh.wsum[wid] = before;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t x = 0;
+            for (int w = 0; w < wpb; ++w) x += sh.wsum[w];
+            sh.s_before = x;
+            if (blockIdx.x == gridDim.x - 1) p.ntot[L & 1] = x + carry;
+        }
+        __syncthreads();
+        if (sh.s_fail) return;
+        int64_t boff = sh.s_before;
+        if (boff < 0 || hi + boff + carry > p.N) {  // cannot happen for a valid queue; stop before any overrun
+            if (threadIdx.x == 0) atomicCAS(p.gb.err, 0, (int)kDevOverflow);
+            return;
+        }
+        const int64_t base_pos = hi + boff;
+        // (B) the children in order at base_pos + offset + idx with priority
+        // ((k + 1) << 32) | idx: staged lists are sorted by adjacency offset
+        // (= rank order) and copied; the others are found again from the
+        // claims, which no longer change for these vertices
+        for (int64_t k = c0 + threadIdx.x; k < c1; k += blockDim.x) {
+            int kl = (int)(k - c0);
+            if (staged && sh.scnt[kl] <= kStage) {
+                int n = sh.scnt[kl];
+                int64_t o = base_pos + sh.soff[kl];
+                int32_t j[kStage], w[kStage];
+#pragma unroll
+                for (int i = 0; i < kStage; ++i) {
+                    j[i] = i < n ? sh.sj[i][kl] : INT32_MAX;
+                    w[i] = i < n ? sh.sw[i][kl] : 0;
+                }
+#pragma unroll
+                for (int r = 0; r < kStage; ++r)  // odd-even transposition sort of 8
+#pragma unroll
+                    for (int i = r & 1; i + 1 < kStage; i += 2) cswap(j[i], w[i], j[i + 1], w[i + 1]);
+#pragma unroll
+                for (int i = 0; i < kStage; ++i)
+                    if (i < n) cm_place(p, o + i, w[i], k, i);
+                continue;
+            }
+            int32_t u = p.Q[k];
+            int64_t o = base_pos + (staged ? sh.soff[kl] : p.cnt[k]);
+            if (p.gp[u + 1] - p.gp[u] > kHeavyDeg && kl < kHeavyBuf) {
+                sh.heavy[atomicAdd(&sh.s_nheavy, 1)] = kl;
+                continue;
+            }
+            cm_rescan_thread(p, k, u, o);
+        }
+        __syncthreads();
+        for (int h = wid; h < sh.s_nheavy; h += wpb) {
+            int kl = sh.heavy[h];
+            int64_t k = c0 + kl;
+            int64_t o = base_pos + (staged ? sh.soff[kl] : p.cnt[k]);
+            cm_rescan_warp(p, k, p.Q[k], o, lane);
+        }
+        __syncthreads();
+        // (C) the new vertices of this block claim their neighbours
+        if (threadIdx.x == 0) sh.s_nheavy = 0;
+        __syncthreads();
+        {
+            const int G = group_lanes(carry);
+            const int lg = threadIdx.x & (G - 1);
+            const int ipp = blockDim.x / G;
+            for (int64_t j = threadIdx.x / G; j < carry; j += ipp) {
+                int32_t w = p.Q[base_pos + j];
+                int64_t b = p.gp[w], e = p.gp[w + 1];
+                if (heavy_for(e - b, G) && j < kHeavyBuf) {
+                    if (lg == 0) sh.heavy[atomicAdd(&sh.s_nheavy, 1)] = (int32_t)j;
+                    continue;
+                }
+                claim_group(p, b, e, G, lg, p.prio[w]);
+            }
+        }
+        __syncthreads();
+        for (int h = wid; h < sh.s_nheavy; h += wpb) {
+            int32_t w = p.Q[base_pos + sh.heavy[h]];
+            claim_group(p, p.gp[w], p.gp[w + 1], 32, lane, p.prio[w]);
+        }
         if (!grid_sync(p.gb)) return;
-        block_offsets(p.bsum, &s_before, &s_total);
-        int64_t nf = s_total;
-        if (nf < 0 || hi + nf > p.N) {  // cannot happen for a valid queue; stop before any overrun
+        int64_t nf = *(volatile int64_t*)(p.ntot + (L & 1));
+        if (nf < 0 || hi + nf > p.N) {
             if (tid == 0) atomicCAS(p.gb.err, 0, (int)kDevOverflow);
             return;
         }
-        // (2) children of this block's chunk, in rank order, then their claims
-        int64_t boff = s_before;
-        for (int64_t k = c0 + wid; k < c1; k += wpb) {
-            int32_t u = p.Q[k];
-            int64_t b = p.gp[u], e = p.gp[u + 1];
-            int64_t o = hi + boff + p.cnt[k];
-            for (int64_t base = b; base < e; base += 32) {
-                int64_t q = base + lane;
-                bool child = false;
-                int32_t w = 0;
-                if (q < e) {
-                    w = p.adj_r[q];
-                    child = p.vis[w] == kUnvisited && p.claim[w] == (int32_t)k;
-                }
-                unsigned m = __ballot_sync(0xffffffffu, child);
-                if (child) {
-                    int64_t pos = o + __popc(m & lt);
-                    if (pos < p.N) p.Q[pos] = w;
-                    else atomicCAS(p.gb.err, 0, (int)kDevOverflow);
-                    p.vis[w] = L + 1;
-                }
-                // each new vertex claims its unvisited neighbours (the whole warp
-                // walks the new vertices of this chunk one by one)
-                while (m) {
-                    int src = __ffs(m) - 1;
-                    m &= m - 1;
-                    int32_t wn = __shfl_sync(0xffffffffu, w, src);
-                    int64_t posn = o + __popc(__ballot_sync(0xffffffffu, child) & ((1u << src) - 1u));
-                    claim_neighbours(p, wn, posn, lane);
-                }
-                o += __popc(__ballot_sync(0xffffffffu, child));
-            }
-        }
-        if (!grid_sync(p.gb)) return;
         lo = hi;
         hi = hi + nf;
         ++L;
@@ -802,15 +1034,15 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
     mark();
 
     // 6. Cuthill-McKee levels into one queue, then the per-component order
-    DBuf<int32_t> vis(N, st), claim(N, st);
-    DBuf<int64_t> ccnt(N, st), nl(2, st);
+    DBuf<unsigned long long> claim(N, st), prio(N, st);
+    DBuf<int64_t> ccnt(N, st), nl(2, st), ntot(2, st);
     int32_t* Q = qa.p;
-    OBK_CUDA(cudaMemsetAsync(vis.p, 0xff, N * sizeof(int32_t), st));
-    OBK_CUDA(cudaMemsetAsync(claim.p, 0x7f, N * sizeof(int32_t), st));
+    OBK_CUDA(cudaMemsetAsync(claim.p, 0xff, N * sizeof(unsigned long long), st));
     OBK_CUDA(cudaMemsetAsync(bar.p, 0, kBarrierWords * sizeof(unsigned), st));
     int cm_grid = coop_grid((const void*)cm_levels, kCoopBlock, 0, want);
-    DBuf<int64_t> bsum(cm_grid + 1, st);
-    CmParams cp{N, gp.p, adj_r, roots.p, C, vis.p, claim.p, Q, ccnt.p, bsum.p, nl.p,
+    DBuf<unsigned long long> agg(cm_grid, st);
+    OBK_CUDA(cudaMemsetAsync(agg.p, 0, cm_grid * sizeof(unsigned long long), st));
+    CmParams cp{N, gp.p, adj_r, roots.p, C, claim.p, prio.p, Q, ccnt.p, agg.p, ntot.p, nl.p,
                 GridBarrier{bar.p, d_err, spin_limit}};
     void* args[] = {&cp};
     OBK_COOP_LAUNCH(cm_levels, cm_grid, kCoopBlock, args, st);
