@@ -101,6 +101,27 @@ struct SweepLayout {
     DBuf<int32_t> mir_row;  // nnz_gm, group-major row index
     DBuf<double> mir_val;   // nnz_gm
     DBuf<float> mir_val32;  // nnz_gm
+    // Sliced ELL (SELL-32) copies for the persistent sweep.  Inside each group
+    // the rows (and the mirror segments) are cut into slices of 32 in their
+    // (length, index) order; a slice stores entry j of its 32 rows next to each
+    // other (position base + 32 j + lane), rows shorter than the slice's
+    // longest padded with value 0 and index 0.
+    int64_t ns = 0, nms = 0;         // row slices, mirror slices
+    int64_t sell_nnz = 0, msell_nnz = 0;
+    std::vector<int64_t> h_sl_gptr;  // G+1, first row slice of each group
+    std::vector<int64_t> h_ml_gptr;  // G+1, first mirror slice of each group
+    DBuf<int64_t> sl_gptr, ml_gptr;  // device copies of the two
+    DBuf<int64_t> sl_ptr;            // ns+1, first entry of each row slice
+    DBuf<int64_t> sl_row0;           // ns, group-major index of the slice's first row
+    DBuf<int32_t> sl_nrow;           // ns, rows in the slice (32 except a group's last)
+    DBuf<int32_t> sci;               // sell_nnz, column indices
+    DBuf<double> sv;                 // sell_nnz
+    DBuf<float> sv32;                // sell_nnz (precision form)
+    DBuf<int64_t> ml_ptr;            // nms+1
+    DBuf<int32_t> mcol;              // 32 nms, column of each slice lane (-1: padding)
+    DBuf<int32_t> mrow;              // msell_nnz, group-major row index
+    DBuf<double> mv;                 // msell_nnz
+    DBuf<float> mv32;                // msell_nnz
     // permuted-order results kept for inspection
     DBuf<double> nsq;       // N
     DBuf<int32_t> group_of; // N

@@ -669,6 +669,67 @@ __global__ void mirror_segments(int64_t M, const uint32_t* order, const int32_t*
     }
 }
 
+// ---- sliced ELL (SELL-32) copies of the group-major rows and the mirror ----------
+
+// 32 * (longest row of the slice) for every slice; slices of group g start at
+// slice index sg[g]
+__global__ void sell_lengths(int64_t ns, int64_t G, const int64_t* sg, const int64_t* item_g,
+                             const int64_t* ptr, int64_t* slen, int64_t* row0, int32_t* nrow)
+{
+    GRID_STRIDE(s, ns)
+    {
+        int64_t lo = 0, hi = G;  // group of slice s: largest g with sg[g] <= s
+        while (hi - lo > 1) {
+            int64_t mid = (lo + hi) >> 1;
+            if (sg[mid] <= s) lo = mid;
+            else hi = mid;
+        }
+        int64_t k0 = item_g[lo] + (s - sg[lo]) * 32;
+        int64_t k1 = k0 + 32 < item_g[lo + 1] ? k0 + 32 : item_g[lo + 1];
+        int64_t mx = 0;
+        for (int64_t k = k0; k < k1; ++k) mx = max(mx, ptr[k + 1] - ptr[k]);
+        slen[s] = 32 * mx;
+        if (row0) row0[s] = k0;
+        if (nrow) nrow[s] = (int32_t)(k1 - k0);
+    }
+}
+
+// entries of slice s, lane l: item row0[s] + l (rows) with the padding zeros
+template <class TI>
+__global__ void sell_fill(int64_t ns, const int64_t* sl_ptr, const int64_t* row0, const int32_t* nrow,
+                          const int64_t* ptr, const TI* idx, const double* val, TI* sidx, double* sval,
+                          float* sval32, TI pad_idx)
+{
+    GRID_STRIDE(t, ns * 32)
+    {
+        int64_t s = t >> 5;
+        int lane = (int)(t & 31);
+        int64_t base = sl_ptr[s], len = (sl_ptr[s + 1] - base) >> 5;
+        bool valid = lane < nrow[s];
+        int64_t k = row0[s] + lane;
+        int64_t b = valid ? ptr[k] : 0, rl = valid ? ptr[k + 1] - b : 0;
+        for (int64_t j = 0; j < len; ++j) {
+            int64_t q = base + 32 * j + lane;
+            bool live = j < rl;
+            double a = live ? val[b + j] : 0.0;
+            sidx[q] = live ? idx[b + j] : pad_idx;
+            sval[q] = a;
+            if (sval32) sval32[q] = (float)a;
+        }
+    }
+}
+
+__global__ void sell_mcol(int64_t nms, const int64_t* row0, const int32_t* nrow, const int32_t* seg_col,
+                          int32_t* mcol)
+{
+    GRID_STRIDE(t, nms * 32)
+    {
+        int64_t s = t >> 5;
+        int lane = (int)(t & 31);
+        mcol[t] = lane < nrow[s] ? seg_col[row0[s] + lane] : -1;
+    }
+}
+
 }  // namespace
 
 int64_t max_segment_length(int64_t n, const int64_t* ptr, cudaStream_t st)
@@ -715,6 +776,80 @@ void permute_csr(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
     segmented_sort_u32(rp_t, N, keys.p, src.p, st);
     permute_finish<<<grid_for(nnz), kBlock, 0, st>>>(nnz, keys.p, src.p, v, ci_t, v_t);
     OBK_CHECK_LAUNCH();
+}
+
+namespace {
+
+// slices of each group: host prefix over the (few) groups
+std::vector<int64_t> slice_starts(const std::vector<int64_t>& item_g)
+{
+    int64_t G = (int64_t)item_g.size() - 1;
+    std::vector<int64_t> sg(G + 1, 0);
+    for (int64_t g = 0; g < G; ++g) sg[g + 1] = sg[g] + ceil_div(item_g[g + 1] - item_g[g], (int64_t)32);
+    return sg;
+}
+
+}  // namespace
+
+void build_sell(SweepLayout& L, bool want_fp32, cudaStream_t st)
+{
+    int64_t G = L.G;
+    // rows
+    L.h_sl_gptr = slice_starts(L.h_gptr);
+    int64_t ns = L.h_sl_gptr[G];
+    L.ns = ns;
+    L.sl_gptr.alloc(G + 1, st);
+    DBuf<int64_t>& sg = L.sl_gptr;
+    DBuf<int64_t> slen(std::max<int64_t>(ns, 1), st);
+    OBK_CUDA(cudaMemcpyAsync(sg.p, L.h_sl_gptr.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    L.sl_ptr.alloc(ns + 1, st);
+    L.sl_row0.alloc(std::max<int64_t>(ns, 1), st);
+    L.sl_nrow.alloc(std::max<int64_t>(ns, 1), st);
+    if (ns) {
+        sell_lengths<<<grid_for(ns), kBlock, 0, st>>>(ns, G, sg.p, L.gptr.p, L.grp_rp.p, slen.p, L.sl_row0.p,
+                                                      L.sl_nrow.p);
+        OBK_CHECK_LAUNCH();
+    }
+    exclusive_scan_i64(slen.p, L.sl_ptr.p, ns, st);
+    L.sell_nnz = read_scalar(L.sl_ptr.p + ns, st);
+    L.sci.alloc(std::max<int64_t>(L.sell_nnz, 1), st);
+    L.sv.alloc(std::max<int64_t>(L.sell_nnz, 1), st);
+    if (want_fp32) L.sv32.alloc(std::max<int64_t>(L.sell_nnz, 1), st);
+    if (ns) {
+        sell_fill<int32_t><<<grid_for(ns * 32), kBlock, 0, st>>>(ns, L.sl_ptr.p, L.sl_row0.p, L.sl_nrow.p,
+                                                                 L.grp_rp.p, L.grp_ci.p, L.grp_v.p, L.sci.p,
+                                                                 L.sv.p, want_fp32 ? L.sv32.p : nullptr, 0);
+        OBK_CHECK_LAUNCH();
+    }
+    // mirror segments
+    L.h_ml_gptr = slice_starts(L.h_gseg_ptr);
+    int64_t nms = L.h_ml_gptr[G];
+    L.nms = nms;
+    L.ml_gptr.alloc(G + 1, st);
+    DBuf<int64_t>& mg = L.ml_gptr;
+    DBuf<int64_t> mlen(std::max<int64_t>(nms, 1), st), mrow0(std::max<int64_t>(nms, 1), st);
+    DBuf<int32_t> mnrow(std::max<int64_t>(nms, 1), st);
+    OBK_CUDA(cudaMemcpyAsync(mg.p, L.h_ml_gptr.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    L.ml_ptr.alloc(nms + 1, st);
+    if (nms) {
+        sell_lengths<<<grid_for(nms), kBlock, 0, st>>>(nms, G, mg.p, L.gseg_ptr.p, L.seg_ptr.p, mlen.p, mrow0.p,
+                                                       mnrow.p);
+        OBK_CHECK_LAUNCH();
+    }
+    exclusive_scan_i64(mlen.p, L.ml_ptr.p, nms, st);
+    L.msell_nnz = read_scalar(L.ml_ptr.p + nms, st);
+    L.mcol.alloc(std::max<int64_t>(nms * 32, 1), st);
+    L.mrow.alloc(std::max<int64_t>(L.msell_nnz, 1), st);
+    L.mv.alloc(std::max<int64_t>(L.msell_nnz, 1), st);
+    if (want_fp32) L.mv32.alloc(std::max<int64_t>(L.msell_nnz, 1), st);
+    if (nms) {
+        sell_mcol<<<grid_for(nms * 32), kBlock, 0, st>>>(nms, mrow0.p, mnrow.p, L.seg_col.p, L.mcol.p);
+        OBK_CHECK_LAUNCH();
+        sell_fill<int32_t><<<grid_for(nms * 32), kBlock, 0, st>>>(nms, L.ml_ptr.p, mrow0.p, mnrow.p, L.seg_ptr.p,
+                                                                  L.mir_row.p, L.mir_val.p, L.mrow.p, L.mv.p,
+                                                                  want_fp32 ? L.mv32.p : nullptr, 0);
+        OBK_CHECK_LAUNCH();
+    }
 }
 
 void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* v, int64_t nnz,
@@ -920,6 +1055,8 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
     OBK_CUDA(cudaMemcpyAsync(L.h_gseg_ptr.data(), L.gseg_ptr.p, (G + 1) * sizeof(int64_t),
                              cudaMemcpyDeviceToHost, st));
     OBK_CUDA(cudaStreamSynchronize(st));
+    // 8. sliced ELL copies for the persistent sweep
+    build_sell(L, want_fp32, st);
 }
 
 }  // namespace obk

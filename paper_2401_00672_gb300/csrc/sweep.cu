@@ -49,6 +49,21 @@ struct SweepParams {
     const int32_t* mir_row;
     const double* mir_val;
     const float* mir_val32;
+    // sliced ELL (SELL-32) copies: one thread per row / per mirror segment
+    int64_t ns;
+    const int64_t* sl_gptr;
+    const int64_t* sl_ptr;
+    const int64_t* sl_row0;
+    const int32_t* sl_nrow;
+    const int32_t* sci;
+    const double* sv;
+    const float* sv32;
+    const int64_t* ml_gptr;
+    const int64_t* ml_ptr;
+    const int32_t* mcol;
+    const int32_t* mrow;
+    const double* mv;
+    const float* mv32;
     const double* f;  // group-major
     double* x;        // N
     double* y;        // Ngm
@@ -122,27 +137,6 @@ __device__ __forceinline__ T sub_batch(const int32_t* ci, const T* vals, const T
     return acc;
 }
 
-// rhs - A_k . xv for row k (one thread)
-template <class T>
-__device__ __forceinline__ T row_residual(const int64_t* rp, const int32_t* ci, const T* vals, const T* xv, int64_t k,
-                                          T rhs)
-{
-    int64_t q = rp[k], e = rp[k + 1];
-    T acc = rhs;
-    for (; q + kBatch <= e; q += kBatch) acc = sub_batch<kBatch, T>(ci, vals, xv, q, acc);
-    switch ((int)(e - q)) {
-        case 7: acc = sub_batch<7, T>(ci, vals, xv, q, acc); break;
-        case 6: acc = sub_batch<6, T>(ci, vals, xv, q, acc); break;
-        case 5: acc = sub_batch<5, T>(ci, vals, xv, q, acc); break;
-        case 4: acc = sub_batch<4, T>(ci, vals, xv, q, acc); break;
-        case 3: acc = sub_batch<3, T>(ci, vals, xv, q, acc); break;
-        case 2: acc = sub_batch<2, T>(ci, vals, xv, q, acc); break;
-        case 1: acc = sub_batch<1, T>(ci, vals, xv, q, acc); break;
-        default: break;
-    }
-    return acc;
-}
-
 // Dot product of one row with xv by a sub-warp of SUB > 1 lanes (long rows):
 // lanes stride by SUB, batched loads, shuffle reduction afterwards.
 template <int SUB, class T>
@@ -174,13 +168,10 @@ template <int SUB, class T>
 __device__ __forceinline__ T row_residual_sub(const SweepParams& p, const T* vals, const T* xv, int64_t k, T rhs,
                                               int sub)
 {
-    if constexpr (SUB == 1) {
-        return row_residual<T>(p.grp_rp, p.grp_ci, vals, xv, k, rhs);
-    } else {
-        T acc = row_dot_wide<SUB, T>(p.grp_rp, p.grp_ci, vals, xv, k, sub);
-        acc = sub_reduce<SUB>(acc);
-        return rhs - acc;
-    }
+    static_assert(SUB > 1, "one lane per row uses the sliced layout");
+    T acc = row_dot_wide<SUB, T>(p.grp_rp, p.grp_ci, vals, xv, k, sub);
+    acc = sub_reduce<SUB>(acc);
+    return rhs - acc;
 }
 
 // phase 1: y_k = (rhs_k - A_k . xv) * inv_k for group-major rows [r0, r1)
@@ -194,6 +185,97 @@ __device__ __forceinline__ void phase1(const SweepParams& p, int64_t r0, int64_t
     for (int64_t k = r0 + sw; k < r1; k += nsw) {
         T r = row_residual_sub<SUB, T>(p, vals, xv, k, (T)rhs[k], sub);
         if (sub == 0) y[k] = r * inv[k];
+    }
+}
+
+// ---- sliced ELL (one thread per row / per segment) ------------------------------
+//
+// A slice holds 32 rows of one group (similar lengths: rows are sorted by
+// length inside a group) with entry j of lane l at base + 32 j + l, so every
+// load instruction of a warp reads 32 consecutive values, each FP64
+// instruction does 32 useful multiply-adds (up to the padding of the shorter
+// rows), and the residual f_k starts the accumulator: no shuffle reduction
+// and no separate subtraction.
+
+// acc + S * sum_{j<B} a[q + 32 j] * v[idx[q + 32 j]]   (S = -1 or +1)
+template <int B, int S, class T>
+__device__ __forceinline__ T sell_batch(const int32_t* idx, const T* vals, const T* v, int64_t q, T acc)
+{
+    int32_t c[B];
+    T a[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+        c[j] = idx[q + 32 * j];
+        a[j] = vals[q + 32 * j];
+    }
+    T g[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) g[j] = v[c[j]];
+#pragma unroll
+    for (int j = 0; j < B; ++j) acc = fma(S > 0 ? a[j] : -a[j], g[j], acc);
+    return acc;
+}
+
+// one lane's row (or segment) of a slice: len entries from position q
+template <int S, class T>
+__device__ __forceinline__ T sell_lane(const int32_t* idx, const T* vals, const T* v, int64_t q, int64_t len, T acc)
+{
+    int64_t j = 0;
+    for (; j + kBatch <= len; j += kBatch, q += 32 * kBatch) acc = sell_batch<kBatch, S, T>(idx, vals, v, q, acc);
+    switch ((int)(len - j)) {  // the same for the whole warp
+        case 7: acc = sell_batch<7, S, T>(idx, vals, v, q, acc); break;
+        case 6: acc = sell_batch<6, S, T>(idx, vals, v, q, acc); break;
+        case 5: acc = sell_batch<5, S, T>(idx, vals, v, q, acc); break;
+        case 4: acc = sell_batch<4, S, T>(idx, vals, v, q, acc); break;
+        case 3: acc = sell_batch<3, S, T>(idx, vals, v, q, acc); break;
+        case 2: acc = sell_batch<2, S, T>(idx, vals, v, q, acc); break;
+        case 1: acc = sell_batch<1, S, T>(idx, vals, v, q, acc); break;
+        default: break;
+    }
+    return acc;
+}
+
+// Slices go to warps in warp-major order over the blocks (warp w of block b is
+// number w * gridDim + b): in every round of the grid stride, consecutive
+// slices -- neighbours in memory and of about the same length -- land on
+// different blocks, so the GPU streams one contiguous stretch of the layout at
+// a time and a partial last round spreads over all SMs.
+__device__ __forceinline__ int64_t sell_warp()
+{
+    return (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+}
+
+// phase 1 over the row slices of group g: y_k = (rhs_k - A_k . xv) * inv_k
+template <class T, class TR>
+__device__ __forceinline__ void phase1_sell(const SweepParams& p, int64_t g, const T* sval, const T* inv,
+                                            const TR* rhs, const T* xv, T* y)
+{
+    int lane = threadIdx.x & 31;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t s1 = p.sl_gptr[g + 1];
+    for (int64_t s = p.sl_gptr[g] + sell_warp(); s < s1; s += nw) {
+        int64_t base = p.sl_ptr[s], len = (p.sl_ptr[s + 1] - base) >> 5;
+        bool valid = lane < p.sl_nrow[s];
+        int64_t k = p.sl_row0[s] + lane;
+        T acc = valid ? (T)rhs[k] : T(0);
+        acc = sell_lane<-1, T>(p.sci, sval, xv, base + lane, len, acc);
+        if (valid) y[k] = acc * inv[k];
+    }
+}
+
+// phase 2 over the mirror slices of group g: xv_c += sum_k A_kc y_k
+template <class T>
+__device__ __forceinline__ void phase2_sell(const SweepParams& p, int64_t g, const T* mval, const T* y, T* xv)
+{
+    int lane = threadIdx.x & 31;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t s1 = p.ml_gptr[g + 1];
+    for (int64_t s = p.ml_gptr[g] + sell_warp(); s < s1; s += nw) {
+        int64_t base = p.ml_ptr[s], len = (p.ml_ptr[s + 1] - base) >> 5;
+        int32_t c = p.mcol[s * 32 + lane];
+        T acc = c >= 0 ? xv[c] : T(0);
+        acc = sell_lane<1, T>(p.mrow, mval, y, base + lane, len, acc);
+        if (c >= 0) xv[c] = acc;
     }
 }
 
@@ -260,19 +342,38 @@ __device__ double block_sum(double v)
 template <int SUB>
 __device__ void residual_partial(const SweepParams& p, bool store_r)
 {
-    int64_t sw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / SUB;
-    int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / SUB;
-    int sub = threadIdx.x & (SUB - 1);
-    double local = 0.0;
-    for (int64_t k = sw; k < p.Ngm; k += nsw) {
-        double r = row_residual_sub<SUB, double>(p, p.grp_v, p.x, k, p.f[k], sub);
-        if (sub == 0) {
-            if (store_r) p.r64[k] = r;
-            local = fma(r, r, local);
+    if constexpr (SUB == 1) {
+        int lane = threadIdx.x & 31;
+        int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        double local = 0.0;
+        for (int64_t s = sell_warp(); s < p.ns; s += nw) {
+            int64_t base = p.sl_ptr[s], len = (p.sl_ptr[s + 1] - base) >> 5;
+            bool valid = lane < p.sl_nrow[s];
+            int64_t k = p.sl_row0[s] + lane;
+            double acc = valid ? p.f[k] : 0.0;
+            acc = sell_lane<-1, double>(p.sci, p.sv, p.x, base + lane, len, acc);
+            if (valid) {
+                if (store_r) p.r64[k] = acc;
+                local = fma(acc, acc, local);
+            }
         }
+        double sum = block_sum(local);
+        if (threadIdx.x == 0) p.partial[blockIdx.x] = sum;
+    } else {
+        int64_t sw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / SUB;
+        int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / SUB;
+        int sub = threadIdx.x & (SUB - 1);
+        double local = 0.0;
+        for (int64_t k = sw; k < p.Ngm; k += nsw) {
+            double r = row_residual_sub<SUB, double>(p, p.grp_v, p.x, k, p.f[k], sub);
+            if (sub == 0) {
+                if (store_r) p.r64[k] = r;
+                local = fma(r, r, local);
+            }
+        }
+        double s = block_sum(local);
+        if (threadIdx.x == 0) p.partial[blockIdx.x] = s;
     }
-    double s = block_sum(local);
-    if (threadIdx.x == 0) p.partial[blockIdx.x] = s;
 }
 
 // Total of the per-block partial sums, computed by block 0 with a fixed
@@ -308,6 +409,22 @@ __device__ __forceinline__ int64_t next_check(int64_t s, double rr, int64_t s_pr
     return s + step;
 }
 
+// one group step's two phases: sliced layout for SUB == 1, sub-warps per CSR row otherwise
+template <int SUB, class T, class TR>
+__device__ __forceinline__ void group_phase1(const SweepParams& p, int64_t g, const T* vals, const T* svals,
+                                             const T* inv, const TR* rhs, const T* xv, T* y)
+{
+    if constexpr (SUB == 1) phase1_sell<T, TR>(p, g, svals, inv, rhs, xv, y);
+    else phase1<SUB, T, TR>(p, p.gptr[g], p.gptr[g + 1], vals, inv, rhs, xv, y);
+}
+template <int SUB, class T>
+__device__ __forceinline__ void group_phase2(const SweepParams& p, int64_t g, const T* mvals, const T* smvals,
+                                             const T* y, T* xv)
+{
+    if constexpr (SUB == 1) phase2_sell<T>(p, g, smvals, y, xv);
+    else phase2<T>(p, p.gseg_ptr[g], p.gseg_ptr[g + 1], mvals, y, xv);
+}
+
 template <int SUB>
 __global__ void __launch_bounds__(kBlock, kBlocksPerSm) obk_solve_kernel(SweepParams p)
 {
@@ -341,9 +458,9 @@ __global__ void __launch_bounds__(kBlock, kBlocksPerSm) obk_solve_kernel(SweepPa
         while (vout[3] == 0) {
             unsigned long long t0 = lead ? globaltimer() : 0;
             for (int64_t g = 0; g < p.G; ++g) {
-                phase1<SUB, double, double>(p, p.gptr[g], p.gptr[g + 1], p.grp_v, p.grp_inv, p.f, p.x, p.y);
+                group_phase1<SUB, double, double>(p, g, p.grp_v, p.sv, p.grp_inv, p.f, p.x, p.y);
                 if (!grid_sync(p.gb)) return;
-                phase2<double>(p, p.gseg_ptr[g], p.gseg_ptr[g + 1], p.mir_val, p.y, p.x);
+                group_phase2<SUB, double>(p, g, p.mir_val, p.mv, p.y, p.x);
                 if (!grid_sync(p.gb)) return;
             }
             ++s;
@@ -396,10 +513,9 @@ __global__ void __launch_bounds__(kBlock, kBlocksPerSm) obk_solve_kernel(SweepPa
         if (sweeps + nin > p.maxit) nin = (int)(p.maxit - sweeps);
         for (int it = 0; it < nin; ++it) {
             for (int64_t g = 0; g < p.G; ++g) {
-                phase1<SUB, float, float>(p, p.gptr[g], p.gptr[g + 1], p.grp_v32, p.grp_inv32, p.b32, p.d32,
-                                          p.y32);
+                group_phase1<SUB, float, float>(p, g, p.grp_v32, p.sv32, p.grp_inv32, p.b32, p.d32, p.y32);
                 if (!grid_sync(p.gb)) return;
-                phase2<float>(p, p.gseg_ptr[g], p.gseg_ptr[g + 1], p.mir_val32, p.y32, p.d32);
+                group_phase2<SUB, float>(p, g, p.mir_val32, p.mv32, p.y32, p.d32);
                 if (!grid_sync(p.gb)) return;
             }
         }
@@ -466,14 +582,14 @@ void launch_solve(SweepParams& p, cudaStream_t st)
 
 // Lanes per row in phase 1.  FP64 issue is scarce on this GPU (a warp-wide
 // FP64 instruction occupies the FP64 pipe for the same time whatever the
-// number of active lanes), so rows get one or two lanes and at most one
-// shuffle step; two lanes per row measured fastest for rows of ~15 entries
-// (twice as many independent loads in flight per row).
+// number of active lanes).  One lane per row on the sliced layout wastes none
+// of it (no shuffle reduction, no separate subtraction, coalesced loads) and
+// measured fastest for rows of up to a few dozen entries; long rows get a
+// sub-warp each so that a row's loads are spread over lanes.
 int choose_sub(double avg_row)
 {
     // (a measured choice from obk_autotune takes precedence, see capi.cu)
-    if (avg_row <= 6) return 1;
-    if (avg_row <= 64) return 2;
+    if (avg_row <= 64) return 1;
     if (avg_row <= 160) return 8;
     return 32;
 }
@@ -515,6 +631,20 @@ SolveResult run_solve(const SweepLayout& L, const double* f_gm, double fnorm2, d
     p.mir_row = L.mir_row.p;
     p.mir_val = L.mir_val.p;
     p.mir_val32 = L.mir_val32.p;
+    p.ns = L.ns;
+    p.sl_gptr = L.sl_gptr.p;
+    p.sl_ptr = L.sl_ptr.p;
+    p.sl_row0 = L.sl_row0.p;
+    p.sl_nrow = L.sl_nrow.p;
+    p.sci = L.sci.p;
+    p.sv = L.sv.p;
+    p.sv32 = L.sv32.p;
+    p.ml_gptr = L.ml_gptr.p;
+    p.ml_ptr = L.ml_ptr.p;
+    p.mcol = L.mcol.p;
+    p.mrow = L.mrow.p;
+    p.mv = L.mv.p;
+    p.mv32 = L.mv32.p;
     p.f = f_gm;
     p.x = x;
     p.y = y.p;
