@@ -83,6 +83,7 @@ struct SweepLayout {
     int64_t nseg = 0;       // (group, column) segments of the column mirror
     int64_t nnz_gm = 0;     // entries of grouped rows
     int64_t n_conflicts = 0;
+    int64_t color_rounds = 0;  // rounds of the fixed-point colouring
     // group-major CSR: rows of group 0, then group 1, ...
     DBuf<int64_t> grp_rp;   // Ngm+1
     DBuf<int32_t> grp_ci;   // nnz_gm (columns in permuted numbering)
