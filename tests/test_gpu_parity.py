@@ -72,6 +72,63 @@ def _zero_rows():
     return synth.System(A, s.xstar, f, "zero_rows")
 
 
+def _hubs():
+    # sparse diagonally dominant rows plus three hub rows/columns of degree 2000:
+    # heavy frontier vertices in the RCM kernels and slices whose rows differ
+    # in length by two orders of magnitude
+    rng = np.random.default_rng(21)
+    N = 6000
+    rows, cols = [], []
+    for i in range(N):
+        c = rng.choice(N - 1, 5, replace=False)
+        c[c >= i] += 1
+        rows += [i] * 5
+        cols += list(c)
+    for h in (17, 3001, 5998):
+        nb = rng.choice(N, 2000, replace=False)
+        nb = nb[nb != h]
+        rows += [h] * len(nb) + list(nb)
+        cols += list(nb) + [h] * len(nb)
+    r = np.array(rows, np.int64)
+    c = np.array(cols, np.int64)
+    key = np.unique(r * N + c)
+    r, c = key // N, key % N
+    v = rng.standard_normal(len(r))
+    # weak hub couplings keep every group step contractive (the sum of a hub
+    # row's cosines with its group stays below one)
+    hub = np.isin(r, (17, 3001, 5998)) | np.isin(c, (17, 3001, 5998))
+    v[hub] *= 1e-3
+    off = np.bincount(r, weights=np.abs(v), minlength=N)
+    r = np.concatenate([r, np.arange(N)])
+    c = np.concatenate([c, np.arange(N)])
+    v = np.concatenate([v, 1.0 + off])
+    A = synth.csr_from_coo(N, N, r, c, v)
+    xs = rng.standard_normal(N)
+    return synth.System(A, xs, A.matvec(xs), "hubs")
+
+
+def _many_groups():
+    # 150 rows sharing one strong column conflict pairwise (|cos| = 0.41), so
+    # first fit needs more than 64 groups
+    rng = np.random.default_rng(5)
+    N = 1000
+    base = synth.random_dominant(N, 3, seed=55).A
+    r = np.repeat(np.arange(N), np.diff(base.row_ptr)).astype(np.int64)
+    c = base.col_idx.astype(np.int64)
+    v = base.val.copy()
+    keep = ~((r < 150) & (c == N - 1))
+    r, c, v = r[keep], c[keep], v[keep]
+    v[(r < 150) & (r == c)] = 12.0
+    v[(r < 150) & (r != c)] = 0.0
+    r = np.concatenate([r, np.arange(150)])
+    c = np.concatenate([c, np.full(150, N - 1)])
+    v = np.concatenate([v, np.full(150, 10.0)])
+    v[(r == N - 1) & (c == N - 1)] = 2000.0
+    A = synth.csr_from_coo(N, N, r, c, v)
+    xs = rng.standard_normal(N)
+    return synth.System(A, xs, A.matvec(xs), "many_groups")
+
+
 CASES = {
     "random_dominant_2000": lambda: synth.random_dominant(2000, 7, seed=1000),
     "knn_30000": lambda: synth.knn_dominant(30000, 12, seed=1001),
@@ -81,6 +138,8 @@ CASES = {
     "components": _components,
     "zero_rows": _zero_rows,
     "tiny_3x3": lambda: synth.random_dominant(3, 1, seed=5),
+    "hubs": _hubs,
+    "many_groups": _many_groups,
 }
 
 _cache = {}
