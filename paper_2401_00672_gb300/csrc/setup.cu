@@ -168,10 +168,11 @@ __global__ void pair_upper_bound(int64_t N, const int64_t* rp, const int32_t* ci
     }
 }
 
+// hash slots for a row with at most ub candidates: a power of two, load <= 2/3
 __host__ __device__ inline int64_t table_cap(int64_t ub)
 {
     int64_t c = 32;
-    while (c < 2 * ub) c <<= 1;
+    while (c < ub + (ub + 1) / 2) c <<= 1;
     return c;
 }
 
