@@ -12,6 +12,9 @@ namespace obk {
 // Whether obk_solve_batch can take this system (capi.cu).
 bool batch_eligible(const obk_handle* h);
 
+// The stream a handle was created on (capi.cu).
+void* handle_stream(const obk_handle* h);
+
 // Everything one block needs to solve one prepared system (device pointers).
 struct BatchSystem {
     int64_t m, n, N, Ngm, G, n_zero;

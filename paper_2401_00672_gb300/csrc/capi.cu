@@ -524,6 +524,8 @@ bool batch_eligible(const obk_handle* h)
 {
     return h && batch_smem_bytes(h->N, h->L.Ngm) <= batch_smem_limit();
 }
+
+void* handle_stream(const obk_handle* h) { return h ? (void*)h->st : nullptr; }
 }  // namespace obk
 
 extern "C" {

@@ -208,14 +208,21 @@ void exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaS
 // key.  keys/vals are sorted in place (scratch allocated internally).
 void radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaStream_t st);
 
+// A small pinned host buffer of the calling thread (allocated on first use,
+// held until the thread exits): device-to-host reads of single values into
+// pageable memory would be staged through the driver, which serialises them
+// with the other threads' copies.
+void* pinned_scratch();
+
 // Read one value back (synchronises the stream).
 template <class T>
 T read_scalar(const T* dptr, cudaStream_t st)
 {
-    T v;
-    OBK_CUDA(cudaMemcpyAsync(&v, dptr, sizeof(T), cudaMemcpyDeviceToHost, st));
+    static_assert(sizeof(T) <= 64, "read_scalar reads small values");
+    T* v = static_cast<T*>(pinned_scratch());
+    OBK_CUDA(cudaMemcpyAsync(v, dptr, sizeof(T), cudaMemcpyDeviceToHost, st));
     OBK_CUDA(cudaStreamSynchronize(st));
-    return v;
+    return *v;
 }
 
 // Cooperative launch helper: grid = min(want, co-resident capacity).

@@ -315,6 +315,23 @@ void radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaS
     }
 }
 
+namespace {
+struct PinnedSlot {
+    void* p = nullptr;
+    ~PinnedSlot()
+    {
+        if (p) cudaFreeHost(p);
+    }
+};
+}  // namespace
+
+void* pinned_scratch()
+{
+    thread_local PinnedSlot slot;
+    if (!slot.p) OBK_CUDA(cudaMallocHost(&slot.p, 64));
+    return slot.p;
+}
+
 int coop_grid(const void* kernel, int block, size_t smem, int64_t want_blocks)
 {
     DevInfo di = dev_info();

@@ -136,8 +136,10 @@ static void run_batches(obk_server* s)
             int ri = rc < 0 ? (int)rc : (int)st[i];
             if (ri >= 0) {
                 r->x.assign((size_t)r->n, 0.0);
-                if (cudaMemcpy(r->x.data(), r->xdev.p, (size_t)r->n * sizeof(double), cudaMemcpyDeviceToHost) !=
-                    cudaSuccess) {
+                cudaStream_t hst = static_cast<cudaStream_t>(obk::handle_stream(r->h));
+                if (cudaMemcpyAsync(r->x.data(), r->xdev.p, (size_t)r->n * sizeof(double), cudaMemcpyDeviceToHost,
+                                    hst) != cudaSuccess ||
+                    cudaStreamSynchronize(hst) != cudaSuccess) {
                     ri = OBK_ERR_CUDA;
                     r->err = "copying the result failed";
                 }
