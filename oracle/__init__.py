@@ -161,6 +161,21 @@ def group_build(N, rp, ci, v, nsq, thr):
     return gof, int(G.value), int(nc.value)
 
 
+def cosine_stats(N, rp, ci, v, nsq):
+    """Definitions 1-2 at the row level: (nonzero entries of the N x N row-cosine
+    table, sum of |cos| over them in units of 2^-32, zn, nn)."""
+    rp, ci, v = _csr(rp, ci, v)
+    nsq = np.ascontiguousarray(nsq, np.float64)
+    nz = ctypes.c_int64(0)
+    tot = ctypes.c_uint64(0)
+    rc = _load().orc_cosine_stats(ctypes.c_int64(N), _p(rp), _p(ci), _p(v), _p(nsq), ctypes.byref(nz),
+                                  ctypes.byref(tot))
+    if rc:
+        raise MemoryError("oracle cosine_stats failed")
+    num = float(N) * float(N)
+    return int(nz.value), int(tot.value), (num - nz.value) / num, tot.value * 2.0 ** -32 / num
+
+
 def group_lists(group_of, G):
     gof = np.ascontiguousarray(group_of, np.int32)
     N = gof.size

@@ -394,6 +394,74 @@ int orc_group_build(int64_t N, const int64_t* rp, const int32_t* ci, const doubl
     return ORC_OK;
 }
 
+/* Cosine table statistics (Section 3.6, Definitions 1 and 2, read at the row
+ * level k = N): C is the N x N table of row cosines C_ij = dot_ij /
+ * (||A_i|| ||A_j||) with dot_ij the left fold of the products over the common
+ * columns in ascending order (the grouping's arithmetic), C_ii = 1 for a
+ * nonzero row, and every entry of a zero row 0.  *nz = number of nonzero
+ * entries of C; *sum = sum over the nonzero entries of |C_ij| rounded to the
+ * nearest multiple of 2^-32, in units of 2^-32 (an integer, so the total does
+ * not depend on the order of summation).  Then zn = (N^2 - nz) / N^2 and
+ * nn = sum 2^-32 / N^2. */
+int orc_cosine_stats(int64_t N, const int64_t* rp, const int32_t* ci, const double* v, const double* nsq,
+                     int64_t* nz, uint64_t* sum)
+{
+    int64_t nnz = rp[N];
+    int64_t* cptr = calloc((size_t)N + 1, sizeof(int64_t));
+    int32_t* crow = malloc((size_t)(nnz + 1) * sizeof(int32_t));
+    double* cval = malloc((size_t)(nnz + 1) * sizeof(double));
+    double* acc = calloc((size_t)N, sizeof(double));
+    char* touched = calloc((size_t)N, 1);
+    int32_t* tlist = malloc((size_t)N * sizeof(int32_t));
+    double* s = malloc((size_t)N * sizeof(double));
+    int64_t* fill = malloc((size_t)N * sizeof(int64_t));
+    if (!cptr || !crow || !cval || !acc || !touched || !tlist || !s || !fill) {
+        free(cptr); free(crow); free(cval); free(acc); free(touched); free(tlist); free(s); free(fill);
+        return ORC_NOMEM;
+    }
+    for (int64_t e = 0; e < nnz; ++e) cptr[ci[e] + 1]++;
+    for (int64_t c = 0; c < N; ++c) cptr[c + 1] += cptr[c];
+    for (int64_t c = 0; c < N; ++c) fill[c] = cptr[c];
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+            int64_t p = fill[ci[e]]++;
+            crow[p] = (int32_t)i;
+            cval[p] = v[e];
+        }
+    for (int64_t i = 0; i < N; ++i) s[i] = sqrt(nsq[i]);
+    int64_t cnt = 0;
+    uint64_t tot = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        if (nsq[i] == 0.0) continue;
+        cnt += 1;                     /* C_ii = 1 */
+        tot += (uint64_t)1 << 32;
+        int64_t nt = 0;
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+            int32_t c = ci[e];
+            for (int64_t p = cptr[c]; p < cptr[c + 1]; ++p) {
+                int32_t j = crow[p];
+                if (j >= i) break;
+                if (nsq[j] == 0.0) continue;
+                if (!touched[j]) { touched[j] = 1; acc[j] = 0.0; tlist[nt++] = j; }
+                acc[j] = acc[j] + v[e] * cval[p];
+            }
+        }
+        for (int64_t t = 0; t < nt; ++t) {
+            int32_t j = tlist[t];
+            double cosv = acc[j] / (s[j] * s[i]);
+            if (cosv != 0.0) {        /* C_ij and C_ji */
+                cnt += 2;
+                tot += 2 * (uint64_t)llrint(fabs(cosv) * 0x1p32);
+            }
+            touched[j] = 0;
+        }
+    }
+    *nz = cnt;
+    *sum = tot;
+    free(cptr); free(crow); free(cval); free(acc); free(touched); free(tlist); free(s); free(fill);
+    return ORC_OK;
+}
+
 /* group_ptr[G+1], group_rows[count of grouped rows]: rows ascending per group. */
 void orc_group_lists(int64_t N, const int32_t* group_of, int64_t G, int64_t* gptr, int32_t* grows)
 {
