@@ -140,6 +140,34 @@ OBK_API obk_status obk_get_groups(const obk_handle* h, int32_t* group_of);
 OBK_API obk_status obk_get_row_norms(const obk_handle* h, double* nsq);
 OBK_API obk_status obk_get_info(const obk_handle* h, obk_info* info);
 
+/* Statistics of the cosine table (Section 3.6, Definitions 1 and 2), read at
+ * the row level k = N of the extended, permuted matrix A~ (N x N): C_ij is the
+ * cosine of rows i and j with the grouping's arithmetic (products over the
+ * common columns added in ascending column order, divided by
+ * sqrt(nsq_i) sqrt(nsq_j)), C_ii = 1 for a nonzero row, and every entry of an
+ * all-zero row is 0.  nonzero_entries counts the nonzero C_ij, abs_cos_sum is
+ * the sum of their |C_ij| each rounded to the nearest multiple of 2^-32 (in
+ * units of 2^-32, so the total is exact whatever the order of summation),
+ * zn = (N^2 - nonzero_entries) / N^2 (Definition 1, the orthogonality
+ * proportion) and nn = abs_cos_sum 2^-32 / N^2 (Definition 2, the
+ * non-orthogonality severity).  The groups fields describe the built groups. */
+typedef struct {
+    int64_t N;
+    int64_t nonzero_entries;
+    uint64_t abs_cos_sum;
+    double zn;
+    double nn;
+    int64_t groups;
+    int64_t min_group_rows;
+    int64_t max_group_rows;
+    int64_t reserved[4];
+} obk_gstats;
+
+/* Computes the statistics above for a prepared system (recomputes the pair
+ * dot products; costs about one pair-cosine stage of obk_create).  out is host
+ * memory owned by the caller.  OBK_ERR_INVALID for NULL arguments. */
+OBK_API obk_status obk_grouping_stats(obk_handle* h, obk_gstats* out);
+
 /* Device time of the stages of obk_create, in order: (0) upload, validation
  * and extension, (1) bandwidth of the input, Reverse Cuthill-McKee in four
  * parts: (2) the graph pattern(A^ + A^T), (3) the (degree, index) ranks and

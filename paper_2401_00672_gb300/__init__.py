@@ -27,7 +27,7 @@ EXPORTS = [
     "obk_get_groups", "obk_get_row_norms", "obk_get_info", "obk_destroy", "obk_server_create",
     "obk_submit", "obk_poll", "obk_cancel", "obk_server_destroy", "obk_last_error", "obk_version",
     "obk_kernel_launches", "obk_residual", "obk_residual_noalloc", "obk_autotune", "obk_solve_batch",
-    "obk_batch_max_n", "obk_get_setup_profile",
+    "obk_batch_max_n", "obk_get_setup_profile", "obk_grouping_stats",
 ]
 
 
@@ -48,6 +48,13 @@ class Opts(ctypes.Structure):
                 ("inner_sweeps", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("stagnation", ctypes.c_double), ("timeout_spins", ctypes.c_int64),
                 ("rows_per_warp", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class _GStats(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("nonzero_entries", ctypes.c_int64), ("abs_cos_sum", ctypes.c_uint64),
+                ("zn", ctypes.c_double), ("nn", ctypes.c_double), ("groups", ctypes.c_int64),
+                ("min_group_rows", ctypes.c_int64), ("max_group_rows", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 4)]
 
 
 class _Tune(ctypes.Structure):
@@ -112,6 +119,7 @@ def _load() -> ctypes.CDLL:
         "obk_solve_batch": ([vp, i32, vp, vp, vp, dbl, i64, vp, vp, vp], ctypes.c_int),
         "obk_batch_max_n": ([], ctypes.c_int64),
         "obk_get_setup_profile": ([vp, vp, i32], ctypes.c_int32),
+        "obk_grouping_stats": ([vp, vp], ctypes.c_int32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -189,6 +197,12 @@ class Handle:
     SETUP_STAGES = ("upload_validate_extend", "bandwidth_in", "rcm_graph", "rcm_ranks", "rcm_search",
                     "rcm_cuthill_mckee", "permute", "norms_transpose",
                     "pair_cosines", "grouping", "group_rows", "mirror_segments", "bookkeeping")
+
+    def grouping_stats(self) -> dict:
+        """obk_grouping_stats: Definitions 1-2 (zn, nn) of the row cosine table and group sizes."""
+        g = _GStats()
+        _check(lib.obk_grouping_stats(self._h, ctypes.byref(g)), "obk_grouping_stats")
+        return {k: getattr(g, k) for k, _ in _GStats._fields_ if k != "reserved"}
 
     def setup_profile(self) -> dict:
         """obk_get_setup_profile: device milliseconds per obk_create stage."""

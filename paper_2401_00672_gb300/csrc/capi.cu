@@ -517,6 +517,34 @@ obk_status obk_solve(obk_handle* h, const double* f, const double* x0, double to
     return obk_solve_ex(h, nullptr, f, x0, tol, maxit, x_out, info);
 }
 
+obk_status obk_grouping_stats(obk_handle* h, obk_gstats* out)
+{
+    OBK_API_BEGIN
+    set_last_error("");
+    if (!h || !out) throw Error{-1, "handle or output NULL"};
+    OBK_CUDA(cudaSetDevice(h->device));
+    obk_gstats r{};
+    r.N = h->N;
+    int64_t nz = 0;
+    uint64_t sum = 0;
+    cosine_stats(h->L, &nz, &sum, h->err.p, h->st);
+    r.nonzero_entries = nz;
+    r.abs_cos_sum = sum;
+    double num = (double)h->N * (double)h->N;
+    r.zn = num > 0 ? (num - (double)nz) / num : 0.0;
+    r.nn = num > 0 ? (double)sum * 0x1p-32 / num : 0.0;
+    r.groups = h->L.G;
+    r.min_group_rows = h->L.G ? INT64_MAX : 0;
+    for (int64_t g = 0; g < h->L.G; ++g) {
+        int64_t c = h->L.h_gptr[g + 1] - h->L.h_gptr[g];
+        r.min_group_rows = std::min(r.min_group_rows, c);
+        r.max_group_rows = std::max(r.max_group_rows, c);
+    }
+    *out = r;
+    return OBK_OK;
+    OBK_API_END
+}
+
 }  // extern "C"
 
 namespace obk {

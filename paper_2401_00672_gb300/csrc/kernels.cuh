@@ -134,6 +134,10 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
                  double thr, long long spin_limit, int* d_err, SweepLayout& L, bool want_fp32,
                  cudaStream_t st, StageClock* clock = nullptr);
 
+// Row cosine-table statistics of a built layout (Definitions 1-2 at the row
+// level): nonzero entries and the sum of |cos| in units of 2^-32 (setup.cu).
+void cosine_stats(const SweepLayout& L, int64_t* nz, uint64_t* sum, int* d_err, cudaStream_t st);
+
 // ---- sweep.cu -----------------------------------------------------------------
 
 struct SolveArgs {

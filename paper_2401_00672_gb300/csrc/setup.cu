@@ -214,6 +214,7 @@ struct PairParams {
     unsigned long long* pool_used;
     unsigned long long* n_conflicts;
     int* err;
+    unsigned long long* stats;  // STATS mode: [0] nonzero cosine-table entries, [1] sum of |cos| in 2^-32
 };
 
 __device__ __forceinline__ uint32_t hslot(int32_t j, uint32_t mask)
@@ -241,6 +242,10 @@ __device__ __forceinline__ bool is_conflict(double dot, double sj, double si, do
     return fabs(__ddiv_rn(dot, __dmul_rn(sj, si))) >= thr;
 }
 
+// STATS: instead of conflict lists, count the nonzero entries of the row
+// cosine table and add up their magnitudes (rounded to units of 2^-32) for
+// Definitions 1-2; the diagonal (1 for every row here) is included.
+template <bool STATS>
 __global__ void __launch_bounds__(kPairWarps * 32) pair_conflicts(PairParams p)
 {
     __shared__ int32_t skey[kPairWarps][kPairCap];
@@ -254,7 +259,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_conflicts(PairParams p)
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = gw; i < p.N; i += nw) {
         if (p.nsq[i] == 0.0) {
-            if (lane == 0) { p.conf_cnt[i] = 0; p.conf_off[i] = 0; }
+            if (!STATS && lane == 0) { p.conf_cnt[i] = 0; p.conf_off[i] = 0; }
             continue;
         }
         int64_t cap = table_cap(p.ub[i]);
@@ -357,6 +362,27 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_conflicts(PairParams p)
             }
             nc += __popc(m);
             __syncwarp();
+        }
+        if (STATS) {
+            double si0 = p.s[i];
+            unsigned long long c_nz = 0, c_sum = 0;
+            for (int t = lane; t < nc; t += 32) {
+                double cv = fabs(__ddiv_rn(val[t], __dmul_rn(p.s[key[t]], si0)));
+                if (cv != 0.0) {  // C_ij and C_ji
+                    c_nz += 2;
+                    c_sum += 2ull * __double2ull_rn(cv * 0x1p32);
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                c_nz += __shfl_xor_sync(0xffffffffu, c_nz, o);
+                c_sum += __shfl_xor_sync(0xffffffffu, c_sum, o);
+            }
+            if (lane == 0) {
+                atomicAdd(p.stats, c_nz + 1);             // + C_ii
+                atomicAdd(p.stats + 1, c_sum + (1ull << 32));
+            }
+            __syncwarp();
+            continue;
         }
         // one conflict decision per candidate, kept as bits (64 candidates per lane)
         double si = p.s[i];
@@ -782,6 +808,93 @@ void permute_csr(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
 
 namespace {
 
+// Column lists of a CSR matrix (nrows x ncols, columns sorted in each row):
+// cptr[ncols+1], rows ascending inside each column with their values, and the
+// column-list position of every CSR entry.
+void build_csc(int64_t nrows, int64_t ncols, const int64_t* rp, const int32_t* ci, const double* v, int64_t nnz,
+               DBuf<int64_t>& cptr, DBuf<int32_t>& crow, DBuf<double>& cval, DBuf<int64_t>& pos_of,
+               cudaStream_t st)
+{
+    DBuf<int32_t> row_of(std::max<int64_t>(nnz, 1), st);
+    DBuf<int64_t> ccnt(ncols + 1, st);
+    cptr.alloc(ncols + 1, st);
+    pos_of.alloc(std::max<int64_t>(nnz, 1), st);
+    crow.alloc(std::max<int64_t>(nnz, 1), st);
+    cval.alloc(std::max<int64_t>(nnz, 1), st);
+    OBK_CUDA(cudaMemsetAsync(ccnt.p, 0, (ncols + 1) * sizeof(int64_t), st));
+    if (nnz) {
+        expand_rows_k<<<grid_for(nrows), kBlock, 0, st>>>(rp, nrows, row_of.p);
+        OBK_CHECK_LAUNCH();
+        DBuf<uint64_t> keys(nnz, st);
+        DBuf<uint32_t> order(nnz, st);
+        col_key_kernel<<<grid_for(nnz), kBlock, 0, st>>>(nnz, ci, keys.p, order.p);
+        OBK_CHECK_LAUNCH();
+        radix_sort_pairs(keys.p, order.p, nnz, bits_for((uint64_t)std::max<int64_t>(ncols - 1, 1)), st);
+        count_cols_k<<<grid_for(nnz), kBlock, 0, st>>>(nnz, ci, ccnt.p);
+        OBK_CHECK_LAUNCH();
+        csc_fill<<<grid_for(nnz), kBlock, 0, st>>>(nnz, order.p, row_of.p, v, crow.p, cval.p, pos_of.p);
+        OBK_CHECK_LAUNCH();
+    }
+    exclusive_scan_i64(ccnt.p, cptr.p, ncols, st);
+}
+
+__global__ void gm_norms(int64_t Ngm, const int32_t* grp_row, const double* nsq, double* nsq_gm, double* s_gm)
+{
+    GRID_STRIDE(k, Ngm)
+    {
+        double q = nsq[grp_row[k]];
+        nsq_gm[k] = q;
+        s_gm[k] = sqrt(q);
+    }
+}
+
+}  // namespace
+
+void cosine_stats(const SweepLayout& L, int64_t* nz, uint64_t* sum, int* d_err, cudaStream_t st)
+{
+    int64_t Ngm = L.Ngm, N = L.N, nnz = L.nnz_gm;
+    if (Ngm == 0) {
+        *nz = 0;
+        *sum = 0;
+        return;
+    }
+    DevInfo di = dev_info();
+    // the group-major rows are the nonzero rows of the permuted matrix (columns in
+    // its numbering, ascending): their dot products fold in the same order
+    DBuf<double> nsq(Ngm, st), s(Ngm, st);
+    gm_norms<<<grid_for(Ngm), kBlock, 0, st>>>(Ngm, L.grp_row.p, L.nsq.p, nsq.p, s.p);
+    OBK_CHECK_LAUNCH();
+    DBuf<int64_t> cptr, pos_of;
+    DBuf<int32_t> crow;
+    DBuf<double> cval;
+    build_csc(Ngm, N, L.grp_rp.p, L.grp_ci.p, L.grp_v.p, nnz, cptr, crow, cval, pos_of, st);
+    DBuf<int64_t> ub(Ngm, st), bigsz(Ngm, st), bigoff(Ngm + 1, st);
+    pair_upper_bound<<<grid_for(Ngm), kBlock, 0, st>>>(Ngm, L.grp_rp.p, L.grp_ci.p, cptr.p, pos_of.p, ub.p);
+    OBK_CHECK_LAUNCH();
+    big_table_sizes<<<grid_for(Ngm), kBlock, 0, st>>>(Ngm, ub.p, kPairCap, bigsz.p);
+    OBK_CHECK_LAUNCH();
+    exclusive_scan_i64(bigsz.p, bigoff.p, Ngm, st);
+    int64_t big_total = read_scalar(bigoff.p + Ngm, st);
+    DBuf<int32_t> big_key(std::max<int64_t>(big_total, 1), st);
+    DBuf<double> big_val(std::max<int64_t>(big_total, 1), st);
+    DBuf<unsigned long long> acc(2, st);
+    OBK_CUDA(cudaMemsetAsync(acc.p, 0, 2 * sizeof(unsigned long long), st));
+    PairParams pp{Ngm, L.grp_rp.p, L.grp_ci.p, L.grp_v.p, cptr.p, crow.p, cval.p, pos_of.p, nsq.p, s.p, 0.0, ub.p,
+                  bigoff.p, big_key.p, big_val.p, nullptr, nullptr, nullptr, 0, nullptr, nullptr, d_err, acc.p};
+    int blocks = (int)std::min<int64_t>(ceil_div(Ngm, kPairWarps), (int64_t)di.sms * 16);
+    pair_conflicts<true><<<blocks, kPairWarps * 32, 0, st>>>(pp);
+    OBK_CHECK_LAUNCH();
+    if (read_scalar(d_err, st) != 0) throw Error{-5, "internal error: pair table overflow"};
+    unsigned long long h[2];
+    OBK_CUDA(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    OBK_CUDA(cudaStreamSynchronize(st));
+    *nz = (int64_t)h[0];
+    *sum = (uint64_t)h[1];
+}
+
+
+namespace {
+
 // slices of each group: host prefix over the (few) groups
 std::vector<int64_t> slice_starts(const std::vector<int64_t>& item_g)
 {
@@ -871,25 +984,10 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
     OBK_CHECK_LAUNCH();
 
     // 2. transpose (rows ascending inside each column)
-    DBuf<int32_t> row_of(nnz, st);
-    DBuf<int64_t> cptr(N + 1, st), ccnt(N + 1, st), pos_of(nnz, st);
-    DBuf<int32_t> crow(nnz, st);
-    DBuf<double> cval(nnz, st);
-    OBK_CUDA(cudaMemsetAsync(ccnt.p, 0, (N + 1) * sizeof(int64_t), st));
-    if (nnz) {
-        expand_rows_k<<<grid_for(N), kBlock, 0, st>>>(rp, N, row_of.p);
-        OBK_CHECK_LAUNCH();
-        DBuf<uint64_t> keys(nnz, st);
-        DBuf<uint32_t> order(nnz, st);
-        col_key_kernel<<<grid_for(nnz), kBlock, 0, st>>>(nnz, ci, keys.p, order.p);
-        OBK_CHECK_LAUNCH();
-        radix_sort_pairs(keys.p, order.p, nnz, bits_for((uint64_t)(N - 1)), st);
-        count_cols_k<<<grid_for(nnz), kBlock, 0, st>>>(nnz, ci, ccnt.p);
-        OBK_CHECK_LAUNCH();
-        csc_fill<<<grid_for(nnz), kBlock, 0, st>>>(nnz, order.p, row_of.p, v, crow.p, cval.p, pos_of.p);
-        OBK_CHECK_LAUNCH();
-    }
-    exclusive_scan_i64(ccnt.p, cptr.p, N, st);
+    DBuf<int64_t> cptr, pos_of;
+    DBuf<int32_t> crow;
+    DBuf<double> cval;
+    build_csc(N, N, rp, ci, v, nnz, cptr, crow, cval, pos_of, st);
 
     mark();
     // 3. pair cosines -> lower conflict lists
@@ -912,9 +1010,9 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
         OBK_CUDA(cudaMemsetAsync(counters.p, 0, 2 * sizeof(unsigned long long), st));
         PairParams pp{N, rp, ci, v, cptr.p, crow.p, cval.p, pos_of.p, L.nsq.p, s.p, thr, ub.p,
                       bigoff.p, big_key.p, big_val.p, conf_cnt.p, conf_off.p, pool.p, pool_cap,
-                      counters.p, counters.p + 1, d_err};
+                      counters.p, counters.p + 1, d_err, nullptr};
         int blocks = (int)std::min<int64_t>(ceil_div(N, kPairWarps), (int64_t)di.sms * 16);
-        pair_conflicts<<<blocks, kPairWarps * 32, 0, st>>>(pp);
+        pair_conflicts<false><<<blocks, kPairWarps * 32, 0, st>>>(pp);
         OBK_CHECK_LAUNCH();
         if (read_scalar(d_err, st) != 0) throw Error{-5, "internal error: pair table overflow"};
         unsigned long long used = read_scalar(counters.p, st);

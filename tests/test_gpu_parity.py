@@ -477,3 +477,23 @@ def test_full_size_knn_1m_parity(obk):
         assert st == st_o == obk.OBK_OK and abs(info.sweeps - io.sweeps) <= 1
         st2, x2, _ = h.solve(s.f, tol=1e-300, maxit=io.sweeps)
     assert np.linalg.norm(x2 - x_o) / np.linalg.norm(x_o) <= XTOL
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_cosine_stats_bit_exact(obk, name):
+    """Definitions 1-2 from the GPU equal the oracle's on the permuted matrix."""
+    s, su = _case(name)
+    A = s.A
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
+        g = h.grouping_stats()
+    N = su.N
+    # the oracle's extended (Algorithms 5/6: N = max(m, n), appended rows empty)
+    # and permuted matrix
+    rp_ext = np.concatenate([A.row_ptr, np.full(N - A.m, A.row_ptr[-1], np.int64)])
+    rp, ci, v = oracle.permute(N, rp_ext, A.col_idx, A.val, su.perm)
+    nsq = oracle.row_norms(N, rp, v)
+    nz, tot, zn, nn = oracle.cosine_stats(N, rp, ci, v, nsq)
+    assert g["N"] == N
+    assert g["nonzero_entries"] == nz and g["abs_cos_sum"] == tot
+    assert g["zn"] == pytest.approx(zn, rel=1e-15) and g["nn"] == pytest.approx(nn, rel=1e-15)
+    assert g["groups"] == su.G
