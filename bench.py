@@ -81,7 +81,24 @@ def workload(name: str, rank: int):
         s = synth.rect_random(800_000, 200_000, 10, seed=replica_seed(1002, rank), noise=1e-3)
         return s, dict(workload="rect_m8e5_n2e5_10nnz_fp64_noise1e-3", m=800_000, n=200_000, nnz_per_row=10,
                        thr=0.1, tol=1e-8, precision="fp64", variant="inconsistent, stops on stagnation")
+    if name == "rect_under800k":
+        s = synth.rect_random(200_000, 800_000, 10, seed=replica_seed(1005, rank), full_columns=False)
+        return s, dict(workload="rect_m2e5_n8e5_10nnz_fp64", m=200_000, n=800_000, nnz_per_row=10, thr=0.1,
+                       tol=1e-8, precision="fp64", variant="underdetermined consistent (UOBK, Algorithm 6)")
     raise SystemExit(f"unknown workload {name}")
+
+
+def min_norm_solution(A, f, tol=1e-13, maxit=5000):
+    """x = A^T y with A A^T y = f by conjugate gradients on the host (float64,
+    scipy): the minimum-norm solution of a consistent underdetermined system
+    of full row rank, the limit of the iteration from x0 = 0."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+
+    M = sp.csr_matrix((A.val, A.col_idx, A.row_ptr), shape=(A.m, A.n))
+    op = spla.LinearOperator((A.m, A.m), matvec=lambda y: M @ (M.T @ y), dtype=np.float64)
+    y, info = spla.cg(op, f, rtol=tol, maxiter=maxit)
+    return M.T @ y
 
 
 class ClockSampler:
@@ -253,7 +270,8 @@ def serving_study(args):
     import paper_2401_00672_gb300 as obk
     import synth
 
-    reqs = synth.request_stream(args.requests, rate_per_s=1.0, seed=1004, materialize=True)
+    reqs = synth.request_stream(args.requests, rate_per_s=1.0, seed=1004, materialize=True,
+                                frac_under=args.under_frac)
 
     def run(rate):
         srv = obk.Server(hbm_budget_bytes=150 << 30, max_streams=args.streams)
@@ -291,7 +309,54 @@ def serving_study(args):
     mu = closed["req_per_s"]
     opened = run(0.8 * mu)
     print(json.dumps({"metric": "serving", "requests": len(reqs), "streams": args.streams,
-                      "closed_loop": closed, "open_loop_0.8mu": opened}), flush=True)
+                      "under_frac": args.under_frac, "closed_loop": closed, "open_loop_0.8mu": opened}),
+          flush=True)
+
+
+def thr_sweep(args):
+    """Grouping threshold sweep (Section 3.6 / Table 5 analogue) on the kNN
+    generator at n = args.tn: for each thr the groups, conflicts, sweeps and
+    times to rel. residual 1e-8, plus the row cosine-table statistics zn and nn
+    (Definitions 1-2; they do not depend on thr)."""
+    import torch
+
+    import paper_2401_00672_gb300 as obk
+    import synth
+
+    s = synth.knn_dominant(args.tn, 12, seed=1001)
+    A = s.A
+    dev = torch.device("cuda")
+    stream = torch.cuda.Stream()
+    rp = torch.from_numpy(A.row_ptr).to(dev)
+    ci = torch.from_numpy(A.col_idx).to(dev)
+    v = torch.from_numpy(A.val).to(dev)
+    f = torch.from_numpy(s.f).to(dev)
+    x = torch.empty(A.n, dtype=torch.float64, device=dev)
+    rows = []
+    stats = None
+    for thr in (0.02, 0.05, 0.1, 0.2, 0.3, 0.5):
+        best = None
+        for rep in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h = obk.Handle(rp, ci, v, A.m, A.n, thr=thr, stream=stream.cuda_stream)
+            st, _, info = h.solve(f, None, tol=1e-8, maxit=20000, out=x, opts=obk.Opts(check_every=-1))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if stats is None:
+                stats = h.grouping_stats()
+            r = {"thr": thr, "groups": h.G, "conflicts": info.n_conflicts, "sweeps": info.sweeps,
+                 "status": int(st), "setup_ms": round(info.setup_ms, 3), "solve_ms": round(info.solve_ms, 3),
+                 "time_to_solution_ms": round(e0.elapsed_time(e1), 3)}
+            h.close()
+            if best is None or r["time_to_solution_ms"] < best["time_to_solution_ms"]:
+                best = r
+        rows.append(best)
+    out = {"metric": "thr_sweep", "workload": f"knn_n{args.tn}_12nn_fp64", "tol": 1e-8,
+           "zn": stats["zn"], "nn": stats["nn"], "cosine_nonzero_entries": stats["nonzero_entries"],
+           "rows": rows}
+    print(json.dumps(out), flush=True)
 
 
 def main():
@@ -308,11 +373,16 @@ def main():
     ap.add_argument("--serving", action="store_true", help="request-loop throughput and latency (extra run)")
     ap.add_argument("--requests", type=int, default=512)
     ap.add_argument("--streams", type=int, default=8)
+    ap.add_argument("--under-frac", type=float, default=0.0, help="serving: fraction of underdetermined requests")
+    ap.add_argument("--thr-sweep", action="store_true", help="grouping threshold sweep with zn/nn (extra run)")
+    ap.add_argument("--tn", type=int, default=200_000, help="n of the threshold sweep")
     args = ap.parse_args()
     if args.precision_study:
         return precision_study(args)
     if args.serving:
         return serving_study(args)
+    if args.thr_sweep:
+        return thr_sweep(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -388,6 +458,10 @@ def main():
     hp.close()
     xh = x.cpu().numpy()
     err_xstar = float(np.linalg.norm(xh - s.xstar) / np.linalg.norm(s.xstar))
+    err_min_norm = None
+    if A.m < A.n:  # the iterate from x0 = 0 approaches the minimum-norm solution
+        xmn = min_norm_solution(A, s.f)
+        err_min_norm = float(np.linalg.norm(xh - xmn) / np.linalg.norm(xmn))
 
     # roofline of the sweep kernel: two solves on one prepared handle, 10 and 60
     # sweeps with a residual only at start and end; the difference is 50 sweeps
@@ -495,6 +569,7 @@ def main():
             "sweeps": info.sweeps, "groups": info.groups, "setup_ms": info.setup_ms, "solve_ms": info.solve_ms,
             "setup_profile_ms": setup_profile,
             "rel_res": info.rel_res, "status": st, "x_err_vs_xstar": err_xstar,
+            **({"x_err_vs_min_norm": err_min_norm} if err_min_norm is not None else {}),
             "bandwidth": [info.bandwidth_before, info.bandwidth_after],
             "gpu_launches": int(launches // max(args.steps, 1)), "gpu_launches_timed_region": int(launches),
             "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,

@@ -197,17 +197,21 @@ class Request:
 
 def request_stream(count: int = 4096, rate_per_s: float = 1000.0, seed: int = 1004,
                    n_lo: int = 1000, n_hi: int = 200_000, frac_over: float = 0.25,
-                   materialize: bool = True) -> list[Request]:
+                   materialize: bool = True, frac_under: float = 0.0) -> list[Request]:
     """Poisson arrivals of independent systems.  n is log-uniform in [n_lo, n_hi];
-    a fraction frac_over is overdetermined (m = 2n, rect_random recipe), the rest is
-    square (random_dominant recipe).  Precision is drawn 50/50 per request.
-    Request r uses seed 10**6 + r for its system."""
+    a fraction frac_over is overdetermined (m = 2n, rect_random recipe), a fraction
+    frac_under underdetermined (m = n // 2, rect_random recipe without the
+    every-column rule), the rest square (random_dominant recipe).  Precision is
+    drawn 50/50 per request.  Request r uses seed 10**6 + r for its system; the
+    stream with frac_under = 0 does not depend on that draw."""
     rng = np.random.Generator(np.random.PCG64(seed))
     gaps = rng.exponential(1.0 / rate_per_s, size=count)
     t = np.cumsum(gaps) - gaps[0]
     logn = rng.uniform(math.log(n_lo), math.log(n_hi), size=count)
     over = rng.random(count) < frac_over
     prec = (rng.random(count) < 0.5).astype(int)
+    under_u = rng.random(count)
+    under = ~over & (under_u < frac_under / max(1.0 - frac_over, 1e-12))
     out = []
     for r in range(count):
         n = int(math.floor(math.exp(logn[r])))
@@ -215,6 +219,9 @@ def request_stream(count: int = 4096, rate_per_s: float = 1000.0, seed: int = 10
         if over[r]:
             m = 2 * n
             sys_ = rect_random(m, n, 10, s) if materialize else None
+        elif under[r]:
+            m = max(n // 2, 1)
+            sys_ = rect_random(m, n, 10, s, full_columns=False) if materialize else None
         else:
             m = n
             sys_ = random_dominant(n, 7, s) if materialize else None

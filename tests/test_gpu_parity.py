@@ -497,3 +497,16 @@ def test_cosine_stats_bit_exact(obk, name):
     assert g["nonzero_entries"] == nz and g["abs_cos_sum"] == tot
     assert g["zn"] == pytest.approx(zn, rel=1e-15) and g["nn"] == pytest.approx(nn, rel=1e-15)
     assert g["groups"] == su.G
+
+
+def test_underdetermined_min_norm(obk):
+    """UOBK (Algorithm 6) from x0 = 0 ends at the minimum-norm solution of a
+    consistent underdetermined system (full row rank): compare with numpy's
+    least-squares minimum-norm solution."""
+    s = synth.rect_random(300, 800, 8, seed=11, full_columns=False)
+    A = s.A
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
+        st, x, info = h.solve(s.f, None, tol=1e-12, maxit=200000)
+    assert st == 0
+    xmn = np.linalg.lstsq(A.to_dense(), s.f, rcond=None)[0]
+    assert np.linalg.norm(x - xmn) / np.linalg.norm(xmn) < 1e-9

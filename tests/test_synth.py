@@ -54,3 +54,18 @@ def test_request_stream_mix():
     assert 0.15 < over < 0.35
     t = np.array([r.arrival_s for r in reqs])
     assert np.all(np.diff(t) >= 0)
+
+
+def test_request_stream_underdetermined_share():
+    base = synth.request_stream(400, seed=5, materialize=False)
+    mixed = synth.request_stream(400, seed=5, materialize=False, frac_under=0.2)
+    # the draw for underdetermined requests leaves the default stream unchanged
+    assert [(r.n, r.m, r.precision) for r in base] == [
+        (r.n, r.m if r.m >= r.n else r.n, r.precision) for r in mixed]
+    under = np.mean([r.m < r.n for r in mixed])
+    assert 0.12 < under < 0.28
+    assert all(r.m == r.n // 2 for r in mixed if r.m < r.n)
+    small = synth.request_stream(30, seed=9, n_lo=1000, n_hi=3000, frac_under=0.5)
+    for r in small:
+        if r.m < r.n:
+            assert r.system.A.m == r.m and r.system.A.n == r.n
