@@ -65,6 +65,8 @@ class _Opts(ctypes.Structure):
         ("inner_sweeps", ctypes.c_int32),
         ("max_outer", ctypes.c_int32),
         ("stagnation", ctypes.c_double),
+        ("pinv_iters", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -211,6 +213,22 @@ def group_step(rp, ci, v, nsq, f, rows, x) -> np.ndarray:
     return x
 
 
+def group_step_pinv(rp, ci, v, nsq, f, rows, x, K) -> np.ndarray:
+    """One group step of Eq. 1.3 from x with K Jacobi steps on the group's Gram
+    system (K = 0: the simultaneous step); returns the new x."""
+    rp, ci, v = _csr(rp, ci, v)
+    N = rp.size - 1
+    x = np.array(x, dtype=np.float64, copy=True)
+    rows = np.ascontiguousarray(rows, np.int32)
+    rc = _load().orc_group_step_pinv(ctypes.c_int64(N), _p(rp), _p(ci), _p(v),
+                                     _p(np.ascontiguousarray(nsq, np.float64)),
+                                     _p(np.ascontiguousarray(f, np.float64)), _p(rows),
+                                     ctypes.c_int64(rows.size), _p(x), ctypes.c_int32(K))
+    if rc:
+        raise MemoryError("oracle group_step_pinv failed")
+    return x
+
+
 def residual(N, rp, ci, v, f, x) -> float:
     rp, ci, v = _csr(rp, ci, v)
     return float(_load().orc_residual(ctypes.c_int64(N), _p(rp), _p(ci), _p(v),
@@ -260,8 +278,9 @@ def setup(m, n, rp, ci, v, f, x0=None, thr=0.1) -> Setup:
 
 
 def solve(m, n, rp, ci, v, f, x0=None, thr=0.1, tol=1e-8, maxit=10000, check_every=1,
-          precision=0, inner_sweeps=4, max_outer=100, stagnation=0.0, return_setup=False):
+          precision=0, inner_sweeps=4, max_outer=100, stagnation=0.0, return_setup=False, pinv_iters=0):
     """Whole OBK-RCM solve (extend, RCM, groups, sweeps to tol, un-permute).
+    pinv_iters > 0: group steps of Eq. 1.3 with that many Jacobi steps (FP64).
     Returns (status, x[n], Info) and, with return_setup, also (perm, group_of)."""
     rp, ci, v = _csr(rp, ci, v)
     N = max(m, n)
@@ -271,7 +290,7 @@ def solve(m, n, rp, ci, v, f, x0=None, thr=0.1, tol=1e-8, maxit=10000, check_eve
     perm = np.empty(N, np.int32)
     gof = np.empty(N, np.int32)
     info = _Info()
-    opts = _Opts(check_every, precision, inner_sweeps, max_outer, stagnation)
+    opts = _Opts(check_every, precision, inner_sweeps, max_outer, stagnation, pinv_iters, 0)
     st = _load().orc_solve(ctypes.c_int64(m), ctypes.c_int64(n), _p(rp), _p(ci), _p(v), _p(f),
                            None if x0p is None else _p(x0p), ctypes.c_double(thr),
                            ctypes.c_double(tol), ctypes.c_int64(maxit), ctypes.byref(opts),

@@ -504,6 +504,128 @@ static void group_step(const int64_t* rp, const int32_t* ci, const double* v,
     }
 }
 
+/* Group step with the projection of Eq. 1.3, x += A_tau^+ (f_tau - A_tau x),
+ * for a group whose rows are not exactly orthogonal: y solves
+ * (A_tau A_tau^T) y = r_tau, r_tau = f_tau - A_tau x from the group-start x,
+ * by K Jacobi steps from y0 = r / ||A_i||^2,
+ *   y_t <- (r_t - sum_{u != t} (A_i . A_j) y_u) / ||A_i||^2   (i = rows[t], j = rows[u]),
+ * the off-diagonal Gram entries being the dot products of the group's rows
+ * that share a column; then x += sum_t y_t A_i^T.  K = 0 is the simultaneous
+ * step.  With every row's sum of |cos| to the others below one the Jacobi
+ * steps converge to the exact solution (Gershgorin), so a large K gives the
+ * pseudo-inverse projection of Eq. 1.3.  cptr/crow/cval: the column lists of
+ * A; pos: N entries, all -1 (restored on return). */
+static int group_step_pinv(int64_t N, const int64_t* rp, const int32_t* ci, const double* v, const double* nsq,
+                           const double* f, const int32_t* rows, int64_t cnt, double* x, int32_t K,
+                           const int64_t* cptr, const int32_t* crow, const double* cval, int64_t* pos)
+{
+    double* r = malloc((size_t)(cnt + 1) * sizeof(double));
+    double* y = malloc((size_t)(cnt + 1) * sizeof(double));
+    double* yn = malloc((size_t)(cnt + 1) * sizeof(double));
+    int64_t* gp = calloc((size_t)cnt + 1, sizeof(int64_t));
+    double* acc = calloc((size_t)cnt + 1, sizeof(double));
+    char* touched = calloc((size_t)cnt + 1, 1);
+    int64_t* tl = malloc((size_t)(cnt + 1) * sizeof(int64_t));
+    int64_t gcap = 16 * (cnt + 1), gn = 0;
+    int64_t* gu = malloc((size_t)gcap * sizeof(int64_t));
+    double* gv = malloc((size_t)gcap * sizeof(double));
+    int rc = ORC_OK;
+    if (!r || !y || !yn || !gp || !acc || !touched || !tl || !gu || !gv) { rc = ORC_NOMEM; goto out; }
+    for (int64_t t = 0; t < cnt; ++t) pos[rows[t]] = t;
+    for (int64_t t = 0; t < cnt; ++t) {
+        int64_t i = rows[t];
+        r[t] = f[i] - row_dot(rp, ci, v, i, x);
+        y[t] = r[t] / nsq[i];
+    }
+    /* off-diagonal Gram entries of the group, row by row (partners ascending) */
+    for (int64_t t = 0; t < cnt; ++t) {
+        int64_t i = rows[t], nt = 0;
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e)
+            for (int64_t q = cptr[ci[e]]; q < cptr[ci[e] + 1]; ++q) {
+                int64_t u = pos[crow[q]];
+                if (u < 0 || u == t) continue;
+                if (!touched[u]) { touched[u] = 1; acc[u] = 0.0; tl[nt++] = u; }
+                acc[u] = acc[u] + v[e] * cval[q];
+            }
+        /* ascending partner order */
+        for (int64_t a = 1; a < nt; ++a) {
+            int64_t key = tl[a], b = a - 1;
+            while (b >= 0 && tl[b] > key) { tl[b + 1] = tl[b]; --b; }
+            tl[b + 1] = key;
+        }
+        for (int64_t a = 0; a < nt; ++a) {
+            int64_t u = tl[a];
+            touched[u] = 0;
+            if (acc[u] == 0.0) continue;
+            if (gn == gcap) {
+                gcap *= 2;
+                int64_t* nu = realloc(gu, (size_t)gcap * sizeof(int64_t));
+                double* nv = realloc(gv, (size_t)gcap * sizeof(double));
+                if (!nu || !nv) { free(nu ? nu : gu); free(nv ? nv : gv); gu = NULL; gv = NULL; rc = ORC_NOMEM; goto out; }
+                gu = nu; gv = nv;
+            }
+            gu[gn] = u; gv[gn] = acc[u]; ++gn;
+        }
+        gp[t + 1] = gn;
+    }
+    for (int32_t k = 0; k < K; ++k) {
+        for (int64_t t = 0; t < cnt; ++t) {
+            double sacc = r[t];
+            for (int64_t a = gp[t]; a < gp[t + 1]; ++a) sacc = sacc - gv[a] * y[gu[a]];
+            yn[t] = sacc / nsq[rows[t]];
+        }
+        double* tmp = y; y = yn; yn = tmp;
+    }
+    for (int64_t t = 0; t < cnt; ++t) {
+        int64_t i = rows[t];
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) x[ci[e]] = x[ci[e]] + v[e] * y[t];
+    }
+out:
+    for (int64_t t = 0; t < cnt; ++t) pos[rows[t]] = -1;
+    (void)N;
+    free(r); free(y); free(yn); free(gp); free(acc); free(touched); free(tl); free(gu); free(gv);
+    return rc;
+}
+
+/* column lists of A (rows ascending) with values */
+static int build_columns(int64_t N, const int64_t* rp, const int32_t* ci, const double* v, int64_t** cptr,
+                         int32_t** crow, double** cval)
+{
+    int64_t nnz = rp[N];
+    *cptr = calloc((size_t)N + 1, sizeof(int64_t));
+    *crow = malloc((size_t)(nnz + 1) * sizeof(int32_t));
+    *cval = malloc((size_t)(nnz + 1) * sizeof(double));
+    int64_t* fill = malloc((size_t)(N + 1) * sizeof(int64_t));
+    if (!*cptr || !*crow || !*cval || !fill) { free(fill); return ORC_NOMEM; }
+    for (int64_t e = 0; e < nnz; ++e) (*cptr)[ci[e] + 1]++;
+    for (int64_t c = 0; c < N; ++c) (*cptr)[c + 1] += (*cptr)[c];
+    for (int64_t c = 0; c < N; ++c) fill[c] = (*cptr)[c];
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+            int64_t q = fill[ci[e]]++;
+            (*crow)[q] = (int32_t)i;
+            (*cval)[q] = v[e];
+        }
+    free(fill);
+    return ORC_OK;
+}
+
+/* Single group step of Eq. 1.3 with K Jacobi steps, exposed for tests. */
+int orc_group_step_pinv(int64_t N, const int64_t* rp, const int32_t* ci, const double* v, const double* nsq,
+                        const double* f, const int32_t* rows, int64_t cnt, double* x, int32_t K)
+{
+    int64_t* cptr = NULL; int32_t* crow = NULL; double* cval = NULL;
+    int64_t* pos = malloc((size_t)(N + 1) * sizeof(int64_t));
+    int rc = build_columns(N, rp, ci, v, &cptr, &crow, &cval);
+    if (rc == ORC_OK && !pos) rc = ORC_NOMEM;
+    if (rc == ORC_OK) {
+        for (int64_t i = 0; i < N; ++i) pos[i] = -1;
+        rc = group_step_pinv(N, rp, ci, v, nsq, f, rows, cnt, x, K, cptr, crow, cval, pos);
+    }
+    free(cptr); free(crow); free(cval); free(pos);
+    return rc;
+}
+
 /* nsweeps full sweeps over groups 0..G-1 in order. */
 int orc_sweep(int64_t N, const int64_t* rp, const int32_t* ci, const double* v,
               const double* nsq, const double* f, int64_t G, const int64_t* gptr,
@@ -571,6 +693,8 @@ typedef struct {
     int32_t inner_sweeps;  /* FP32 sweeps per refinement step */
     int32_t max_outer;     /* refinement steps at most */
     double stagnation;     /* stop (not converged) when rr moved less than this over 10 checks */
+    int32_t pinv_iters;    /* > 0: group steps of Eq. 1.3 with this many Jacobi steps (FP64 form) */
+    int32_t reserved;
 } orc_opts;
 
 /* Adaptive residual-check schedule (a stopping-test cadence, not part of the
@@ -717,12 +841,27 @@ int orc_solve(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci, const 
         for (int64_t g = 0; g < s.G; ++g)
             if (s.gptr[g + 1] - s.gptr[g] > maxc) maxc = s.gptr[g + 1] - s.gptr[g];
         double* y = malloc((size_t)maxc * sizeof(double));
+        int32_t K = opts ? opts->pinv_iters : 0;
+        int64_t* cptr = NULL; int32_t* crow = NULL; double* cval = NULL; int64_t* pos = NULL;
+        if (K > 0) {
+            pos = malloc((size_t)(s.N + 1) * sizeof(int64_t));
+            if (!pos || build_columns(s.N, s.rp, s.ci, s.v, &cptr, &crow, &cval) != ORC_OK) {
+                free(y); free(pos); free(cptr); free(crow); free(cval);
+                sys_free(&s);
+                return ORC_NOMEM;
+            }
+            for (int64_t i = 0; i < s.N; ++i) pos[i] = -1;
+        }
         int64_t next = 1, s_prev = 0;
         double rr_prev = rr;
         for (int64_t sw = 1; sw <= maxit; ++sw) {
-            for (int64_t g = 0; g < s.G; ++g)
-                group_step(s.rp, s.ci, s.v, s.nsq, s.f, s.grows + s.gptr[g],
-                           s.gptr[g + 1] - s.gptr[g], s.x, y);
+            for (int64_t g = 0; g < s.G; ++g) {
+                if (K > 0)
+                    group_step_pinv(s.N, s.rp, s.ci, s.v, s.nsq, s.f, s.grows + s.gptr[g], s.gptr[g + 1] - s.gptr[g],
+                                    s.x, K, cptr, crow, cval, pos);
+                else
+                    group_step(s.rp, s.ci, s.v, s.nsq, s.f, s.grows + s.gptr[g], s.gptr[g + 1] - s.gptr[g], s.x, y);
+            }
             info->sweeps = sw;
             int check = check_every > 0 ? (sw % check_every == 0 || sw == maxit) : (sw >= next || sw == maxit);
             if (check) {
@@ -738,7 +877,7 @@ int orc_solve(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci, const 
                 rr_prev = rr;
             }
         }
-        free(y);
+        free(y); free(pos); free(cptr); free(crow); free(cval);
     } else if (status != ORC_OK) {
         /* precision form: FP64 residual and correction, FP32 inner sweeps */
         int64_t N = s.N;
