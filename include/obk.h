@@ -79,7 +79,15 @@ typedef struct {
     int64_t timeout_spins;  /* bound on every device-side wait (0 = default, ~seconds) */
     int32_t rows_per_warp;  /* sweep kernel: rows one warp handles at a time, 1..32
                                (0 = chosen from the mean row length)                  */
-    int32_t reserved;
+    int32_t pinv_iters;     /* FP64: 0 = the simultaneous group step (default); K > 0 =
+                               the projection of Eq. 1.3 for groups whose rows are not
+                               exactly orthogonal: y solves (A_tau A_tau^T) y = r_tau by
+                               K Jacobi steps from y = r / ||A_i||^2 on the group's Gram
+                               entries (built on the first such solve of a handle), then
+                               x += A_tau^T y.  Each step costs one grid barrier per
+                               group; the steps converge when every row's sum of |cos|
+                               to the rest of its group is below one.  Ignored by
+                               precision 1.  Negative values are OBK_ERR_INVALID.     */
 } obk_opts;
 
 typedef struct {
@@ -220,7 +228,8 @@ OBK_API obk_status obk_residual_noalloc(const int64_t* row_ptr, const int32_t* c
  * x0[i] (n_i values or NULL) and x_out[i] (n_i values) must be device memory.
  * Every system must satisfy (N + 2 * grouped rows) * 8 bytes <= the device's
  * shared memory per block (about N <= 9,000 on GB300), else OBK_ERR_INVALID.
- * Runs FP64 sweeps (opts->precision must be 0); check_every and stagnation
+ * Runs FP64 sweeps (opts->precision must be 0) with the simultaneous group
+ * step (opts->pinv_iters must be 0); check_every and stagnation
  * apply as in obk_solve_ex.  status[i] (and info[i] when not NULL) receive
  * each system's result; the call returns OBK_OK when all were solved
  * (converged or not).  Work is issued on hs[0]'s stream and waited for. */

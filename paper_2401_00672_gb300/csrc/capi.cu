@@ -447,6 +447,7 @@ obk_status obk_solve_ex(obk_handle* h, const obk_opts* opts, const double* f, co
     if (o.precision != 0 && o.precision != 1) throw Error{-1, "precision must be 0 or 1"};
     if (o.check_every < -1 || o.inner_sweeps < 0 || o.max_outer < 0 || o.timeout_spins < 0)
         throw Error{-1, "negative option"};
+    if (o.pinv_iters < 0) throw Error{-1, "pinv_iters must be >= 0"};
     if (o.rows_per_warp != 0 && o.rows_per_warp != 1 && o.rows_per_warp != 2 && o.rows_per_warp != 4 &&
         o.rows_per_warp != 8 && o.rows_per_warp != 16 && o.rows_per_warp != 32)
         throw Error{-1, "rows_per_warp must be 0, 1, 2, 4, 8, 16 or 32"};
@@ -487,6 +488,8 @@ obk_status obk_solve_ex(obk_handle* h, const obk_opts* opts, const double* f, co
     a.maxit = maxit;
     a.spin_limit = o.timeout_spins > 0 ? o.timeout_spins : kDefaultSpins;
     a.sub = o.rows_per_warp > 0 ? 32 / o.rows_per_warp : tuned_or_rule(h, o.precision);
+    a.pinv_iters = o.precision == 0 ? o.pinv_iters : 0;
+    if (a.pinv_iters > 0 && !h->L.has_gram) build_group_gram(h->L, h->err.p, st);
     SolveResult r = run_solve(h->L, fgm.p, fnorm2, zero_f2, xt.p, a, h->err.p, st);
     // x = P^T x~, then x^(1:n)
     double* xo = x_out;
@@ -579,6 +582,7 @@ obk_status obk_solve_batch(obk_handle* const* hs, int32_t count, const obk_opts*
     obk_opts o{};
     if (opts) o = *opts;
     if (o.precision != 0) throw Error{-1, "batched solves run FP64 sweeps (precision 0)"};
+    if (o.pinv_iters != 0) throw Error{-1, "batched solves take the simultaneous group step (pinv_iters 0)"};
     if (o.check_every < -1) throw Error{-1, "check_every must be >= -1"};
     int dev = hs[0] ? hs[0]->device : -1;
     OBK_CUDA(cudaSetDevice(dev));

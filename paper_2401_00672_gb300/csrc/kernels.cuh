@@ -112,6 +112,12 @@ struct SweepLayout {
     std::vector<int64_t> h_sl_gptr;  // G+1, first row slice of each group
     std::vector<int64_t> h_ml_gptr;  // G+1, first mirror slice of each group
     DBuf<int64_t> sl_gptr, ml_gptr;  // device copies of the two
+    // off-diagonal Gram entries of each group (rows of one group sharing a
+    // column), partners ascending; built on the first solve with pinv_iters > 0
+    bool has_gram = false;
+    DBuf<int64_t> gram_ptr;          // Ngm+1
+    DBuf<int32_t> gram_idx;          // group-major partner index
+    DBuf<double> gram_val;           // A_i . A_j
     DBuf<int64_t> sl_ptr;            // ns+1, first entry of each row slice
     DBuf<int64_t> sl_row0;           // ns, group-major index of the slice's first row
     DBuf<int32_t> sl_nrow;           // ns, rows in the slice (32 except a group's last)
@@ -134,6 +140,9 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
                  double thr, long long spin_limit, int* d_err, SweepLayout& L, bool want_fp32,
                  cudaStream_t st, StageClock* clock = nullptr);
 
+// Off-diagonal Gram entries of every group of a built layout (setup.cu).
+void build_group_gram(SweepLayout& L, int* d_err, cudaStream_t st);
+
 // Row cosine-table statistics of a built layout (Definitions 1-2 at the row
 // level): nonzero entries and the sum of |cos| in units of 2^-32 (setup.cu).
 void cosine_stats(const SweepLayout& L, int64_t* nz, uint64_t* sum, int* d_err, cudaStream_t st);
@@ -143,6 +152,7 @@ void cosine_stats(const SweepLayout& L, int64_t* nz, uint64_t* sum, int* d_err, 
 struct SolveArgs {
     int precision = 0;
     int check_every = 1;  // < 0: adaptive schedule
+    int pinv_iters = 0;   // > 0: Jacobi steps of the Eq. 1.3 group projection (FP64)
     int inner_sweeps = 0;
     int max_outer = 100;
     double stagnation = 0.0;

@@ -194,7 +194,8 @@ static void worker_loop(obk_server* s)
         obk_csr A{r->rp.data(), r->ci.data(), r->v.data(), (int64_t)r->ci.size(), 0};
         obk_handle* h = nullptr;
         obk_status rc = obk_create_on_stream(&A, r->m, r->n, r->thr, (void*)st, &h);
-        if (rc == OBK_OK && r->opts.precision == 0 && obk::batch_eligible(h) && !r->cancel.load()) {
+        if (rc == OBK_OK && r->opts.precision == 0 && r->opts.pinv_iters == 0 && obk::batch_eligible(h) &&
+            !r->cancel.load()) {
             // small system: stage f (and x0) on the device, then join the ready list
             bool ok = true;
             try {

@@ -215,6 +215,8 @@ struct PairParams {
     unsigned long long* n_conflicts;
     int* err;
     unsigned long long* stats;  // STATS mode: [0] nonzero cosine-table entries, [1] sum of |cos| in 2^-32
+    const int64_t* gstart;      // GRAM mode: first group-major row of each row's group
+    double* pool_val;           // GRAM mode: the dot product of each listed pair
 };
 
 __device__ __forceinline__ uint32_t hslot(int32_t j, uint32_t mask)
@@ -242,12 +244,17 @@ __device__ __forceinline__ bool is_conflict(double dot, double sj, double si, do
     return fabs(__ddiv_rn(dot, __dmul_rn(sj, si))) >= thr;
 }
 
-// STATS: instead of conflict lists, count the nonzero entries of the row
-// cosine table and add up their magnitudes (rounded to units of 2^-32) for
-// Definitions 1-2; the diagonal (1 for every row here) is included.
-template <bool STATS>
+// Modes: kPairConflicts lists the earlier conflicting rows (|cos| >= thr);
+// kPairStats counts the nonzero entries of the row cosine table and adds up
+// their magnitudes (rounded to units of 2^-32) for Definitions 1-2, the
+// diagonal (1 for every row here) included; kPairGram lists the earlier rows
+// of the same group with a nonzero dot product, with that product.
+enum PairMode { kPairConflicts = 0, kPairStats = 1, kPairGram = 2 };
+
+template <int MODE>
 __global__ void __launch_bounds__(kPairWarps * 32) pair_conflicts(PairParams p)
 {
+    constexpr bool STATS = MODE == kPairStats;
     __shared__ int32_t skey[kPairWarps][kPairCap];
     __shared__ double sval[kPairWarps][kPairCap];
     __shared__ int64_t spre[kPairWarps][32];  // incidence prefix of the current 32 entries
@@ -384,16 +391,21 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_conflicts(PairParams p)
             __syncwarp();
             continue;
         }
-        // one conflict decision per candidate, kept as bits (64 candidates per lane)
+        // one decision per candidate, kept as bits (64 candidates per lane)
         double si = p.s[i];
         double thr_si = p.thr * si;
+        int64_t g0 = MODE == kPairGram ? p.gstart[i] : 0;
+        auto keep = [&](int t) -> bool {
+            if (MODE == kPairGram) return key[t] >= g0 && val[t] != 0.0;
+            return is_conflict(val[t], p.s[key[t]], si, thr_si, p.thr);
+        };
         int cnt = 0;
         unsigned long long flags = 0;
         bool many = nc > 32 * 64;
         for (int t0 = 0, it = 0; t0 < nc; t0 += 32, ++it) {
             int t = t0 + lane;
             bool conf = false;
-            if (t < nc) conf = is_conflict(val[t], p.s[key[t]], si, thr_si, p.thr);
+            if (t < nc) conf = keep(t);
             if (conf && !many) flags |= 1ull << it;
             cnt += __popc(__ballot_sync(0xffffffffu, conf));
         }
@@ -411,9 +423,12 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_conflicts(PairParams p)
                 int t = t0 + lane;
                 bool conf;
                 if (!many) conf = (flags >> it) & 1ull;
-                else conf = t < nc && is_conflict(val[t], p.s[key[t]], si, thr_si, p.thr);
+                else conf = t < nc && keep(t);
                 unsigned b = __ballot_sync(0xffffffffu, conf);
-                if (conf) p.pool[base + run + __popc(b & lt)] = key[t];
+                if (conf) {
+                    p.pool[base + run + __popc(b & lt)] = key[t];
+                    if (MODE == kPairGram) p.pool_val[base + run + __popc(b & lt)] = val[t];
+                }
                 run += __popc(b);
             }
         }
@@ -880,9 +895,10 @@ void cosine_stats(const SweepLayout& L, int64_t* nz, uint64_t* sum, int* d_err, 
     DBuf<unsigned long long> acc(2, st);
     OBK_CUDA(cudaMemsetAsync(acc.p, 0, 2 * sizeof(unsigned long long), st));
     PairParams pp{Ngm, L.grp_rp.p, L.grp_ci.p, L.grp_v.p, cptr.p, crow.p, cval.p, pos_of.p, nsq.p, s.p, 0.0, ub.p,
-                  bigoff.p, big_key.p, big_val.p, nullptr, nullptr, nullptr, 0, nullptr, nullptr, d_err, acc.p};
+                  bigoff.p, big_key.p, big_val.p, nullptr, nullptr, nullptr, 0, nullptr, nullptr, d_err, acc.p,
+                  nullptr, nullptr};
     int blocks = (int)std::min<int64_t>(ceil_div(Ngm, kPairWarps), (int64_t)di.sms * 16);
-    pair_conflicts<true><<<blocks, kPairWarps * 32, 0, st>>>(pp);
+    pair_conflicts<kPairStats><<<blocks, kPairWarps * 32, 0, st>>>(pp);
     OBK_CHECK_LAUNCH();
     if (read_scalar(d_err, st) != 0) throw Error{-5, "internal error: pair table overflow"};
     unsigned long long h[2];
@@ -892,6 +908,125 @@ void cosine_stats(const SweepLayout& L, int64_t* nz, uint64_t* sum, int* d_err, 
     *sum = (uint64_t)h[1];
 }
 
+
+namespace {
+
+__global__ void gm_group_start(int64_t Ngm, int64_t G, const int64_t* gptr, int64_t* gstart)
+{
+    GRID_STRIDE(k, Ngm)
+    {
+        int64_t lo = 0, hi = G;  // the group g with gptr[g] <= k < gptr[g+1]
+        while (hi - lo > 1) {
+            int64_t mid = (lo + hi) >> 1;
+            if (gptr[mid] <= k) lo = mid;
+            else hi = mid;
+        }
+        gstart[k] = gptr[lo];
+    }
+}
+
+// both directions of every listed pair: key row * Ngm + partner, value = the pair's slot
+__global__ void gram_directed(int64_t Ngm, const int32_t* cnt, const int64_t* off, const int32_t* pool,
+                              uint64_t* keys, uint32_t* slot)
+{
+    GRID_STRIDE(i, Ngm)
+    {
+        for (int t = 0; t < cnt[i]; ++t) {
+            int64_t q = off[i] + t;
+            uint64_t j = (uint64_t)pool[q];
+            keys[2 * q] = (uint64_t)i * (uint64_t)Ngm + j;
+            keys[2 * q + 1] = j * (uint64_t)Ngm + (uint64_t)i;
+            slot[2 * q] = (uint32_t)q;
+            slot[2 * q + 1] = (uint32_t)q;
+        }
+    }
+}
+
+__global__ void gram_fill(int64_t n, int64_t Ngm, const uint64_t* keys, const uint32_t* slot, const double* pool_val,
+                          int32_t* idx, double* val, int64_t* rowcnt)
+{
+    GRID_STRIDE(t, n)
+    {
+        uint64_t k = keys[t];
+        idx[t] = (int32_t)(k % (uint64_t)Ngm);
+        val[t] = pool_val[slot[t]];
+        atomicAdd((unsigned long long*)(rowcnt + k / (uint64_t)Ngm), 1ull);
+    }
+}
+
+}  // namespace
+
+void build_group_gram(SweepLayout& L, int* d_err, cudaStream_t st)
+{
+    int64_t Ngm = L.Ngm, N = L.N, nnz = L.nnz_gm;
+    L.gram_ptr.alloc(Ngm + 1, st);
+    OBK_CUDA(cudaMemsetAsync(L.gram_ptr.p, 0, (Ngm + 1) * sizeof(int64_t), st));
+    if (Ngm == 0) {
+        L.gram_idx.alloc(1, st);
+        L.gram_val.alloc(1, st);
+        L.has_gram = true;
+        return;
+    }
+    DevInfo di = dev_info();
+    DBuf<double> nsq(Ngm, st), s(Ngm, st);
+    gm_norms<<<grid_for(Ngm), kBlock, 0, st>>>(Ngm, L.grp_row.p, L.nsq.p, nsq.p, s.p);
+    OBK_CHECK_LAUNCH();
+    DBuf<int64_t> cptr, pos_of;
+    DBuf<int32_t> crow;
+    DBuf<double> cval;
+    build_csc(Ngm, N, L.grp_rp.p, L.grp_ci.p, L.grp_v.p, nnz, cptr, crow, cval, pos_of, st);
+    DBuf<int64_t> ub(Ngm, st), bigsz(Ngm, st), bigoff(Ngm + 1, st), gstart(Ngm, st);
+    pair_upper_bound<<<grid_for(Ngm), kBlock, 0, st>>>(Ngm, L.grp_rp.p, L.grp_ci.p, cptr.p, pos_of.p, ub.p);
+    OBK_CHECK_LAUNCH();
+    big_table_sizes<<<grid_for(Ngm), kBlock, 0, st>>>(Ngm, ub.p, kPairCap, bigsz.p);
+    OBK_CHECK_LAUNCH();
+    exclusive_scan_i64(bigsz.p, bigoff.p, Ngm, st);
+    gm_group_start<<<grid_for(Ngm), kBlock, 0, st>>>(Ngm, L.G, L.gptr.p, gstart.p);
+    OBK_CHECK_LAUNCH();
+    int64_t big_total = read_scalar(bigoff.p + Ngm, st);
+    DBuf<int32_t> big_key(std::max<int64_t>(big_total, 1), st);
+    DBuf<double> big_val(std::max<int64_t>(big_total, 1), st);
+    DBuf<int32_t> cnt(Ngm, st);
+    DBuf<int64_t> off(Ngm, st);
+    DBuf<unsigned long long> counters(2, st);
+    int64_t pool_cap = 8 * Ngm + 1024;
+    DBuf<int32_t> pool;
+    DBuf<double> pool_val;
+    unsigned long long used = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        pool.alloc(pool_cap, st);
+        pool_val.alloc(pool_cap, st);
+        OBK_CUDA(cudaMemsetAsync(counters.p, 0, 2 * sizeof(unsigned long long), st));
+        PairParams pp{Ngm, L.grp_rp.p, L.grp_ci.p, L.grp_v.p, cptr.p, crow.p, cval.p, pos_of.p, nsq.p, s.p, 0.0,
+                      ub.p, bigoff.p, big_key.p, big_val.p, cnt.p, off.p, pool.p, pool_cap, counters.p,
+                      counters.p + 1, d_err, nullptr, gstart.p, pool_val.p};
+        int blocks = (int)std::min<int64_t>(ceil_div(Ngm, kPairWarps), (int64_t)di.sms * 16);
+        pair_conflicts<kPairGram><<<blocks, kPairWarps * 32, 0, st>>>(pp);
+        OBK_CHECK_LAUNCH();
+        if (read_scalar(d_err, st) != 0) throw Error{-5, "internal error: pair table overflow"};
+        used = read_scalar(counters.p, st);
+        if ((int64_t)used <= pool_cap) break;
+        pool_cap = (int64_t)used + 1024;
+    }
+    int64_t M = 2 * (int64_t)used;  // directed entries
+    L.gram_idx.alloc(std::max<int64_t>(M, 1), st);
+    L.gram_val.alloc(std::max<int64_t>(M, 1), st);
+    if (M > 0) {
+        DBuf<uint64_t> keys(M, st);
+        DBuf<uint32_t> slot(M, st);
+        gram_directed<<<grid_for(Ngm), kBlock, 0, st>>>(Ngm, cnt.p, off.p, pool.p, keys.p, slot.p);
+        OBK_CHECK_LAUNCH();
+        radix_sort_pairs(keys.p, slot.p, M, bits_for((uint64_t)Ngm * (uint64_t)Ngm - 1), st);
+        DBuf<int64_t> rowcnt(Ngm, st);
+        OBK_CUDA(cudaMemsetAsync(rowcnt.p, 0, Ngm * sizeof(int64_t), st));
+        gram_fill<<<grid_for(M), kBlock, 0, st>>>(M, Ngm, keys.p, slot.p, pool_val.p, L.gram_idx.p, L.gram_val.p,
+                                                 rowcnt.p);
+        OBK_CHECK_LAUNCH();
+        exclusive_scan_i64(rowcnt.p, L.gram_ptr.p, Ngm, st);
+    }
+    OBK_CUDA(cudaStreamSynchronize(st));
+    L.has_gram = true;
+}
 
 namespace {
 
@@ -1010,9 +1145,9 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
         OBK_CUDA(cudaMemsetAsync(counters.p, 0, 2 * sizeof(unsigned long long), st));
         PairParams pp{N, rp, ci, v, cptr.p, crow.p, cval.p, pos_of.p, L.nsq.p, s.p, thr, ub.p,
                       bigoff.p, big_key.p, big_val.p, conf_cnt.p, conf_off.p, pool.p, pool_cap,
-                      counters.p, counters.p + 1, d_err, nullptr};
+                      counters.p, counters.p + 1, d_err, nullptr, nullptr, nullptr};
         int blocks = (int)std::min<int64_t>(ceil_div(N, kPairWarps), (int64_t)di.sms * 16);
-        pair_conflicts<false><<<blocks, kPairWarps * 32, 0, st>>>(pp);
+        pair_conflicts<kPairConflicts><<<blocks, kPairWarps * 32, 0, st>>>(pp);
         OBK_CHECK_LAUNCH();
         if (read_scalar(d_err, st) != 0) throw Error{-5, "internal error: pair table overflow"};
         unsigned long long used = read_scalar(counters.p, st);

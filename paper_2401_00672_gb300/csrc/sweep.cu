@@ -64,6 +64,13 @@ struct SweepParams {
     const int32_t* mrow;
     const double* mv;
     const float* mv32;
+    // Eq. 1.3 group projection by Jacobi steps (pinv_iters > 0)
+    int pinv_iters;
+    const int64_t* gram_ptr;
+    const int32_t* gram_idx;
+    const double* gram_val;
+    double* y0;       // Ngm: r / ||A_i||^2 of the current group step
+    double* yb;       // Ngm: second Jacobi buffer
     const double* f;  // group-major
     double* x;        // N
     double* y;        // Ngm
@@ -409,6 +416,25 @@ __device__ __forceinline__ int64_t next_check(int64_t s, double rr, int64_t s_pr
     return s + step;
 }
 
+// One Jacobi step of the group's Gram system (A_tau A_tau^T) y = r_tau for the
+// rows of group g: dst_k = y0_k - (1/||A_k||^2) sum_u (A_k . A_u) src_u over
+// the row's partners in the group (ascending), with y0 = r / ||A_k||^2 the
+// phase-1 value, saved from src at the first step.
+__device__ __forceinline__ void jacobi_step(const SweepParams& p, int64_t g, const double* src, double* dst,
+                                            bool first)
+{
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = p.gptr[g] + tid; k < p.gptr[g + 1]; k += nth) {
+        double y0 = src[k];
+        if (first) p.y0[k] = y0;
+        else y0 = p.y0[k];
+        double acc = 0.0;
+        for (int64_t a = p.gram_ptr[k]; a < p.gram_ptr[k + 1]; ++a) acc = fma(p.gram_val[a], src[p.gram_idx[a]], acc);
+        dst[k] = fma(-p.grp_inv[k], acc, y0);
+    }
+}
+
 // one group step's two phases: sliced layout for SUB == 1, sub-warps per CSR row otherwise
 template <int SUB, class T, class TR>
 __device__ __forceinline__ void group_phase1(const SweepParams& p, int64_t g, const T* vals, const T* svals,
@@ -459,8 +485,21 @@ __global__ void __launch_bounds__(kBlock, kBlocksPerSm) obk_solve_kernel(SweepPa
             unsigned long long t0 = lead ? globaltimer() : 0;
             for (int64_t g = 0; g < p.G; ++g) {
                 group_phase1<SUB, double, double>(p, g, p.grp_v, p.sv, p.grp_inv, p.f, p.x, p.y);
+                const double* yg = p.y;
+                if (p.pinv_iters > 0) {  // y <- solution of the group's Gram system
+                    double* src = p.y;
+                    double* dst = p.yb;
+                    for (int k = 0; k < p.pinv_iters; ++k) {
+                        if (!grid_sync(p.gb)) return;
+                        jacobi_step(p, g, src, dst, k == 0);
+                        double* t_ = src;
+                        src = dst;
+                        dst = t_;
+                    }
+                    yg = src;
+                }
                 if (!grid_sync(p.gb)) return;
-                group_phase2<SUB, double>(p, g, p.mir_val, p.mv, p.y, p.x);
+                group_phase2<SUB, double>(p, g, p.mir_val, p.mv, yg, p.x);
                 if (!grid_sync(p.gb)) return;
             }
             ++s;
@@ -614,6 +653,12 @@ SolveResult run_solve(const SweepLayout& L, const double* f_gm, double fnorm2, d
     OBK_CUDA(cudaMemsetAsync(out.p, 0, 8 * sizeof(int64_t), st));
     OBK_CUDA(cudaMemsetAsync(bar.p, 0, kBarrierWords * sizeof(unsigned), st));
     OBK_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+    DBuf<double> y0, yb;
+    if (a.precision == 0 && a.pinv_iters > 0) {
+        if (!L.has_gram) throw Error{-5, "internal error: Gram entries not built"};
+        y0.alloc(std::max<int64_t>(L.Ngm, 1), st);
+        yb.alloc(std::max<int64_t>(L.Ngm, 1), st);
+    }
     SweepParams p{};
     p.N = L.N;
     p.Ngm = L.Ngm;
@@ -645,6 +690,12 @@ SolveResult run_solve(const SweepLayout& L, const double* f_gm, double fnorm2, d
     p.mrow = L.mrow.p;
     p.mv = L.mv.p;
     p.mv32 = L.mv32.p;
+    p.pinv_iters = a.precision == 0 ? a.pinv_iters : 0;
+    p.gram_ptr = L.gram_ptr.p;
+    p.gram_idx = L.gram_idx.p;
+    p.gram_val = L.gram_val.p;
+    p.y0 = y0.p;
+    p.yb = yb.p;
     p.f = f_gm;
     p.x = x;
     p.y = y.p;

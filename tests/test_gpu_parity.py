@@ -510,3 +510,29 @@ def test_underdetermined_min_norm(obk):
     assert st == 0
     xmn = np.linalg.lstsq(A.to_dense(), s.f, rcond=None)[0]
     assert np.linalg.norm(x - xmn) / np.linalg.norm(xmn) < 1e-9
+
+
+@pytest.mark.parametrize("name", ["random_dominant_2000", "knn_30000", "rect_over_3000x1000", "hubs"])
+def test_pinv_group_steps_parity(obk, name):
+    """Eq. 1.3 group steps (K Jacobi steps on each group's Gram system) against
+    the oracle with the same K."""
+    s, su = _case(name)
+    A = s.A
+    K = 8
+    st_o, x_o, io = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1, tol=1e-8, maxit=20000,
+                                 pinv_iters=K)
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
+        st, x, info = h.solve(s.f, None, tol=1e-8, maxit=20000, opts=obk.Opts(pinv_iters=K))
+        st0, x0, info0 = h.solve(s.f, None, tol=1e-8, maxit=20000)  # the default step afterwards
+    assert st == st_o == 0
+    assert abs(info.sweeps - io.sweeps) <= 1
+    assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) <= XTOL
+    assert st0 == 0
+
+
+def test_pinv_iters_rejected_where_unsupported(obk):
+    s, _ = _case("tiny_3x3")
+    A = s.A
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
+        with pytest.raises(obk.ObkError):
+            h.solve(s.f, None, opts=obk.Opts(pinv_iters=-1))
