@@ -359,6 +359,45 @@ def thr_sweep(args):
     print(json.dumps(out), flush=True)
 
 
+def pinv_study(args):
+    """Simultaneous group step against the Eq. 1.3 projection with K Jacobi
+    steps (opts.pinv_iters) on the 1M kNN workload: sweeps and times to 1e-8."""
+    import torch
+
+    import paper_2401_00672_gb300 as obk
+
+    s, cfg = workload("knn1m", 0)
+    A = s.A
+    dev = torch.device("cuda")
+    stream = torch.cuda.Stream()
+    rp = torch.from_numpy(A.row_ptr).to(dev)
+    ci = torch.from_numpy(A.col_idx).to(dev)
+    v = torch.from_numpy(A.val).to(dev)
+    f = torch.from_numpy(s.f).to(dev)
+    x = torch.empty(A.n, dtype=torch.float64, device=dev)
+    h = obk.Handle(rp, ci, v, A.m, A.n, thr=cfg["thr"], stream=stream.cuda_stream)
+    rows = []
+    for K in (0, 1, 2, 4, 8):
+        o = obk.Opts(check_every=-1, pinv_iters=K)
+        h.solve(f, None, tol=cfg["tol"], maxit=20000, out=x, opts=o)  # builds the Gram entries once
+        best = None
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, _, info = h.solve(f, None, tol=cfg["tol"], maxit=20000, out=x, opts=o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        err = float(np.linalg.norm(x.cpu().numpy() - s.xstar) / np.linalg.norm(s.xstar))
+        rows.append({"pinv_iters": K, "status": int(st), "sweeps": info.sweeps, "solve_ms": round(best, 3),
+                     "ms_per_sweep": round(best / max(info.sweeps, 1), 4), "x_err_vs_xstar": err})
+    h.close()
+    print(json.dumps({"metric": "pinv_study", "workload": cfg["workload"], "tol": cfg["tol"], "rows": rows}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -375,6 +414,7 @@ def main():
     ap.add_argument("--streams", type=int, default=8)
     ap.add_argument("--under-frac", type=float, default=0.0, help="serving: fraction of underdetermined requests")
     ap.add_argument("--thr-sweep", action="store_true", help="grouping threshold sweep with zn/nn (extra run)")
+    ap.add_argument("--pinv-study", action="store_true", help="Eq. 1.3 group projection vs the simultaneous step")
     ap.add_argument("--tn", type=int, default=200_000, help="n of the threshold sweep")
     args = ap.parse_args()
     if args.precision_study:
@@ -383,6 +423,8 @@ def main():
         return serving_study(args)
     if args.thr_sweep:
         return thr_sweep(args)
+    if args.pinv_study:
+        return pinv_study(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
