@@ -300,3 +300,50 @@ def solve(m, n, rp, ci, v, f, x0=None, thr=0.1, tol=1e-8, maxit=10000, check_eve
     if return_setup:
         return st, x, _info(info), perm, gof
     return st, x, _info(info)
+
+
+def block_classes(N, rp, ci, v, k, thr):
+    """Algorithm 4's classes on k uniform row blocks: (list of Oclass pairs, Nclass list)."""
+    rp, ci, v = _csr(rp, ci, v)
+    pairs = np.empty(2 * k + 2, np.int32)
+    ncl = np.empty(k + 1, np.int32)
+    np_ = ctypes.c_int32(0)
+    nq = ctypes.c_int32(0)
+    rc = _load().orc_block_classes(ctypes.c_int64(N), _p(rp), _p(ci), _p(v), ctypes.c_int32(k),
+                                   ctypes.c_double(thr), _p(pairs), ctypes.byref(np_), _p(ncl), ctypes.byref(nq))
+    if rc:
+        raise MemoryError("oracle block_classes failed")
+    return [(int(pairs[2 * i]), int(pairs[2 * i + 1])) for i in range(np_.value)], [int(c) for c in ncl[: nq.value]]
+
+
+def block_project(rp, ci, v, f, b0, b1, x, inner_max=500, inner_tol=1e-13) -> np.ndarray:
+    """x + A_b^+ (f_b - A_b x) for the rows [b0, b1), by CGLS from zero."""
+    rp, ci, v = _csr(rp, ci, v)
+    N = rp.size - 1
+    x = np.array(x, dtype=np.float64, copy=True)
+    rc = _load().orc_block_project(ctypes.c_int64(N), _p(rp), _p(ci), _p(v), _p(np.ascontiguousarray(f, np.float64)),
+                                   ctypes.c_int64(b0), ctypes.c_int64(b1), _p(x), ctypes.c_int32(inner_max),
+                                   ctypes.c_double(inner_tol))
+    if rc:
+        raise MemoryError("oracle block_project failed")
+    return x
+
+
+def solve_blocks(m, n, rp, ci, v, f, x0=None, k=8, thr=0.1, tol=1e-8, maxit=1000, inner_max=500, inner_tol=1e-13):
+    """Algorithm 4 as printed (k uniform blocks, centroid-cosine classes, CGLS
+    block projections).  Returns (status, x[n], Info, number of pairs, Nclass size)."""
+    rp, ci, v = _csr(rp, ci, v)
+    f = np.ascontiguousarray(f, np.float64)
+    x0p = None if x0 is None else np.ascontiguousarray(x0, np.float64)
+    x = np.empty(n, np.float64)
+    info = _Info()
+    np_ = ctypes.c_int32(0)
+    nq = ctypes.c_int32(0)
+    st = _load().orc_solve_blocks(ctypes.c_int64(m), ctypes.c_int64(n), _p(rp), _p(ci), _p(v), _p(f),
+                                  None if x0p is None else _p(x0p), ctypes.c_int32(k), ctypes.c_double(thr),
+                                  ctypes.c_double(tol), ctypes.c_int64(maxit), ctypes.c_int32(inner_max),
+                                  ctypes.c_double(inner_tol), _p(x), ctypes.byref(info), ctypes.byref(np_),
+                                  ctypes.byref(nq))
+    if st < 0:
+        raise ValueError(f"oracle solve_blocks rejected the input ({st})")
+    return st, x, _info(info), np_.value, nq.value

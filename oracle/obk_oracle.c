@@ -945,3 +945,192 @@ int orc_setup_export(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci,
     sys_free(&s);
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* The paper-literal block form (Section 3.3, Algorithm 4)             */
+/* ------------------------------------------------------------------ */
+
+/* rows of block b of k uniform chunks of N rows: the first k - 1 take
+ * floor(N / k) rows each in order, the last the rest */
+static void block_range(int64_t N, int32_t k, int32_t b, int64_t* b0, int64_t* b1)
+{
+    int64_t w = N / k;
+    *b0 = (int64_t)b * w;
+    *b1 = b == k - 1 ? N : *b0 + w;
+}
+
+/* Classes of Algorithm 4: centroid of block i = mean of its rows; blocks i
+ * and j are orthogonal when |cos(centroid_i, centroid_j)| < thr (a zero
+ * centroid is orthogonal to everything); for i = 0..k-1 in order, a block not
+ * yet in a class is paired with the first later block, not yet in a class,
+ * orthogonal to it.  pairs[2p], pairs[2p+1] for p < *np; the blocks left over
+ * form Nclass, nclass[q] for q < *nq (ascending). */
+int orc_block_classes(int64_t N, const int64_t* rp, const int32_t* ci, const double* v, int32_t k, double thr,
+                      int32_t* pairs, int32_t* np, int32_t* nclass, int32_t* nq)
+{
+    double* cen = calloc((size_t)k * (size_t)N + 1, sizeof(double));
+    double* nrm = calloc((size_t)k + 1, sizeof(double));
+    char* used = calloc((size_t)k + 1, 1);
+    if (!cen || !nrm || !used) { free(cen); free(nrm); free(used); return ORC_NOMEM; }
+    for (int32_t b = 0; b < k; ++b) {
+        int64_t b0, b1;
+        block_range(N, k, b, &b0, &b1);
+        double* cb = cen + (size_t)b * (size_t)N;
+        for (int64_t i = b0; i < b1; ++i)
+            for (int64_t e = rp[i]; e < rp[i + 1]; ++e) cb[ci[e]] = cb[ci[e]] + v[e];
+        double cnt = (double)(b1 - b0);
+        for (int64_t c = 0; c < N; ++c) cb[c] = cb[c] / cnt;
+        double q = 0.0;
+        for (int64_t c = 0; c < N; ++c) q = q + cb[c] * cb[c];
+        nrm[b] = sqrt(q);
+    }
+    *np = 0;
+    for (int32_t i = 0; i < k; ++i) {
+        if (used[i]) continue;
+        for (int32_t j = i + 1; j < k; ++j) {
+            if (used[j]) continue;
+            double g = 0.0;
+            const double* a = cen + (size_t)i * (size_t)N;
+            const double* b = cen + (size_t)j * (size_t)N;
+            for (int64_t c = 0; c < N; ++c) g = g + a[c] * b[c];
+            double den = nrm[i] * nrm[j];
+            double cosv = den > 0.0 ? g / den : 0.0;
+            if (fabs(cosv) < thr) {
+                pairs[2 * *np] = i;
+                pairs[2 * *np + 1] = j;
+                (*np)++;
+                used[i] = used[j] = 1;
+                break;
+            }
+        }
+    }
+    *nq = 0;
+    for (int32_t i = 0; i < k; ++i)
+        if (!used[i]) nclass[(*nq)++] = i;
+    free(cen); free(nrm); free(used);
+    return ORC_OK;
+}
+
+/* x += A_b^+ (f_b - A_b x) for the rows [b0, b1) of A, the minimum-norm
+ * correction computed by CGLS on min ||A_b d - r|| from d = 0 (which converges
+ * to A_b^+ r): stops when ||A_b^T (r - A_b d)|| <= inner_tol ||A_b^T r|| or after
+ * inner_max steps.  w: 3 N + 2 (b1 - b0) doubles of scratch.  Returns the
+ * number of CGLS steps. */
+static int64_t block_project(int64_t N, const int64_t* rp, const int32_t* ci, const double* v, const double* f,
+                             int64_t b0, int64_t b1, double* x, int32_t inner_max, double inner_tol, double* w)
+{
+    int64_t B = b1 - b0;
+    double* d = w;
+    double* p = w + N;
+    double* sv = w + 2 * N;
+    double* r = w + 3 * N;
+    double* q = r + B;
+    for (int64_t c = 0; c < N; ++c) { d[c] = 0.0; sv[c] = 0.0; }
+    for (int64_t t = 0; t < B; ++t) {
+        int64_t i = b0 + t;
+        double a = 0.0;
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) a = a + v[e] * x[ci[e]];
+        r[t] = f[i] - a;
+    }
+    for (int64_t t = 0; t < B; ++t)
+        for (int64_t e = rp[b0 + t]; e < rp[b0 + t + 1]; ++e) sv[ci[e]] = sv[ci[e]] + v[e] * r[t];
+    double gamma = 0.0;
+    for (int64_t c = 0; c < N; ++c) { p[c] = sv[c]; gamma = gamma + sv[c] * sv[c]; }
+    double gamma0 = gamma;
+    int64_t it = 0;
+    while (it < inner_max && gamma > inner_tol * inner_tol * gamma0 && gamma > 0.0) {
+        double qq = 0.0;
+        for (int64_t t = 0; t < B; ++t) {
+            int64_t i = b0 + t;
+            double a = 0.0;
+            for (int64_t e = rp[i]; e < rp[i + 1]; ++e) a = a + v[e] * p[ci[e]];
+            q[t] = a;
+            qq = qq + a * a;
+        }
+        if (qq == 0.0) break;
+        double alpha = gamma / qq;
+        for (int64_t c = 0; c < N; ++c) d[c] = d[c] + alpha * p[c];
+        for (int64_t t = 0; t < B; ++t) r[t] = r[t] - alpha * q[t];
+        for (int64_t c = 0; c < N; ++c) sv[c] = 0.0;
+        for (int64_t t = 0; t < B; ++t)
+            for (int64_t e = rp[b0 + t]; e < rp[b0 + t + 1]; ++e) sv[ci[e]] = sv[ci[e]] + v[e] * r[t];
+        double gn = 0.0;
+        for (int64_t c = 0; c < N; ++c) gn = gn + sv[c] * sv[c];
+        double beta = gn / gamma;
+        for (int64_t c = 0; c < N; ++c) p[c] = sv[c] + beta * p[c];
+        gamma = gn;
+        ++it;
+    }
+    for (int64_t c = 0; c < N; ++c) x[c] = x[c] + d[c];
+    return it;
+}
+
+/* Single block projection exposed for tests. */
+int orc_block_project(int64_t N, const int64_t* rp, const int32_t* ci, const double* v, const double* f, int64_t b0,
+                      int64_t b1, double* x, int32_t inner_max, double inner_tol)
+{
+    double* w = malloc((size_t)(3 * N + 2 * (b1 - b0) + 1) * sizeof(double));
+    if (!w) return ORC_NOMEM;
+    block_project(N, rp, ci, v, f, b0, b1, x, inner_max, inner_tol, w);
+    free(w);
+    return ORC_OK;
+}
+
+/* Algorithm 4 as printed: extend, RCM, permute; k uniform blocks, their
+ * classes (orc_block_classes); iteration j projects onto the blocks of the
+ * pair j mod P one after the other, then onto the Nclass block j mod Q (either
+ * step is skipped when its class list is empty); the relative residual is
+ * checked after every iteration (info->sweeps counts iterations).  x = P^T x~
+ * then x^(1:n). */
+int orc_solve_blocks(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                     const double* f, const double* x0, int32_t k, double thr, double tol, int64_t maxit,
+                     int32_t inner_max, double inner_tol, double* x_out, orc_info* info, int32_t* np_out,
+                     int32_t* nq_out)
+{
+    memset(info, 0, sizeof(*info));
+    int64_t nnz = rp[m];
+    if (orc_validate(m, n, rp, ci, v, nnz) != ORC_OK) return ORC_INVALID;
+    int64_t N0 = m > n ? m : n;
+    if (k < 1 || k > N0 || !(thr > 0.0 && thr <= 1.0) || !(tol > 0.0) || maxit < 1 || inner_max < 1)
+        return ORC_INVALID;
+    orc_sys s;
+    int rc = sys_setup(m, n, rp, ci, v, f, x0, thr, &s, info);
+    if (rc) return rc;
+    int64_t N = s.N;
+    int32_t* pairs = malloc((size_t)(2 * k + 2) * sizeof(int32_t));
+    int32_t* nclass = malloc((size_t)(k + 1) * sizeof(int32_t));
+    double* w = malloc((size_t)(5 * N + 2) * sizeof(double));
+    int32_t np = 0, nq = 0;
+    if (!pairs || !nclass || !w) rc = ORC_NOMEM;
+    if (!rc) rc = orc_block_classes(N, s.rp, s.ci, s.v, k, thr, pairs, &np, nclass, &nq);
+    int status = ORC_NOT_CONVERGED;
+    if (!rc) {
+        double rr = orc_residual(N, s.rp, s.ci, s.v, s.f, s.x);
+        if (rr <= tol) status = ORC_OK;
+        for (int64_t j = 0; status != ORC_OK && j < maxit; ++j) {
+            int64_t b0, b1;
+            if (np > 0) {
+                int32_t pp = (int32_t)(j % np);
+                for (int h = 0; h < 2; ++h) {
+                    block_range(N, k, pairs[2 * pp + h], &b0, &b1);
+                    block_project(N, s.rp, s.ci, s.v, s.f, b0, b1, s.x, inner_max, inner_tol, w);
+                }
+            }
+            if (nq > 0) {
+                block_range(N, k, nclass[j % nq], &b0, &b1);
+                block_project(N, s.rp, s.ci, s.v, s.f, b0, b1, s.x, inner_max, inner_tol, w);
+            }
+            info->sweeps = j + 1;
+            rr = orc_residual(N, s.rp, s.ci, s.v, s.f, s.x);
+            if (rr <= tol) status = ORC_OK;
+        }
+        info->rel_res = rr;
+        sys_unpermute(&s, n, x_out);
+    }
+    info->status = status;
+    if (np_out) *np_out = np;
+    if (nq_out) *nq_out = nq;
+    free(pairs); free(nclass); free(w);
+    sys_free(&s);
+    return rc ? rc : status;
+}
