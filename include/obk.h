@@ -148,6 +148,37 @@ OBK_API obk_status obk_get_groups(const obk_handle* h, int32_t* group_of);
 OBK_API obk_status obk_get_row_norms(const obk_handle* h, double* nsq);
 OBK_API obk_status obk_get_info(const obk_handle* h, obk_info* info);
 
+/* The paper-literal block form (Section 3.3, Algorithm 4) on a prepared
+ * system: A~ (RCM order) is cut into k uniform row blocks (the first k - 1 take
+ * floor(N / k) rows in order, the last the rest); the centroid of a block is
+ * the mean of its rows; blocks i < j are orthogonal when |cos| of their
+ * centroids is below thr; each block not yet in a class is paired with the
+ * first later block, not yet in a class, orthogonal to it (Oclass), and the
+ * blocks left over form Nclass.  Iteration j projects x~ onto the two blocks
+ * of pair j mod P, one after the other, then onto the Nclass block j mod Q
+ * (Eq. 3.3, x~ += A_b^+ (f~_b - A_b x~), the pseudo-inverse correction computed
+ * by CGLS from zero); the relative residual is checked after every iteration
+ * and info->sweeps counts iterations.  f, x0 and x_out as in obk_solve.  In
+ * bo: k in [1, N]; thr (0 = the handle's grouping threshold); inner_max (0 =
+ * 500) and inner_tol (0 = 1e-13) stop each CGLS run when the normal-equation
+ * residual fell below inner_tol times its start value.  Out: n_pairs,
+ * n_nclass, cgls_steps (over the whole solve).  The first call builds the
+ * column lists of A~ (kept with the handle).  OBK_ERR_INVALID for bad
+ * arguments; OBK_NOT_CONVERGED after maxit iterations. */
+typedef struct {
+    int32_t k;
+    int32_t inner_max;
+    double thr;
+    double inner_tol;
+    int32_t n_pairs;
+    int32_t n_nclass;
+    int64_t cgls_steps;
+    int64_t reserved[2];
+} obk_block_opts;
+
+OBK_API obk_status obk_solve_blocks(obk_handle* h, obk_block_opts* bo, const double* f, const double* x0, double tol,
+                                    int64_t maxit, double* x_out, obk_info* info);
+
 /* Statistics of the cosine table (Section 3.6, Definitions 1 and 2), read at
  * the row level k = N of the extended, permuted matrix A~ (N x N): C_ij is the
  * cosine of rows i and j with the grouping's arithmetic (products over the

@@ -27,7 +27,7 @@ EXPORTS = [
     "obk_get_groups", "obk_get_row_norms", "obk_get_info", "obk_destroy", "obk_server_create",
     "obk_submit", "obk_poll", "obk_cancel", "obk_server_destroy", "obk_last_error", "obk_version",
     "obk_kernel_launches", "obk_residual", "obk_residual_noalloc", "obk_autotune", "obk_solve_batch",
-    "obk_batch_max_n", "obk_get_setup_profile", "obk_grouping_stats",
+    "obk_batch_max_n", "obk_get_setup_profile", "obk_grouping_stats", "obk_solve_blocks",
 ]
 
 
@@ -55,6 +55,13 @@ class _GStats(ctypes.Structure):
                 ("zn", ctypes.c_double), ("nn", ctypes.c_double), ("groups", ctypes.c_int64),
                 ("min_group_rows", ctypes.c_int64), ("max_group_rows", ctypes.c_int64),
                 ("reserved", ctypes.c_int64 * 4)]
+
+
+class BlockOpts(ctypes.Structure):
+    """obk_block_opts (see include/obk.h)."""
+    _fields_ = [("k", ctypes.c_int32), ("inner_max", ctypes.c_int32), ("thr", ctypes.c_double),
+                ("inner_tol", ctypes.c_double), ("n_pairs", ctypes.c_int32), ("n_nclass", ctypes.c_int32),
+                ("cgls_steps", ctypes.c_int64), ("reserved", ctypes.c_int64 * 2)]
 
 
 class _Tune(ctypes.Structure):
@@ -120,6 +127,7 @@ def _load() -> ctypes.CDLL:
         "obk_batch_max_n": ([], ctypes.c_int64),
         "obk_get_setup_profile": ([vp, vp, i32], ctypes.c_int32),
         "obk_grouping_stats": ([vp, vp], ctypes.c_int32),
+        "obk_solve_blocks": ([vp, vp, vp, vp, dbl, i64, vp, vp], ctypes.c_int32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -197,6 +205,20 @@ class Handle:
     SETUP_STAGES = ("upload_validate_extend", "bandwidth_in", "rcm_graph", "rcm_ranks", "rcm_search",
                     "rcm_cuthill_mckee", "permute", "norms_transpose",
                     "pair_cosines", "grouping", "group_rows", "mirror_segments", "bookkeeping")
+
+    def solve_blocks(self, f, x0=None, k: int = 8, thr: float = 0.0, tol: float = 1e-8, maxit: int = 1000,
+                     inner_max: int = 0, inner_tol: float = 0.0, out=None):
+        """obk_solve_blocks (Algorithm 4 as printed).  Returns (status, x, Info, BlockOpts)."""
+        pf, _, kf = _ptr(f, np.float64)
+        px, _, kx = _ptr(x0, np.float64)
+        if out is None:
+            out = np.empty(self.n, np.float64)
+        po, _, ko = _ptr(out, np.float64)
+        bo = BlockOpts(k=k, inner_max=inner_max, thr=thr, inner_tol=inner_tol)
+        info = _Info()
+        rc = lib.obk_solve_blocks(self._h, ctypes.byref(bo), pf, px, float(tol), int(maxit), po, ctypes.byref(info))
+        _check(rc, "obk_solve_blocks")
+        return rc, ko, _info(info), bo
 
     def grouping_stats(self) -> dict:
         """obk_grouping_stats: Definitions 1-2 (zn, nn) of the row cosine table and group sizes."""

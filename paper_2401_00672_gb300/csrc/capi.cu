@@ -283,6 +283,15 @@ struct obk_handle {
     int tuned_sub[2] = {0, 0};  // lanes per row chosen by obk_autotune (0 = not tuned)
     double stage_ms[16] = {};    // obk_create stages (see obk_get_setup_profile)
     int n_stage = 0;
+    // A~ in RCM order (rows and columns) for the block form, with its column
+    // lists built on the first obk_solve_blocks
+    DBuf<int64_t> at_rp;
+    DBuf<int32_t> at_ci;
+    DBuf<double> at_v;
+    bool has_at_cols = false;
+    DBuf<int64_t> at_cptr;
+    DBuf<int32_t> at_crow;
+    DBuf<double> at_cval;
 };
 
 namespace {
@@ -408,6 +417,9 @@ obk_status obk_create_on_stream(const obk_csr* A, int64_t m, int64_t n, double t
             compose_src<<<grid_for(h->L.Ngm), kBlock, 0, st>>>(h->L.Ngm, h->L.grp_row.p, h->perm.p, h->src_gm.p);
             OBK_CHECK_LAUNCH();
         }
+        h->at_rp = std::move(rpt);
+        h->at_ci = std::move(cit);
+        h->at_v = std::move(vt);
         DBuf<int32_t> zf(N, st);
         DBuf<int64_t> zs(N + 1, st);
         zero_row_flags<<<grid_for(N), kBlock, 0, st>>>(N, h->L.group_of.p, zf.p);
@@ -518,6 +530,80 @@ obk_status obk_solve(obk_handle* h, const double* f, const double* x0, double to
                      obk_info* info)
 {
     return obk_solve_ex(h, nullptr, f, x0, tol, maxit, x_out, info);
+}
+
+obk_status obk_solve_blocks(obk_handle* h, obk_block_opts* bo, const double* f, const double* x0, double tol,
+                            int64_t maxit, double* x_out, obk_info* info)
+{
+    OBK_API_BEGIN
+    set_last_error("");
+    if (!h || !bo || !f || !x_out) throw Error{-1, "handle, options, f and x_out must be non-NULL"};
+    if (!(tol > 0.0) || maxit < 1) throw Error{-1, "tol must be > 0 and maxit >= 1"};
+    if (bo->k < 1 || bo->k > h->N) throw Error{-1, "k must be in [1, N]"};
+    if (bo->inner_max < 0 || bo->thr < 0.0 || bo->thr > 1.0 || bo->inner_tol < 0.0)
+        throw Error{-1, "inner_max, thr or inner_tol out of range"};
+    OBK_CUDA(cudaSetDevice(h->device));
+    cudaStream_t st = h->st;
+    int64_t m = h->m, n = h->n, N = h->N;
+    Timer tm(st);
+    if (!h->has_at_cols) {
+        DBuf<int64_t> pos_of;
+        build_csc(N, N, h->at_rp.p, h->at_ci.p, h->at_v.p, h->nnz, h->at_cptr, h->at_crow, h->at_cval, pos_of, st);
+        h->has_at_cols = true;
+    }
+    bool fdev = is_device_ptr(f), xdev = x0 && is_device_ptr(x0), odev = is_device_ptr(x_out);
+    DBuf<double> fd(m, st), x0d, xt(N, st), ft(N, st);
+    to_device(fd.p, f, m, fdev, st);
+    DBuf<int> bad(1, st);
+    OBK_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+    check_finite<<<grid_for(m), kBlock, 0, st>>>(fd.p, m, bad.p);
+    OBK_CHECK_LAUNCH();
+    if (x0) {
+        x0d.alloc(n, st);
+        to_device(x0d.p, x0, n, xdev, st);
+        check_finite<<<grid_for(n), kBlock, 0, st>>>(x0d.p, n, bad.p);
+        OBK_CHECK_LAUNCH();
+    }
+    if (read_scalar(bad.p, st)) throw Error{-1, "f or x0 holds NaN or Inf"};
+    // f~ = P f^ and x~0 = P x^0 (Eq. 3.1), the extension's appended entries 0
+    permute_x0<<<grid_for(N), kBlock, 0, st>>>(N, h->perm.p, fd.p, m, ft.p);
+    OBK_CHECK_LAUNCH();
+    permute_x0<<<grid_for(N), kBlock, 0, st>>>(N, h->perm.p, x0 ? x0d.p : nullptr, n, xt.p);
+    OBK_CHECK_LAUNCH();
+    BlockArgs a;
+    a.k = bo->k;
+    a.thr = bo->thr > 0.0 ? bo->thr : h->thr;
+    a.inner_max = bo->inner_max > 0 ? bo->inner_max : 500;
+    a.inner_tol = bo->inner_tol > 0.0 ? bo->inner_tol : 1e-13;
+    a.tol = tol;
+    a.maxit = maxit;
+    a.spin_limit = kDefaultSpins;
+    BlockResult r = run_blocks(N, h->at_rp.p, h->at_ci.p, h->at_v.p, h->at_cptr.p, h->at_crow.p, h->at_cval.p, ft.p,
+                               xt.p, a, h->err.p, st);
+    double* xo = x_out;
+    DBuf<double> xtmp;
+    if (!odev) {
+        xtmp.alloc(n, st);
+        xo = xtmp.p;
+    }
+    unpermute_x<<<grid_for(N), kBlock, 0, st>>>(N, h->perm.p, xt.p, n, xo);
+    OBK_CHECK_LAUNCH();
+    if (!odev) OBK_CUDA(cudaMemcpyAsync(x_out, xo, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    double ms = tm.stop_ms();
+    OBK_CUDA(cudaStreamSynchronize(st));
+    bo->n_pairs = r.n_pairs;
+    bo->n_nclass = r.n_nclass;
+    bo->cgls_steps = r.cgls_steps;
+    obk_info inf = h->info;
+    inf.sweeps = r.iters;
+    inf.rel_res = r.rel_res;
+    inf.solve_ms = ms;
+    inf.outer_iters = 0;
+    inf.sweep_ms = 0.0;
+    inf.status = r.status;
+    if (info) *info = inf;
+    return r.status == 0 ? OBK_OK : OBK_NOT_CONVERGED;
+    OBK_API_END
 }
 
 obk_status obk_grouping_stats(obk_handle* h, obk_gstats* out)

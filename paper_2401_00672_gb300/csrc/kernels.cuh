@@ -140,6 +140,36 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
                  double thr, long long spin_limit, int* d_err, SweepLayout& L, bool want_fp32,
                  cudaStream_t st, StageClock* clock = nullptr);
 
+// Column lists of a CSR matrix (nrows x ncols, columns sorted in each row):
+// cptr[ncols+1], rows ascending inside each column with their values, and the
+// column-list position of every CSR entry (setup.cu).
+void build_csc(int64_t nrows, int64_t ncols, const int64_t* rp, const int32_t* ci, const double* v, int64_t nnz,
+               DBuf<int64_t>& cptr, DBuf<int32_t>& crow, DBuf<double>& cval, DBuf<int64_t>& pos_of,
+               cudaStream_t st);
+
+// ---- blocks.cu: the paper-literal block form (Section 3.3, Algorithm 4) ----------
+
+struct BlockArgs {
+    int k = 8;
+    double thr = 0.1;
+    int inner_max = 500;
+    double inner_tol = 1e-13;
+    double tol = 1e-8;
+    int64_t maxit = 1000;
+    long long spin_limit = 0;
+};
+struct BlockResult {
+    int64_t iters = 0;
+    int64_t cgls_steps = 0;
+    double rel_res = 0.0;
+    int status = 1;
+    int n_pairs = 0, n_nclass = 0;
+};
+// On A~ (N x N CSR, RCM order) with its column lists, f~ and x~ (updated in place).
+BlockResult run_blocks(int64_t N, const int64_t* rp, const int32_t* ci, const double* v, const int64_t* cptr,
+                       const int32_t* crow, const double* cval, const double* ft, double* xt, const BlockArgs& a,
+                       int* d_err, cudaStream_t st);
+
 // Off-diagonal Gram entries of every group of a built layout (setup.cu).
 void build_group_gram(SweepLayout& L, int* d_err, cudaStream_t st);
 

@@ -821,11 +821,7 @@ void permute_csr(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
     OBK_CHECK_LAUNCH();
 }
 
-namespace {
-
-// Column lists of a CSR matrix (nrows x ncols, columns sorted in each row):
-// cptr[ncols+1], rows ascending inside each column with their values, and the
-// column-list position of every CSR entry.
+// (column lists of a CSR matrix: see kernels.cuh)
 void build_csc(int64_t nrows, int64_t ncols, const int64_t* rp, const int32_t* ci, const double* v, int64_t nnz,
                DBuf<int64_t>& cptr, DBuf<int32_t>& crow, DBuf<double>& cval, DBuf<int64_t>& pos_of,
                cudaStream_t st)
@@ -852,6 +848,8 @@ void build_csc(int64_t nrows, int64_t ncols, const int64_t* rp, const int32_t* c
     }
     exclusive_scan_i64(ccnt.p, cptr.p, ncols, st);
 }
+
+namespace {
 
 __global__ void gm_norms(int64_t Ngm, const int32_t* grp_row, const double* nsq, double* nsq_gm, double* s_gm)
 {

@@ -536,3 +536,21 @@ def test_pinv_iters_rejected_where_unsupported(obk):
     with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
         with pytest.raises(obk.ObkError):
             h.solve(s.f, None, opts=obk.Opts(pinv_iters=-1))
+
+
+@pytest.mark.parametrize("name,k", [("random_dominant_2000", 8), ("knn_30000", 6), ("rect_over_3000x1000", 5),
+                                    ("rect_under_400x1000", 4), ("components", 3), ("diag", 7)])
+def test_block_form_parity(obk, name, k):
+    """Algorithm 4 as printed (k uniform blocks, centroid-cosine classes, CGLS
+    projections): the same classes as the oracle, and x to the parity bound."""
+    s, _ = _case(name)
+    A = s.A
+    tol = 1e-9
+    st_o, x_o, io, np_o, nq_o = oracle.solve_blocks(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, k=k, thr=0.1,
+                                                    tol=tol, maxit=3000)
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
+        st, x, info, bo = h.solve_blocks(s.f, None, k=k, thr=0.1, tol=tol, maxit=3000)
+    assert (bo.n_pairs, bo.n_nclass) == (np_o, nq_o)
+    assert st == st_o == 0
+    assert abs(info.sweeps - io.sweeps) <= 1
+    assert np.linalg.norm(x - x_o) / max(np.linalg.norm(x_o), 1e-300) <= 1e-8
