@@ -398,6 +398,55 @@ def pinv_study(args):
           flush=True)
 
 
+def blocks_study(args):
+    """Algorithm 4 as printed (k uniform blocks, CGLS projections) against the
+    row-group form on the kNN generator at n = args.tn, tol 1e-8."""
+    import torch
+
+    import paper_2401_00672_gb300 as obk
+    import synth
+
+    s = synth.knn_dominant(args.tn, 12, seed=1001)
+    A = s.A
+    dev = torch.device("cuda")
+    stream = torch.cuda.Stream()
+    rp = torch.from_numpy(A.row_ptr).to(dev)
+    ci = torch.from_numpy(A.col_idx).to(dev)
+    v = torch.from_numpy(A.val).to(dev)
+    f = torch.from_numpy(s.f).to(dev)
+    x = torch.empty(A.n, dtype=torch.float64, device=dev)
+    h = obk.Handle(rp, ci, v, A.m, A.n, thr=0.1, stream=stream.cuda_stream)
+    rows = []
+
+    def timed(fn):
+        best, res = None, None
+        for _ in range(2):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        return best, res
+
+    ms, (st, _, info) = timed(lambda: h.solve(f, None, tol=1e-8, maxit=20000, out=x, opts=obk.Opts(check_every=-1)))
+    err = float(np.linalg.norm(x.cpu().numpy() - s.xstar) / np.linalg.norm(s.xstar))
+    rows.append({"form": "row groups (k = n)", "status": int(st), "iterations": info.sweeps, "groups": h.G,
+                 "solve_ms": round(ms, 3), "x_err_vs_xstar": err})
+    for k in (2, 4, 8, 16):
+        h.solve_blocks(f, None, k=k, thr=0.1, tol=1e-8, maxit=1, out=x)  # builds the column lists once
+        ms, (st, _, info, bo) = timed(lambda: h.solve_blocks(f, None, k=k, thr=0.1, tol=1e-8, maxit=5000, out=x))
+        err = float(np.linalg.norm(x.cpu().numpy() - s.xstar) / np.linalg.norm(s.xstar))
+        rows.append({"form": f"blocks k = {k}", "status": int(st), "iterations": info.sweeps,
+                     "oclass_pairs": bo.n_pairs, "nclass": bo.n_nclass, "cgls_steps": int(bo.cgls_steps),
+                     "solve_ms": round(ms, 3), "x_err_vs_xstar": err})
+    h.close()
+    print(json.dumps({"metric": "blocks_study", "workload": f"knn_n{args.tn}_12nn_fp64", "tol": 1e-8,
+                      "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -415,6 +464,7 @@ def main():
     ap.add_argument("--under-frac", type=float, default=0.0, help="serving: fraction of underdetermined requests")
     ap.add_argument("--thr-sweep", action="store_true", help="grouping threshold sweep with zn/nn (extra run)")
     ap.add_argument("--pinv-study", action="store_true", help="Eq. 1.3 group projection vs the simultaneous step")
+    ap.add_argument("--blocks-study", action="store_true", help="paper-literal k-block form vs the row groups")
     ap.add_argument("--tn", type=int, default=200_000, help="n of the threshold sweep")
     args = ap.parse_args()
     if args.precision_study:
@@ -425,6 +475,8 @@ def main():
         return thr_sweep(args)
     if args.pinv_study:
         return pinv_study(args)
+    if args.blocks_study:
+        return blocks_study(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
