@@ -77,7 +77,9 @@ typedef struct {
     double stagnation;      /* FP64: stop with OBK_NOT_CONVERGED when the relative
                                residual moved less than this over 10 checks (0 = off)  */
     int64_t timeout_spins;  /* bound on every device-side wait (0 = default, ~seconds) */
-    int32_t rows_per_warp;  /* sweep kernel: rows one warp handles at a time, 1..32
+    int32_t rows_per_warp;  /* sweep kernel: rows one warp handles at a time, 1..32;
+                               32 = one thread per row on the sliced (SELL-32) layout,
+                               fewer = a sub-warp per row of the group-major CSR
                                (0 = chosen from the mean row length)                  */
     int32_t pinv_iters;     /* FP64: 0 = the simultaneous group step (default); K > 0 =
                                the projection of Eq. 1.3 for groups whose rows are not

@@ -14,9 +14,9 @@
 // GPU formulation: dot products are accumulated Gustavson style (one warp per
 // row i walks its columns in ascending order and, for each column, adds the
 // products with every earlier row of that column into a per-warp hash table),
-// which keeps the per-pair ascending-column order.  First fit is computed by a
-// cooperative dataflow kernel: a row is coloured as soon as all its
-// conflicting earlier rows are, with the colour = smallest unused by them.
+// which keeps the per-pair ascending-column order.  First fit is computed as
+// the unique fixed point of c_i = mex{c_j : j < i conflicting} by rounds of
+// in-place updates until a round changes nothing.
 #include <algorithm>
 #include <vector>
 

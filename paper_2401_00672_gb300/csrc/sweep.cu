@@ -4,14 +4,16 @@
 //
 // One group step (rows of group g are mutually near-orthogonal):
 //   phase 1  y_k = (f_k - A_k . x) / ||A_k||^2 for every row k of the group,
-//            from the x at the start of the group.  A sub-warp of SUB lanes
-//            per row, coalesced loads of the group-major CSR, warp-shuffle
-//            reduction.
-//   phase 2  x_c += sum_k A_kc y_k over the group's rows (ascending), one
-//            thread per (group, column) segment of the column mirror: a
-//            deterministic gather, no floating-point atomics.
+//            from the x at the start of the group: by default one thread per
+//            row on the sliced (SELL-32) layout; for long rows a sub-warp of
+//            SUB lanes per row of the group-major CSR with a shuffle reduction.
+//   phase 2  x_c += sum_k A_kc y_k over the group's rows, one thread per
+//            (group, column) segment of the column mirror (sliced the same
+//            way): a deterministic gather, no floating-point atomics.
 // A grid barrier separates the phases.  For an exactly orthogonal group the
-// update equals x + A_tau^+ (f_tau - A_tau x) (Eq. 1.3).
+// update equals x + A_tau^+ (f_tau - A_tau x) (Eq. 1.3); with pinv_iters > 0,
+// Jacobi steps on the group's Gram system make it that projection for
+// near-orthogonal groups too.
 //
 // Residual check: ||f - A x|| / ||f|| with a fixed-order two-level reduction
 // (deterministic for a given grid).  Block 0 takes the stop decision and the
