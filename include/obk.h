@@ -302,6 +302,11 @@ OBK_API void obk_destroy(obk_handle* h);
  * max_streams CUDA streams (0 = 8). */
 OBK_API obk_status obk_server_create(size_t hbm_budget_bytes, int32_t max_streams, obk_server** out);
 
+/* HBM bytes the request loop reserves against its budget for a request of
+ * an m x n system with nnz entries (0 for invalid sizes).  A request whose
+ * reservation exceeds the budget is refused with OBK_ERR_BUDGET. */
+OBK_API size_t obk_request_footprint(int64_t m, int64_t n, int64_t nnz);
+
 /* Queue one solve.  A, f and x0 (may be NULL) are copied before the call
  * returns.  *ticket identifies the request for obk_poll.  Errors:
  * OBK_ERR_INVALID, OBK_ERR_BUDGET (the request alone exceeds the budget). */

@@ -28,6 +28,7 @@ EXPORTS = [
     "obk_submit", "obk_poll", "obk_cancel", "obk_server_destroy", "obk_last_error", "obk_version",
     "obk_kernel_launches", "obk_residual", "obk_residual_noalloc", "obk_autotune", "obk_solve_batch",
     "obk_batch_max_n", "obk_get_setup_profile", "obk_grouping_stats", "obk_solve_blocks",
+    "obk_request_footprint",
 ]
 
 
@@ -128,6 +129,7 @@ def _load() -> ctypes.CDLL:
         "obk_get_setup_profile": ([vp, vp, i32], ctypes.c_int32),
         "obk_grouping_stats": ([vp, vp], ctypes.c_int32),
         "obk_solve_blocks": ([vp, vp, vp, vp, dbl, i64, vp, vp], ctypes.c_int32),
+        "obk_request_footprint": ([i64, i64, i64], ctypes.c_size_t),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -137,6 +139,11 @@ def _load() -> ctypes.CDLL:
 
 
 lib = _load()
+
+
+def request_footprint(m: int, n: int, nnz: int) -> int:
+    """obk_request_footprint: HBM bytes the request loop reserves for such a request."""
+    return int(lib.obk_request_footprint(int(m), int(n), int(nnz)))
 
 
 def kernel_launches() -> int:

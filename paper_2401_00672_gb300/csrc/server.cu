@@ -50,13 +50,23 @@ struct Request {
 };
 
 // Upper estimate of the device bytes a solve needs at its peak (setup).
+// HBM a request may need while it is prepared and solved: the handle keeps
+// about 100 bytes per entry (group-major rows and column mirror in FP64 and
+// FP32, their sliced copies with padding, A~ for the block form) and 80 per
+// row; obk_create's transients (sorts, pair tables, conflict lists) add up to
+// about as much again at their peak.
 size_t footprint(int64_t m, int64_t n, int64_t nnz)
 {
     int64_t N = std::max(m, n);
-    return (size_t)(nnz * 96 + N * 160 + (64 << 20));
+    return (size_t)(nnz * 192 + N * 256 + (64 << 20));
 }
 
 }  // namespace
+
+extern "C" size_t obk_request_footprint(int64_t m, int64_t n, int64_t nnz)
+{
+    return m > 0 && n > 0 && nnz >= 0 ? footprint(m, n, nnz) : 0;
+}
 
 struct obk_server {
     size_t budget = 0, in_use = 0;

@@ -452,7 +452,7 @@ def test_request_loop_budget_cancel_and_unknown_ticket(obk):
 def test_request_loop_budget_admits_one_at_a_time(obk):
     # the budget fits one request at a time: all still finish, in arrival order
     systems = [synth.random_dominant(3000 + 500 * k, 7, seed=700 + k) for k in range(4)]
-    foot = max(s.A.nnz * 96 + max(s.A.m, s.A.n) * 160 + (64 << 20) for s in systems)
+    foot = max(obk.request_footprint(s.A.m, s.A.n, s.A.nnz) for s in systems)
     srv = obk.Server(hbm_budget_bytes=foot + 1024, max_streams=4)
     tickets = [srv.submit(s.A.row_ptr, s.A.col_idx, s.A.val, s.A.m, s.A.n, s.f, tol=1e-8, maxit=5000)
                for s in systems]
