@@ -864,6 +864,21 @@ inline unsigned grid_for(int64_t n) { return (unsigned)std::min<int64_t>(ceil_di
 
 }  // namespace
 
+namespace {
+// a second stream of the calling thread on the current device (created on
+// first use, kept for the thread's lifetime)
+cudaStream_t aux_stream()
+{
+    constexpr int kMaxDev = 64;
+    thread_local cudaStream_t streams[kMaxDev] = {};
+    int dev = 0;
+    OBK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDev) throw Error{-5, "device index out of range"};
+    if (!streams[dev]) OBK_CUDA(cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking));
+    return streams[dev];
+}
+}  // namespace
+
 void build_sym_graph(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, DBuf<int64_t>& gp,
                      DBuf<int32_t>& adj, cudaStream_t st)
 {
@@ -946,14 +961,14 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
     // SM) so that small systems leave the rest of the GPU to other requests
     int64_t want = std::min<int64_t>((int64_t)di.sms * kCoopBlocksPerSm, ceil_div(N, 2048));
     int bfs_grid = coop_grid((const void*)bfs_levels, kCoopBlock, 0, want);
-    auto run_bfs = [&](const int32_t* sources, int64_t ns) -> int64_t {
+    auto run_bfs = [&](const int32_t* sources, int64_t ns, int grid) -> int64_t {
         OBK_CUDA(cudaMemsetAsync(dist.p, 0xff, N * sizeof(int32_t), st));
         OBK_CUDA(cudaMemsetAsync(cnt4.p, 0, 4 * sizeof(int64_t), st));
         OBK_CUDA(cudaMemsetAsync(bar.p, 0, kBarrierWords * sizeof(unsigned), st));
         BfsParams bp{N, gp.p, adj_r, sources, ns, dist.p, qa.p, qb.p, cnt4.p, nlev.p,
                      GridBarrier{bar.p, d_err, spin_limit}};
         void* args[] = {&bp};
-        OBK_COOP_LAUNCH(bfs_levels, bfs_grid, kCoopBlock, args, st);
+        OBK_COOP_LAUNCH(bfs_levels, grid, kCoopBlock, args, st);
         OBK_CUDA(cudaMemsetAsync(ecc.p, 0, N * sizeof(int32_t), st));
         OBK_CUDA(cudaMemsetAsync(cand_r.p, 0x7f, N * sizeof(int32_t), st));
         ecc_per_comp<<<grid_for(N), kBlock, 0, st>>>(N, dist.p, label.p, ecc.p);
@@ -967,7 +982,7 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
     OBK_CUDA(cudaMemsetAsync(label.p, 0, N * sizeof(int32_t), st));
     DBuf<int32_t> s0(1, st);
     OBK_CUDA(cudaMemcpyAsync(s0.p, by_rank.p, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-    int64_t reached = run_bfs(s0.p, 1);
+    int64_t reached = run_bfs(s0.p, 1, bfs_grid);
     int64_t C = 1;
     DBuf<int32_t> roots;
     if (reached == N) {
@@ -1003,7 +1018,7 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
         comp_order<<<grid_for(N), kBlock, 0, st>>>(N, by_rank.p, label.p, flag.p, fscan.p, cidx.p, roots.p,
                                                    size_by_idx.p, csize.p);
         OBK_CHECK_LAUNCH();
-        run_bfs(roots.p, C);
+        run_bfs(roots.p, C, bfs_grid);
     }
     adj.release();
 
@@ -1014,6 +1029,44 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
     gl_record_root<<<grid_for(C), kBlock, 0, st>>>(C, roots.p, label.p, ecc.p, cand_r.p, by_rank.p,
                                                     ecc_root.p, cand.p, active.p);
     OBK_CHECK_LAUNCH();
+    // Cuthill-McKee from the current roots overlaps the search's last BFS: once
+    // a round has moved the roots, the next round's BFS (which usually only
+    // confirms them) runs beside a Cuthill-McKee pass from them on a second
+    // stream, each on half the grid; if the roots stay, that pass is the result.
+    DBuf<unsigned long long> claim(N, st), prio(N, st);
+    DBuf<int64_t> ccnt(N, st), nl(2, st), ntot(2, st);
+    DBuf<int32_t> qcm(N, st), roots_cm(C, st);
+    DBuf<unsigned> bar_cm(kBarrierWords, st);
+    int half_grid = std::max(1, bfs_grid / 2);
+    int cm_grid_full = coop_grid((const void*)cm_levels, kCoopBlock, 0, want);
+    int cm_grid_half = coop_grid((const void*)cm_levels, kCoopBlock, 0, std::max<int64_t>(1, want / 2));
+    DBuf<unsigned long long> agg(cm_grid_full, st);
+    cudaStream_t st2 = aux_stream();
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    OBK_CUDA(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+    OBK_CUDA(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+    // on every exit the second stream's pass has ended before its buffers go
+    struct EvGuard {
+        cudaEvent_t a, b;
+        bool pending;
+        ~EvGuard()
+        {
+            if (pending) cudaEventSynchronize(b);
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } evg{ev_in, ev_out, false};
+    // Cuthill-McKee from roots_cm into qcm on stream s with the given grid
+    auto launch_cm = [&](cudaStream_t s, int grid) {
+        OBK_CUDA(cudaMemsetAsync(claim.p, 0xff, N * sizeof(unsigned long long), s));
+        OBK_CUDA(cudaMemsetAsync(bar_cm.p, 0, kBarrierWords * sizeof(unsigned), s));
+        OBK_CUDA(cudaMemsetAsync(agg.p, 0, grid * sizeof(unsigned long long), s));
+        CmParams cp{N, gp.p, adj_r, roots_cm.p, C, claim.p, prio.p, qcm.p, ccnt.p, agg.p, ntot.p, nl.p,
+                    GridBarrier{bar_cm.p, d_err, spin_limit}};
+        void* args[] = {&cp};
+        OBK_COOP_LAUNCH(cm_levels, grid, kCoopBlock, args, s);
+    };
+    bool moved = false, cm_done = false;
     int gl_rounds = 0;
     for (;;) {
         ++gl_rounds;
@@ -1022,30 +1075,43 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
         OBK_CHECK_LAUNCH();
         int64_t ns = read_scalar(nsrc.p, st);
         if (ns == 0) break;
-        run_bfs(src.p, ns);
+        const bool spec = moved && bfs_grid > 1;
+        if (spec) {
+            OBK_CUDA(cudaMemcpyAsync(roots_cm.p, roots.p, C * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+            OBK_CUDA(cudaEventRecord(ev_in, st));
+            OBK_CUDA(cudaStreamWaitEvent(st2, ev_in, 0));
+            evg.pending = true;
+            launch_cm(st2, cm_grid_half);
+            OBK_CUDA(cudaEventRecord(ev_out, st2));
+        }
+        run_bfs(src.p, ns, spec ? half_grid : bfs_grid);
         OBK_CUDA(cudaMemsetAsync(any.p, 0, sizeof(int), st));
         gl_compare<<<grid_for(C), kBlock, 0, st>>>(C, roots.p, label.p, ecc.p, cand_r.p, by_rank.p,
                                                     ecc_root.p, cand.p, active.p, any.p);
         OBK_CHECK_LAUNCH();
-        if (read_scalar(any.p, st) == 0) break;
+        int changed = read_scalar(any.p, st);
+        if (spec) {
+            OBK_CUDA(cudaEventSynchronize(ev_out));
+            evg.pending = false;
+            OBK_CUDA(cudaStreamWaitEvent(st, ev_out, 0));  // later stream work sees the pass's output
+        }
+        if (changed == 0) {
+            cm_done = spec;
+            break;
+        }
+        moved = true;
     }
     dist.release(); ecc.release(); cand_r.release(); ecc_root.release(); cand.release();
     active.release(); src.release();
     mark();
 
-    // 6. Cuthill-McKee levels into one queue, then the per-component order
-    DBuf<unsigned long long> claim(N, st), prio(N, st);
-    DBuf<int64_t> ccnt(N, st), nl(2, st), ntot(2, st);
-    int32_t* Q = qa.p;
-    OBK_CUDA(cudaMemsetAsync(claim.p, 0xff, N * sizeof(unsigned long long), st));
-    OBK_CUDA(cudaMemsetAsync(bar.p, 0, kBarrierWords * sizeof(unsigned), st));
-    int cm_grid = coop_grid((const void*)cm_levels, kCoopBlock, 0, want);
-    DBuf<unsigned long long> agg(cm_grid, st);
-    OBK_CUDA(cudaMemsetAsync(agg.p, 0, cm_grid * sizeof(unsigned long long), st));
-    CmParams cp{N, gp.p, adj_r, roots.p, C, claim.p, prio.p, Q, ccnt.p, agg.p, ntot.p, nl.p,
-                GridBarrier{bar.p, d_err, spin_limit}};
-    void* args[] = {&cp};
-    OBK_COOP_LAUNCH(cm_levels, cm_grid, kCoopBlock, args, st);
+    // 6. Cuthill-McKee levels into one queue (unless the overlapped pass already
+    //    ran from the final roots), then the per-component order
+    if (!cm_done) {
+        OBK_CUDA(cudaMemcpyAsync(roots_cm.p, roots.p, C * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        launch_cm(st, cm_grid_full);
+    }
+    int32_t* Q = qcm.p;
     if (read_scalar(d_err, st) != 0) throw Error{-4, "bounded wait or bound check failed in Cuthill-McKee levels"};
     if (read_scalar(nl.p + 1, st) != N) throw Error{-5, "internal error: Cuthill-McKee order does not cover every vertex"};
     const int32_t* cm = Q;
