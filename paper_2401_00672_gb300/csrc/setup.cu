@@ -463,11 +463,18 @@ struct ColorParams {
     GridBarrier gb;
 };
 
+// S lanes per row: the lanes read a row's conflict list together (S
+// consecutive entries at a time, kColorBatch such reads in flight) and OR
+// their colour masks; S = 1 is one thread per row.
+template <int S>
 __global__ void __launch_bounds__(kBlock) greedy_color(ColorParams p)
 {
     __shared__ int s_changed;
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    int sub = (int)(threadIdx.x & (S - 1));
+    int64_t sw = tid / S, nsw = nth / S;
+    unsigned smask = S == 32 ? 0xffffffffu : (((1u << S) - 1u) << ((threadIdx.x & 31) & ~(S - 1)));
     volatile int32_t* col = p.color;
     for (int64_t i = tid; i < p.N; i += nth) col[i] = p.nsq[i] == 0.0 ? -1 : 0;
     if (!grid_sync(p.gb)) return;
@@ -476,23 +483,33 @@ __global__ void __launch_bounds__(kBlock) greedy_color(ColorParams p)
         if (tid == 0) p.changed[(r + 1) % 3] = 0;  // last read two rounds ago
         __syncthreads();
         int ch = 0;
-        for (int64_t i = tid; i < p.N; i += nth) {
+        for (int64_t i = sw; i < p.N; i += nsw) {
             int32_t ci = col[i];
-            if (ci < 0) continue;
+            if (ci < 0) continue;  // the same for the row's S lanes
             int64_t o = p.conf_off[i];
             int n = p.conf_cnt[i];
             unsigned long long used = 0;
-            for (int t0 = 0; t0 < n; t0 += kColorBatch) {
+            for (int t0 = sub; t0 < n; t0 += S * kColorBatch) {
                 int32_t cj[kColorBatch];
 #pragma unroll
                 for (int u = 0; u < kColorBatch; ++u) {
                     cj[u] = -1;
-                    if (t0 + u < n) cj[u] = col[p.pool[o + t0 + u]];
+                    if (t0 + S * u < n) cj[u] = col[p.pool[o + t0 + S * u]];
                 }
 #pragma unroll
                 for (int u = 0; u < kColorBatch; ++u)
                     if (cj[u] >= 0 && cj[u] < 64) used |= 1ull << cj[u];
             }
+            if (S > 1) {
+                unsigned lo = (unsigned)used, hi = (unsigned)(used >> 32);
+#pragma unroll
+                for (int d = S / 2; d > 0; d >>= 1) {
+                    lo |= __shfl_xor_sync(smask, lo, d);
+                    hi |= __shfl_xor_sync(smask, hi, d);
+                }
+                used = ((unsigned long long)hi << 32) | lo;
+            }
+            if (sub != 0) continue;
             int32_t g;
             if (~used != 0ull) {
                 g = __ffsll((long long)~used) - 1;
@@ -1167,9 +1184,16 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
         OBK_CUDA(cudaMemsetAsync(bar.p, 0, kBarrierWords * sizeof(unsigned), st));
         ColorParams cp{N, L.nsq.p, conf_cnt.p, conf_off.p, pool.p, L.group_of.p, changed.p, rounds.p,
                        GridBarrier{bar.p, d_err, spin_limit}};
-        int cgrid = coop_grid((const void*)greedy_color, kBlock, 0, ceil_div(N, (int64_t)kBlock));
+        // lanes per row from the mean conflict-list length
+        double mean_list = N > 0 ? (double)L.n_conflicts / (double)N : 0.0;
+        int lanes = mean_list <= 6.0 ? 1 : mean_list <= 24.0 ? 4 : mean_list <= 96.0 ? 8 : 32;
+        const void* fn = lanes == 1   ? (const void*)greedy_color<1>
+                         : lanes == 4 ? (const void*)greedy_color<4>
+                         : lanes == 8 ? (const void*)greedy_color<8>
+                                      : (const void*)greedy_color<32>;
+        int cgrid = coop_grid(fn, kBlock, 0, ceil_div(N * lanes, (int64_t)kBlock));
         void* args[] = {&cp};
-        OBK_COOP_LAUNCH(greedy_color, cgrid, kBlock, args, st);
+        OBK_COOP_LAUNCH(fn, cgrid, kBlock, args, st);
         if (read_scalar(d_err, st) != 0) throw Error{-4, "bounded wait expired in greedy grouping"};
         L.color_rounds = read_scalar(rounds.p, st);
     }
