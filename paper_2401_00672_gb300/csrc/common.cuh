@@ -235,4 +235,9 @@ namespace obk {
 // Keys within a segment should be distinct for a deterministic result.
 void segmented_sort_u32(const int64_t* ptr, int64_t nseg, uint32_t* keys, uint32_t* vals,
                         cudaStream_t st);
+// Transpose of a CSR pattern (nrows x ncols, column indices of each row
+// distinct): column pointers cptr (ncols + 1) and, per column in ascending
+// row order, the row (trow) and the source entry index (tsrc) of each entry.
+void transpose_pattern(int64_t nrows, int64_t ncols, const int64_t* rp, const int32_t* ci, int64_t nnz,
+                       DBuf<int64_t>& cptr, DBuf<uint32_t>& trow, DBuf<uint32_t>& tsrc, cudaStream_t st);
 }  // namespace obk

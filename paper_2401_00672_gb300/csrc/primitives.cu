@@ -186,32 +186,99 @@ __global__ void radix_scatter(const uint64_t* keys_in, const uint32_t* vals_in, 
 
 // ---- segmented sort of (u32 key, u32 value) by key inside each segment ------
 //
-// Segments [ptr[s], ptr[s+1]).  Short segments are insertion-sorted by one
-// thread, medium ones by one block with a bitonic network in shared memory,
-// and the rare long ones by the global radix sort on (segment, key).
+// Segments [ptr[s], ptr[s+1]).  Short segments are sorted by one thread in
+// registers with Batcher's odd-even merge sort network (8, 16, 32 or 64 inputs,
+// padded with the largest value), medium ones by one block with a bitonic
+// network in shared memory, and the rare long ones by the global radix sort
+// on (segment, key).  Pairs compare as (key, value), which is key order when
+// the keys of a segment are distinct.
 
 constexpr int kSegShort = 32;
+constexpr int kSegMid = 64;
 constexpr int kSegMedium = 2048;
 
+__device__ __forceinline__ void cmp_swap(uint64_t& a, uint64_t& b)
+{
+    uint64_t lo = a < b ? a : b;
+    b = a < b ? b : a;
+    a = lo;
+}
+
+// Batcher's odd-even merge sort of a[LO, LO + N) (N a power of two), written as
+// template recursion so that every index is a compile-time constant and a[]
+// stays in registers.  merge<LO, N, R> merges the elements R apart.
+template <int W, int LO, int N, int R>
+struct OddEvenMerge {
+    __device__ __forceinline__ static void run(uint64_t (&a)[W])
+    {
+        if constexpr (2 * R < N) {
+            OddEvenMerge<W, LO, N, 2 * R>::run(a);
+            OddEvenMerge<W, LO + R, N, 2 * R>::run(a);
+#pragma unroll
+            for (int i = LO + R; i + R < LO + N; i += 2 * R) cmp_swap(a[i], a[i + R]);
+        } else {
+            cmp_swap(a[LO], a[LO + R]);
+        }
+    }
+};
+
+template <int W, int LO, int N>
+struct OddEvenSort {
+    __device__ __forceinline__ static void run(uint64_t (&a)[W])
+    {
+        if constexpr (N > 1) {
+            OddEvenSort<W, LO, N / 2>::run(a);
+            OddEvenSort<W, LO + N / 2, N / 2>::run(a);
+            OddEvenMerge<W, LO, N, 1>::run(a);
+        }
+    }
+};
+
+template <int W>
+__device__ __forceinline__ void oddeven_sort(uint64_t (&a)[W])
+{
+    OddEvenSort<W, 0, W>::run(a);
+}
+
+template <int W>
+__device__ __forceinline__ void sort_segment(int64_t b, int64_t len, uint32_t* keys, uint32_t* vals)
+{
+    uint64_t a[W];
+#pragma unroll
+    for (int t = 0; t < W; ++t)
+        a[t] = t < len ? ((uint64_t)keys[b + t] << 32) | (uint64_t)vals[b + t] : ~0ull;
+    oddeven_sort<W>(a);
+#pragma unroll
+    for (int t = 0; t < W; ++t)
+        if (t < len) {
+            keys[b + t] = (uint32_t)(a[t] >> 32);
+            vals[b + t] = (uint32_t)a[t];
+        }
+}
+
 __global__ void segsort_short(const int64_t* ptr, int64_t nseg, uint32_t* keys, uint32_t* vals,
-                              int32_t* longs, int32_t* nlong, int32_t* huge, int32_t* nhuge)
+                              int32_t* longs, int32_t* nlong, int32_t* huge, int32_t* nhuge, int32_t* mids,
+                              int32_t* nmid)
 {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nseg) return;
     int64_t b = ptr[s], e = ptr[s + 1], len = e - b;
     if (len <= 1) return;
     if (len > kSegMedium) { huge[atomicAdd(nhuge, 1)] = (int32_t)s; return; }
-    if (len > kSegShort) { longs[atomicAdd(nlong, 1)] = (int32_t)s; return; }
-    uint32_t k[kSegShort], v[kSegShort];
-    for (int t = 0; t < len; ++t) { k[t] = keys[b + t]; v[t] = vals[b + t]; }
-    for (int t = 1; t < len; ++t) {
-        uint32_t kk = k[t], vv = v[t];
-        int u = t - 1;
-        while (u >= 0 && k[u] > kk) { k[u + 1] = k[u]; v[u + 1] = v[u]; --u; }
-        k[u + 1] = kk;
-        v[u + 1] = vv;
-    }
-    for (int t = 0; t < len; ++t) { keys[b + t] = k[t]; vals[b + t] = v[t]; }
+    if (len > kSegMid) { longs[atomicAdd(nlong, 1)] = (int32_t)s; return; }
+    if (len > kSegShort) { mids[atomicAdd(nmid, 1)] = (int32_t)s; return; }
+    if (len <= 8) sort_segment<8>(b, len, keys, vals);
+    else if (len <= 16) sort_segment<16>(b, len, keys, vals);
+    else sort_segment<32>(b, len, keys, vals);
+}
+
+// segments of 33..64 pairs (listed), one thread each
+__global__ void segsort_mid(const int64_t* ptr, const int32_t* mids, int32_t nmid, uint32_t* keys, uint32_t* vals)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nmid) return;
+    int64_t s = mids[t];
+    sort_segment<64>(ptr[s], ptr[s + 1] - ptr[s], keys, vals);
 }
 
 __global__ void segsort_medium(const int64_t* ptr, const int32_t* longs, uint32_t* keys, uint32_t* vals)
@@ -351,14 +418,18 @@ void segmented_sort_u32(const int64_t* ptr, int64_t nseg, uint32_t* keys, uint32
                         cudaStream_t st)
 {
     if (nseg <= 0) return;
-    DBuf<int32_t> longs(nseg, st), huge(nseg, st), cnt(2, st);
-    OBK_CUDA(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(int32_t), st));
+    DBuf<int32_t> longs(nseg, st), huge(nseg, st), mids(nseg, st), cnt(3, st);
+    OBK_CUDA(cudaMemsetAsync(cnt.p, 0, 3 * sizeof(int32_t), st));
     segsort_short<<<(unsigned)ceil_div(nseg, 256), 256, 0, st>>>(ptr, nseg, keys, vals, longs.p, cnt.p,
-                                                                 huge.p, cnt.p + 1);
+                                                                 huge.p, cnt.p + 1, mids.p, cnt.p + 2);
     OBK_CHECK_LAUNCH();
-    int32_t h_cnt[2];
+    int32_t h_cnt[3];
     OBK_CUDA(cudaMemcpyAsync(h_cnt, cnt.p, sizeof(h_cnt), cudaMemcpyDeviceToHost, st));
     OBK_CUDA(cudaStreamSynchronize(st));
+    if (h_cnt[2] > 0) {
+        segsort_mid<<<(unsigned)ceil_div(h_cnt[2], 128), 128, 0, st>>>(ptr, mids.p, h_cnt[2], keys, vals);
+        OBK_CHECK_LAUNCH();
+    }
     if (h_cnt[0] > 0) {
         segsort_medium<<<(unsigned)h_cnt[0], 512, 0, st>>>(ptr, longs.p, keys, vals);
         OBK_CHECK_LAUNCH();
@@ -382,6 +453,62 @@ void segmented_sort_u32(const int64_t* ptr, int64_t nseg, uint32_t* keys, uint32
         segsort_huge_scatter<<<256, 256, 0, st>>>(ptr, huge.p, hoff.p, nh, k64.p, pos.p, vsrc.p, keys,
                                                   vals);
         OBK_CHECK_LAUNCH();
+    }
+}
+
+namespace {
+
+__global__ void column_counts(const int32_t* ci, int64_t nnz, unsigned* cnt)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(cnt + ci[e], 1u);
+}
+
+__global__ void column_scatter(int64_t nrows, const int64_t* rp, const int32_t* ci, const int64_t* cptr,
+                               unsigned* cur, uint32_t* trow, uint32_t* tsrc)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrows;
+         i += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+            int32_t c = ci[e];
+            int64_t slot = cptr[c] + (int64_t)atomicAdd(cur + c, 1u);
+            trow[slot] = (uint32_t)i;
+            tsrc[slot] = (uint32_t)e;
+        }
+}
+
+__global__ void widen_counts(const unsigned* cnt, int64_t n, int64_t* out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int64_t)cnt[i];
+}
+
+}  // namespace
+
+void transpose_pattern(int64_t nrows, int64_t ncols, const int64_t* rp, const int32_t* ci, int64_t nnz,
+                       DBuf<int64_t>& cptr, DBuf<uint32_t>& trow, DBuf<uint32_t>& tsrc, cudaStream_t st)
+{
+    constexpr int kT = 256;
+    auto grid = [](int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kT), 65535)); };
+    cptr.alloc(ncols + 1, st);
+    trow.alloc(std::max<int64_t>(nnz, 1), st);
+    tsrc.alloc(std::max<int64_t>(nnz, 1), st);
+    DBuf<unsigned> cnt(std::max<int64_t>(ncols, 1), st);
+    DBuf<int64_t> wide(std::max<int64_t>(ncols, 1), st);
+    OBK_CUDA(cudaMemsetAsync(cnt.p, 0, std::max<int64_t>(ncols, 1) * sizeof(unsigned), st));
+    if (nnz) {
+        column_counts<<<grid(nnz), kT, 0, st>>>(ci, nnz, cnt.p);
+        OBK_CHECK_LAUNCH();
+    }
+    widen_counts<<<grid(ncols), kT, 0, st>>>(cnt.p, ncols, wide.p);
+    OBK_CHECK_LAUNCH();
+    exclusive_scan_i64(wide.p, cptr.p, ncols, st);
+    if (nnz) {
+        OBK_CUDA(cudaMemsetAsync(cnt.p, 0, std::max<int64_t>(ncols, 1) * sizeof(unsigned), st));
+        column_scatter<<<grid(nrows), kT, 0, st>>>(nrows, rp, ci, cptr.p, cnt.p, trow.p, tsrc.p);
+        OBK_CHECK_LAUNCH();
+        // a column's rows are distinct: sorting them restores row order
+        segmented_sort_u32(cptr.p, ncols, trow.p, tsrc.p, st);
     }
 }
 

@@ -43,30 +43,6 @@ constexpr int32_t kUnvisited = -1;
 
 // ---- symmetric graph: pattern(A + A^T) minus self loops -----------------------
 
-__global__ void expand_rows(const int64_t* rp, int64_t N, int32_t* row_of)
-{
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x)
-        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) row_of[e] = (int32_t)i;
-}
-
-__global__ void col_keys(const int32_t* ci, int64_t nnz, uint64_t* keys, uint32_t* vals,
-                         const int32_t* row_of)
-{
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        keys[e] = (uint64_t)(uint32_t)ci[e];
-        vals[e] = (uint32_t)row_of[e];
-    }
-}
-
-__global__ void count_cols(const int32_t* ci, int64_t nnz, int64_t* cnt)
-{
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
-         e += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd((unsigned long long*)&cnt[ci[e]], 1ull);
-}
-
 // Merge row i of A (sorted columns) with row i of A^T (sorted rows of column i):
 // the union without i.  Pass 0 counts, pass 1 writes.
 template <bool kWrite>
@@ -882,24 +858,11 @@ cudaStream_t aux_stream()
 void build_sym_graph(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, DBuf<int64_t>& gp,
                      DBuf<int32_t>& adj, cudaStream_t st)
 {
-    DBuf<int32_t> row_of(nnz, st);
-    if (nnz) {
-        expand_rows<<<grid_for(N), kBlock, 0, st>>>(rp, N, row_of.p);
-        OBK_CHECK_LAUNCH();
-    }
-    // transpose pattern: stable sort of (column, row) by column
-    DBuf<uint64_t> keys(nnz, st);
-    DBuf<uint32_t> trow(nnz, st);
-    DBuf<int64_t> ccnt(N + 1, st), tp(N + 1, st);
-    OBK_CUDA(cudaMemsetAsync(ccnt.p, 0, (N + 1) * sizeof(int64_t), st));
-    if (nnz) {
-        col_keys<<<grid_for(nnz), kBlock, 0, st>>>(ci, nnz, keys.p, trow.p, row_of.p);
-        OBK_CHECK_LAUNCH();
-        radix_sort_pairs(keys.p, trow.p, nnz, bits_for((uint64_t)(N - 1)), st);
-        count_cols<<<grid_for(nnz), kBlock, 0, st>>>(ci, nnz, ccnt.p);
-        OBK_CHECK_LAUNCH();
-    }
-    exclusive_scan_i64(ccnt.p, tp.p, N, st);
+    // transpose pattern: the rows of each column, ascending
+    DBuf<int64_t> tp;
+    DBuf<uint32_t> trow, tsrc;
+    transpose_pattern(N, N, rp, ci, nnz, tp, trow, tsrc, st);
+    tsrc.release();
     DBuf<int64_t> deg(N + 1, st);
     merge_sym<false><<<grid_for(N), kBlock, 0, st>>>(N, rp, ci, tp.p, trow.p, nullptr, deg.p, nullptr);
     OBK_CHECK_LAUNCH();

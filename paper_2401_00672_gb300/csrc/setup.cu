@@ -122,34 +122,14 @@ __global__ void row_norms_exact(int64_t N, const int64_t* rp, const double* v, d
     }
 }
 
-__global__ void expand_rows_k(const int64_t* rp, int64_t N, int32_t* row_of)
-{
-    GRID_STRIDE(i, N)
-    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) row_of[e] = (int32_t)i;
-}
-
-__global__ void col_key_kernel(int64_t nnz, const int32_t* ci, uint64_t* keys, uint32_t* vals)
-{
-    GRID_STRIDE(e, nnz)
-    {
-        keys[e] = (uint64_t)(uint32_t)ci[e];
-        vals[e] = (uint32_t)e;
-    }
-}
-
-__global__ void count_cols_k(int64_t nnz, const int32_t* ci, int64_t* cnt)
-{
-    GRID_STRIDE(e, nnz) atomicAdd((unsigned long long*)&cnt[ci[e]], 1ull);
-}
-
-// CSC arrays from the sorted entry list; pos_of[e] = CSC position of entry e.
-__global__ void csc_fill(int64_t nnz, const uint32_t* order, const int32_t* row_of, const double* v,
+// CSC arrays from the transposed pattern; pos_of[e] = CSC position of entry e.
+__global__ void csc_fill(int64_t nnz, const uint32_t* src, const uint32_t* trow, const double* v,
                          int32_t* crow, double* cval, int64_t* pos_of)
 {
     GRID_STRIDE(p, nnz)
     {
-        uint32_t e = order[p];
-        crow[p] = row_of[e];
+        uint32_t e = src[p];
+        crow[p] = (int32_t)trow[p];
         cval[p] = v[e];
         pos_of[e] = p;
     }
@@ -843,27 +823,15 @@ void build_csc(int64_t nrows, int64_t ncols, const int64_t* rp, const int32_t* c
                DBuf<int64_t>& cptr, DBuf<int32_t>& crow, DBuf<double>& cval, DBuf<int64_t>& pos_of,
                cudaStream_t st)
 {
-    DBuf<int32_t> row_of(std::max<int64_t>(nnz, 1), st);
-    DBuf<int64_t> ccnt(ncols + 1, st);
-    cptr.alloc(ncols + 1, st);
+    DBuf<uint32_t> trow, tsrc;
+    transpose_pattern(nrows, ncols, rp, ci, nnz, cptr, trow, tsrc, st);
     pos_of.alloc(std::max<int64_t>(nnz, 1), st);
     crow.alloc(std::max<int64_t>(nnz, 1), st);
     cval.alloc(std::max<int64_t>(nnz, 1), st);
-    OBK_CUDA(cudaMemsetAsync(ccnt.p, 0, (ncols + 1) * sizeof(int64_t), st));
     if (nnz) {
-        expand_rows_k<<<grid_for(nrows), kBlock, 0, st>>>(rp, nrows, row_of.p);
-        OBK_CHECK_LAUNCH();
-        DBuf<uint64_t> keys(nnz, st);
-        DBuf<uint32_t> order(nnz, st);
-        col_key_kernel<<<grid_for(nnz), kBlock, 0, st>>>(nnz, ci, keys.p, order.p);
-        OBK_CHECK_LAUNCH();
-        radix_sort_pairs(keys.p, order.p, nnz, bits_for((uint64_t)std::max<int64_t>(ncols - 1, 1)), st);
-        count_cols_k<<<grid_for(nnz), kBlock, 0, st>>>(nnz, ci, ccnt.p);
-        OBK_CHECK_LAUNCH();
-        csc_fill<<<grid_for(nnz), kBlock, 0, st>>>(nnz, order.p, row_of.p, v, crow.p, cval.p, pos_of.p);
+        csc_fill<<<grid_for(nnz), kBlock, 0, st>>>(nnz, tsrc.p, trow.p, v, crow.p, cval.p, pos_of.p);
         OBK_CHECK_LAUNCH();
     }
-    exclusive_scan_i64(ccnt.p, cptr.p, ncols, st);
 }
 
 namespace {
@@ -1153,7 +1121,16 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
     DBuf<int32_t> conf_cnt(N, st);
     DBuf<int64_t> conf_off(N, st);
     DBuf<unsigned long long> counters(2, st);
-    int64_t pool_cap = 8 * N + 1024;
+    // the candidates (earlier rows sharing a column) bound the conflicts: a
+    // pool that holds them all needs one pass; past 24 per entry it starts
+    // smaller and grows once if needed
+    int64_t cand_total = 0;
+    {
+        DBuf<int64_t> ubscan(N + 1, st);
+        exclusive_scan_i64(ub.p, ubscan.p, N, st);
+        cand_total = read_scalar(ubscan.p + N, st);
+    }
+    int64_t pool_cap = std::min(cand_total, std::max<int64_t>(8 * N, 24 * nnz)) + 1024;
     DBuf<int32_t> pool;
     for (int attempt = 0; attempt < 2; ++attempt) {
         pool.alloc(pool_cap, st);
