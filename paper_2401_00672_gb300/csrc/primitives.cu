@@ -464,17 +464,33 @@ __global__ void column_counts(const int32_t* ci, int64_t nnz, unsigned* cnt)
         atomicAdd(cnt + ci[e], 1u);
 }
 
-__global__ void column_scatter(int64_t nrows, const int64_t* rp, const int32_t* ci, const int64_t* cptr,
-                               unsigned* cur, uint32_t* trow, uint32_t* tsrc)
+// one thread per row; a row's entries in batches of kScatterBatch so that
+// their atomics are in flight together
+constexpr int kScatterBatch = 8;
+
+__global__ void column_scatter(int64_t nrows, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                               const int64_t* __restrict__ cptr, unsigned* __restrict__ cur,
+                               uint32_t* __restrict__ trow, uint32_t* __restrict__ tsrc)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrows;
-         i += (int64_t)gridDim.x * blockDim.x)
-        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
-            int32_t c = ci[e];
-            int64_t slot = cptr[c] + (int64_t)atomicAdd(cur + c, 1u);
-            trow[slot] = (uint32_t)i;
-            tsrc[slot] = (uint32_t)e;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e1 = rp[i + 1];
+        for (int64_t e0 = rp[i]; e0 < e1; e0 += kScatterBatch) {
+            int32_t c[kScatterBatch];
+#pragma unroll
+            for (int t = 0; t < kScatterBatch; ++t) c[t] = e0 + t < e1 ? ci[e0 + t] : -1;
+            unsigned k[kScatterBatch];
+#pragma unroll
+            for (int t = 0; t < kScatterBatch; ++t) k[t] = c[t] >= 0 ? atomicAdd(cur + c[t], 1u) : 0u;
+#pragma unroll
+            for (int t = 0; t < kScatterBatch; ++t)
+                if (c[t] >= 0) {
+                    int64_t slot = cptr[c[t]] + (int64_t)k[t];
+                    trow[slot] = (uint32_t)i;
+                    tsrc[slot] = (uint32_t)(e0 + t);
+                }
         }
+    }
 }
 
 __global__ void widen_counts(const unsigned* cnt, int64_t n, int64_t* out)
