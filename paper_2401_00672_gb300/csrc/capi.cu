@@ -43,6 +43,10 @@ cudaMemPool_t lib_pool()
         OBK_CUDA(cudaMemPoolCreate(&pools[dev], &props));
         uint64_t keep = UINT64_MAX;
         OBK_CUDA(cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+        // memory freed on one stream is not handed to another stream by
+        // making it wait for the first: concurrent requests stay independent
+        int no = 0;
+        OBK_CUDA(cudaMemPoolSetAttribute(pools[dev], cudaMemPoolReuseAllowInternalDependencies, &no));
     }
     return pools[dev];
 }
