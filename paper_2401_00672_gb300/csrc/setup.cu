@@ -206,22 +206,28 @@ __device__ __forceinline__ uint32_t hslot(int32_t j, uint32_t mask)
 
 // |cos_ij| >= thr with cos_ij = RN(dot / RN(s_j * s_i)), decided exactly.
 // t = RN(RN(thr * s_i) * s_j) is within 3 units of rounding of thr * s_i * s_j,
-// so |dot| above t (1 + 2^-48) proves the quotient exceeds thr, and below
-// t (1 - 2^-48) proves it rounds below thr; only the narrow band in between
-// takes the IEEE division.  The comparisons use the ordered bit patterns of
-// non-negative doubles (integer compares).
+// so |dot| more than 32 units in the last place of t above t (a relative
+// margin of at least 2^-48) proves the quotient reaches thr, and as far below
+// proves it rounds below thr; only the narrow band in between takes the IEEE
+// division.  Non-negative doubles order like their bit patterns, so the band
+// and range tests are integer compares: one FP64 multiply per candidate.
 __device__ __forceinline__ bool is_conflict(double dot, double sj, double si, double thr_si, double thr)
 {
-    double a = fabs(dot);
-    double t = thr_si * sj;
-    if (t > 1e-280 && t < 1e280 && a < 1e300) {
-        long long ab = __double_as_longlong(a);
-        long long hi = __double_as_longlong(t * (1.0 + 0x1p-48));
-        long long lo = __double_as_longlong(t * (1.0 - 0x1p-48));
-        if (ab > hi) return true;
-        if (ab < lo) return false;
+    const long long kTmin = __double_as_longlong(1e-280), kTmax = __double_as_longlong(1e280);
+    const long long kAmax = __double_as_longlong(1e300);
+    long long ab = __double_as_longlong(dot) & 0x7fffffffffffffffLL;
+    long long tb = __double_as_longlong(thr_si * sj);
+    if (tb > kTmin && tb < kTmax && ab < kAmax) {
+        if (ab > tb + 32) return true;
+        if (ab < tb - 32) return false;
     }
     return fabs(__ddiv_rn(dot, __dmul_rn(sj, si))) >= thr;
+}
+
+// x == 0.0 for a row norm (never negative), by its bits
+__device__ __forceinline__ bool zero_norm(double x)
+{
+    return (__double_as_longlong(x) << 1) == 0;
 }
 
 // Modes: kPairConflicts lists the earlier conflicting rows (|cos| >= thr);
@@ -302,7 +308,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_conflicts(PairParams p)
                     int64_t q = sq0[wl][lo] + (t - spre[wl][lo]);
                     j = p.crow[q];
                     double w = p.cval[q];
-                    if (p.nsq[j] == 0.0) valid = false;
+                    if (zero_norm(p.nsq[j])) valid = false;
                     else prod = __dmul_rn(sa[wl][lo], w);
                 }
                 unsigned peers = __match_any_sync(0xffffffffu, valid ? j : -1 - lane);
