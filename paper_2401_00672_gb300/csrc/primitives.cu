@@ -493,6 +493,63 @@ __global__ void column_scatter(int64_t nrows, const int64_t* __restrict__ rp, co
     }
 }
 
+// Structurally symmetric square pattern: column c lists the same rows as row c
+// lists columns, so entry e = (i, c) sits at CSC slot rp[c] + (rank of i in
+// row c).  One binary search per entry (kSymBatch of a row at a time); a
+// missing partner sets *asym and the caller falls back to the general path.
+constexpr int kSymBatch = 4;
+
+__global__ void symmetric_slots(int64_t n, int64_t stride, const int64_t* __restrict__ rp,
+                                const int32_t* __restrict__ ci, uint32_t* __restrict__ tsrc, int* asym)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k * stride < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = k * stride;
+        int64_t e1 = rp[i + 1];
+        for (int64_t e0 = rp[i]; e0 < e1; e0 += kSymBatch) {
+            if (*(volatile int*)asym) return;  // already known not to be symmetric
+            int64_t lo[kSymBatch], hi[kSymBatch];
+#pragma unroll
+            for (int t = 0; t < kSymBatch; ++t) {
+                lo[t] = 0;
+                hi[t] = 0;
+                if (e0 + t < e1) {
+                    int32_t c = ci[e0 + t];
+                    lo[t] = rp[c];
+                    hi[t] = rp[c + 1];
+                }
+            }
+            // first position in [lo, hi) whose column is >= i
+            bool more = true;
+            while (more) {
+                more = false;
+#pragma unroll
+                for (int t = 0; t < kSymBatch; ++t)
+                    if (lo[t] < hi[t]) {
+                        int64_t mid = (lo[t] + hi[t]) >> 1;
+                        if ((int64_t)ci[mid] < i) lo[t] = mid + 1;
+                        else hi[t] = mid;
+                        more = true;
+                    }
+            }
+#pragma unroll
+            for (int t = 0; t < kSymBatch; ++t)
+                if (e0 + t < e1) {
+                    int32_t c = ci[e0 + t];
+                    int64_t q = lo[t];
+                    if (q < rp[c + 1] && (int64_t)ci[q] == i) tsrc[q] = (uint32_t)(e0 + t);
+                    else *asym = 1;
+                }
+        }
+    }
+}
+
+__global__ void copy_cols_u32(const int32_t* ci, int64_t nnz, uint32_t* out)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = (uint32_t)ci[e];
+}
+
 __global__ void widen_counts(const unsigned* cnt, int64_t n, int64_t* out)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -509,6 +566,26 @@ void transpose_pattern(int64_t nrows, int64_t ncols, const int64_t* rp, const in
     cptr.alloc(ncols + 1, st);
     trow.alloc(std::max<int64_t>(nnz, 1), st);
     tsrc.alloc(std::max<int64_t>(nnz, 1), st);
+    if (nrows == ncols && nnz > 0) {
+        // structurally symmetric patterns (the common case for square systems)
+        // need no counting or sorting: the transpose has the pattern itself
+        DBuf<int> asym(1, st);
+        OBK_CUDA(cudaMemsetAsync(asym.p, 0, sizeof(int), st));
+        // a sample of about 8K rows first: most asymmetric patterns fail it
+        int64_t stride = std::max<int64_t>(1, nrows / 8192);
+        symmetric_slots<<<grid(ceil_div(nrows, stride)), kT, 0, st>>>(nrows, stride, rp, ci, tsrc.p, asym.p);
+        OBK_CHECK_LAUNCH();
+        if (stride > 1 && read_scalar(asym.p, st) == 0) {
+            symmetric_slots<<<grid(nrows), kT, 0, st>>>(nrows, 1, rp, ci, tsrc.p, asym.p);
+            OBK_CHECK_LAUNCH();
+        }
+        if (read_scalar(asym.p, st) == 0) {
+            OBK_CUDA(cudaMemcpyAsync(cptr.p, rp, (nrows + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+            copy_cols_u32<<<grid(nnz), kT, 0, st>>>(ci, nnz, trow.p);
+            OBK_CHECK_LAUNCH();
+            return;
+        }
+    }
     DBuf<unsigned> cnt(std::max<int64_t>(ncols, 1), st);
     DBuf<int64_t> wide(std::max<int64_t>(ncols, 1), st);
     OBK_CUDA(cudaMemsetAsync(cnt.p, 0, std::max<int64_t>(ncols, 1) * sizeof(unsigned), st));
