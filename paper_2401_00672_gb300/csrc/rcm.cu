@@ -40,6 +40,9 @@ constexpr int kBlock = 256;
 constexpr int kCoopBlock = 512;      // cooperative kernels: 512 threads,
 constexpr int kCoopBlocksPerSm = 2;  // two blocks per SM
 constexpr int32_t kUnvisited = -1;
+// level count of the first search from which the overlapped Cuthill-McKee pass
+// starts from the first candidates
+constexpr int32_t kEarlyPassLevels = 32;
 
 // ---- symmetric graph: pattern(A + A^T) minus self loops -----------------------
 
@@ -425,6 +428,22 @@ __global__ void gl_compare(int64_t C, int32_t* roots, const int32_t* label, cons
             active[c] = 0;
         }
     }
+}
+
+// roots_cm[c] = the root of component c if its candidate replaces it
+__global__ void spec_roots(int64_t C, const int32_t* roots, const int32_t* cand, const int32_t* active,
+                           int32_t* roots_cm)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+         c += (int64_t)gridDim.x * blockDim.x)
+        roots_cm[c] = active[c] ? cand[c] : roots[c];
+}
+
+__global__ void roots_differ(int64_t C, const int32_t* a, const int32_t* b, int* differ)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+         c += (int64_t)gridDim.x * blockDim.x)
+        if (a[c] != b[c]) *differ = 1;
 }
 
 __global__ void gather_active_sources(int64_t C, const int32_t* which, const int32_t* active, int32_t* src,
@@ -992,18 +1011,36 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
     gl_record_root<<<grid_for(C), kBlock, 0, st>>>(C, roots.p, label.p, ecc.p, cand_r.p, by_rank.p,
                                                     ecc_root.p, cand.p, active.p);
     OBK_CHECK_LAUNCH();
-    // Cuthill-McKee from the current roots overlaps the search's last BFS: once
-    // a round has moved the roots, the next round's BFS (which usually only
-    // confirms them) runs beside a Cuthill-McKee pass from them on a second
-    // stream, each on half the grid; if the roots stay, that pass is the result.
-    DBuf<unsigned long long> claim(N, st), prio(N, st);
-    DBuf<int64_t> ccnt(N, st), nl(2, st), ntot(2, st);
-    DBuf<int32_t> qcm(N, st), roots_cm(C, st);
-    DBuf<unsigned> bar_cm(kBarrierWords, st);
+    // Cuthill-McKee overlaps the search: a pass from the roots a round would
+    // end with runs on a second stream beside the search's BFS (each on half
+    // the grid); if the search ends with exactly those roots, the pass is the
+    // result.  On long level structures (many levels) the first candidates
+    // usually become the roots and stay, so the first round starts a pass from
+    // them and it overlaps two BFS; otherwise a pass starts from the current
+    // roots once a round has moved them (the next BFS usually confirms them).
+    // buffers of one Cuthill-McKee pass
+    struct CmBufs {
+        DBuf<unsigned long long> claim, prio, agg;
+        DBuf<int64_t> cnt, nl, ntot;
+        DBuf<int32_t> q, roots;
+        DBuf<unsigned> bar;
+        void alloc(int64_t n, int64_t c, int agg_n, cudaStream_t s)
+        {
+            claim.alloc(n, s);
+            prio.alloc(n, s);
+            agg.alloc(agg_n, s);
+            cnt.alloc(n, s);
+            nl.alloc(2, s);
+            ntot.alloc(2, s);
+            q.alloc(n, s);
+            roots.alloc(c, s);
+            bar.alloc(kBarrierWords, s);
+        }
+    };
     int half_grid = std::max(1, bfs_grid / 2);
     int cm_grid_full = coop_grid((const void*)cm_levels, kCoopBlock, 0, want);
     int cm_grid_half = coop_grid((const void*)cm_levels, kCoopBlock, 0, std::max<int64_t>(1, want / 2));
-    DBuf<unsigned long long> agg(cm_grid_full, st);
+    CmBufs pass;  // the overlapped pass (second stream)
     cudaStream_t st2 = aux_stream();
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     OBK_CUDA(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
@@ -1019,17 +1056,45 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
             cudaEventDestroy(b);
         }
     } evg{ev_in, ev_out, false};
-    // Cuthill-McKee from roots_cm into qcm on stream s with the given grid
-    auto launch_cm = [&](cudaStream_t s, int grid) {
-        OBK_CUDA(cudaMemsetAsync(claim.p, 0xff, N * sizeof(unsigned long long), s));
-        OBK_CUDA(cudaMemsetAsync(bar_cm.p, 0, kBarrierWords * sizeof(unsigned), s));
-        OBK_CUDA(cudaMemsetAsync(agg.p, 0, grid * sizeof(unsigned long long), s));
-        CmParams cp{N, gp.p, adj_r, roots_cm.p, C, claim.p, prio.p, qcm.p, ccnt.p, agg.p, ntot.p, nl.p,
-                    GridBarrier{bar_cm.p, d_err, spin_limit}};
+    // Cuthill-McKee from b.roots into b.q on stream s with the given grid
+    auto launch_cm = [&](CmBufs& b, cudaStream_t s, int grid) {
+        OBK_CUDA(cudaMemsetAsync(b.claim.p, 0xff, N * sizeof(unsigned long long), s));
+        OBK_CUDA(cudaMemsetAsync(b.bar.p, 0, kBarrierWords * sizeof(unsigned), s));
+        OBK_CUDA(cudaMemsetAsync(b.agg.p, 0, grid * sizeof(unsigned long long), s));
+        CmParams cp{N, gp.p, adj_r, b.roots.p, C, b.claim.p, b.prio.p, b.q.p, b.cnt.p, b.agg.p, b.ntot.p, b.nl.p,
+                    GridBarrier{b.bar.p, d_err, spin_limit}};
         void* args[] = {&cp};
         OBK_COOP_LAUNCH(cm_levels, grid, kCoopBlock, args, s);
     };
-    bool moved = false, cm_done = false;
+    DBuf<int> differ(1, st);
+    // true when the roots differ from those of the overlapped pass
+    auto roots_moved_from_pass = [&]() -> bool {
+        OBK_CUDA(cudaMemsetAsync(differ.p, 0, sizeof(int), st));
+        roots_differ<<<grid_for(C), kBlock, 0, st>>>(C, roots.p, pass.roots.p, differ.p);
+        OBK_CHECK_LAUNCH();
+        return read_scalar(differ.p, st) != 0;
+    };
+    auto start_pass = [&]() {
+        OBK_CUDA(cudaEventRecord(ev_in, st));
+        OBK_CUDA(cudaStreamWaitEvent(st2, ev_in, 0));
+        evg.pending = true;
+        launch_cm(pass, st2, cm_grid_half);
+        OBK_CUDA(cudaEventRecord(ev_out, st2));
+    };
+    auto end_pass = [&]() {
+        OBK_CUDA(cudaEventSynchronize(ev_out));
+        evg.pending = false;
+        OBK_CUDA(cudaStreamWaitEvent(st, ev_out, 0));  // later stream work sees the pass's output
+    };
+    auto pass_running = [&]() {
+        if (!evg.pending) return false;
+        cudaError_t q = cudaEventQuery(ev_out);
+        if (q == cudaErrorNotReady) return true;
+        OBK_CUDA(q);
+        return false;
+    };
+    const bool long_levels = bfs_grid > 1 && read_scalar(nlev.p, st) >= kEarlyPassLevels;
+    bool moved = false, cm_done = false, live = false;  // live: the pass may still be the result
     int gl_rounds = 0;
     for (;;) {
         ++gl_rounds;
@@ -1038,45 +1103,50 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
         OBK_CHECK_LAUNCH();
         int64_t ns = read_scalar(nsrc.p, st);
         if (ns == 0) break;
-        const bool spec = moved && bfs_grid > 1;
-        if (spec) {
-            OBK_CUDA(cudaMemcpyAsync(roots_cm.p, roots.p, C * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-            OBK_CUDA(cudaEventRecord(ev_in, st));
-            OBK_CUDA(cudaStreamWaitEvent(st2, ev_in, 0));
-            evg.pending = true;
-            launch_cm(st2, cm_grid_half);
-            OBK_CUDA(cudaEventRecord(ev_out, st2));
+        if (!live && bfs_grid > 1 && (moved || (gl_rounds == 1 && long_levels))) {
+            if (!pass.q.p) pass.alloc(N, C, cm_grid_full, st);
+            if (evg.pending) end_pass();  // a pass that is no longer the result: let it end first
+            if (moved) {
+                OBK_CUDA(cudaMemcpyAsync(pass.roots.p, roots.p, C * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+            } else {  // the roots if every active component moves to its candidate
+                spec_roots<<<grid_for(C), kBlock, 0, st>>>(C, roots.p, cand.p, active.p, pass.roots.p);
+                OBK_CHECK_LAUNCH();
+            }
+            start_pass();
+            live = true;
         }
-        run_bfs(src.p, ns, spec ? half_grid : bfs_grid);
+        run_bfs(src.p, ns, pass_running() ? half_grid : bfs_grid);
         OBK_CUDA(cudaMemsetAsync(any.p, 0, sizeof(int), st));
         gl_compare<<<grid_for(C), kBlock, 0, st>>>(C, roots.p, label.p, ecc.p, cand_r.p, by_rank.p,
                                                     ecc_root.p, cand.p, active.p, any.p);
         OBK_CHECK_LAUNCH();
         int changed = read_scalar(any.p, st);
-        if (spec) {
-            OBK_CUDA(cudaEventSynchronize(ev_out));
-            evg.pending = false;
-            OBK_CUDA(cudaStreamWaitEvent(st, ev_out, 0));  // later stream work sees the pass's output
-        }
-        if (changed == 0) {
-            cm_done = spec;
-            break;
-        }
+        if (changed == 0) break;
         moved = true;
+        if (live && roots_moved_from_pass()) live = false;  // that pass cannot be the result any more
+    }
+    if (live && !roots_moved_from_pass()) {
+        end_pass();
+        cm_done = true;
     }
     dist.release(); ecc.release(); cand_r.release(); ecc_root.release(); cand.release();
     active.release(); src.release();
     mark();
 
     // 6. Cuthill-McKee levels into one queue (unless the overlapped pass already
-    //    ran from the final roots), then the per-component order
+    //    ran from the final roots), then the per-component order.  A pass
+    //    still running on the second stream keeps half the grid.
+    CmBufs main_pass;
+    CmBufs* res = &pass;
     if (!cm_done) {
-        OBK_CUDA(cudaMemcpyAsync(roots_cm.p, roots.p, C * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-        launch_cm(st, cm_grid_full);
+        main_pass.alloc(N, C, cm_grid_full, st);
+        OBK_CUDA(cudaMemcpyAsync(main_pass.roots.p, roots.p, C * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        launch_cm(main_pass, st, pass_running() ? cm_grid_half : cm_grid_full);
+        res = &main_pass;
     }
-    int32_t* Q = qcm.p;
+    int32_t* Q = res->q.p;
     if (read_scalar(d_err, st) != 0) throw Error{-4, "bounded wait or bound check failed in Cuthill-McKee levels"};
-    if (read_scalar(nl.p + 1, st) != N) throw Error{-5, "internal error: Cuthill-McKee order does not cover every vertex"};
+    if (read_scalar(res->nl.p + 1, st) != N) throw Error{-5, "internal error: Cuthill-McKee order does not cover every vertex"};
     const int32_t* cm = Q;
     DBuf<uint64_t> ck;
     DBuf<uint32_t> cv;
@@ -1092,7 +1162,7 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
     OBK_CHECK_LAUNCH();
     if (stats) {
         stats->components = C;
-        stats->levels = read_scalar(nl.p, st);
+        stats->levels = read_scalar(res->nl.p, st);
         stats->gl_rounds = gl_rounds;
         stats->graph_edges = M;
     }

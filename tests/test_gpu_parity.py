@@ -129,6 +129,49 @@ def _many_groups():
     return synth.System(A, xs, A.matvec(xs), "many_groups")
 
 
+def _grid_coo(H, W, rng, offset=0):
+    # 5-point pattern on an H x W grid, row-major numbering, off-diagonals N(0,1)
+    idx = np.arange(H * W).reshape(H, W)
+    pairs = [(idx[:, :-1].ravel(), idx[:, 1:].ravel()), (idx[:-1, :].ravel(), idx[1:, :].ravel())]
+    r = np.concatenate([a for a, b in pairs] + [b for a, b in pairs]) + offset
+    c = np.concatenate([b for a, b in pairs] + [a for a, b in pairs]) + offset
+    return r, c, rng.standard_normal(len(r))
+
+
+def _dominant(N, r, c, v, rng, name):
+    off = np.bincount(r, weights=np.abs(v), minlength=N)
+    r = np.concatenate([r, np.arange(N)])
+    c = np.concatenate([c, np.arange(N)])
+    v = np.concatenate([v, 1.0 + off])
+    A = synth.csr_from_coo(N, N, r, c, v)
+    xs = rng.standard_normal(N)
+    return synth.System(A, xs, A.matvec(xs), name)
+
+
+def _grid2d():
+    # 90 x 90 grid: the search starts at a corner, its candidate (the opposite
+    # corner) is no farther, so the root stays; 179 BFS levels
+    rng = np.random.default_rng(31)
+    r, c, v = _grid_coo(90, 90, rng)
+    return _dominant(90 * 90, r, c, v, rng, "grid2d")
+
+
+def _knn_and_grid():
+    # two components with long level structures: a kNN graph whose root moves
+    # to its first candidate and a 70 x 70 grid whose root stays
+    rng = np.random.default_rng(32)
+    k = synth.knn_dominant(20000, 12, seed=33).A
+    kr = np.repeat(np.arange(k.m), np.diff(k.row_ptr)).astype(np.int64)
+    kc = k.col_idx.astype(np.int64)
+    off = kr != kc
+    gr, gc, gv = _grid_coo(70, 70, rng, offset=k.m)
+    N = k.m + 70 * 70
+    r = np.concatenate([kr[off], gr])
+    c = np.concatenate([kc[off], gc])
+    v = np.concatenate([k.val[off], gv])
+    return _dominant(N, r, c, v, rng, "knn_and_grid")
+
+
 CASES = {
     "random_dominant_2000": lambda: synth.random_dominant(2000, 7, seed=1000),
     "knn_30000": lambda: synth.knn_dominant(30000, 12, seed=1001),
@@ -140,6 +183,8 @@ CASES = {
     "tiny_3x3": lambda: synth.random_dominant(3, 1, seed=5),
     "hubs": _hubs,
     "many_groups": _many_groups,
+    "grid2d_90x90": _grid2d,
+    "knn_and_grid": _knn_and_grid,
 }
 
 _cache = {}
