@@ -475,10 +475,12 @@ __global__ void gather_active_sources(int64_t C, const int32_t* which, const int
 //
 // Per level: (A) each frontier vertex u counts its children {w : claim[w] ==
 // P(u)} -- all its neighbours lie in levels L-1..L+1, whose claims no longer
-// change -- gives each child its priority and lets it claim its own
-// neighbours at once; (B) a look-back over the per-block child totals of
-// this level (tagged with the level) gives the block's offset, and the
-// children are written to Q in order; then one grid barrier.
+// change; (B) a look-back over the per-block child totals of this level
+// (tagged with the level) gives the block's offset, and the children are
+// written to Q in order with their priorities beside them; (C) every child
+// records its adjacency range at its queue position and claims its
+// neighbours; then one grid barrier.  A frontier vertex is read as (priority,
+// adjacency range) at its queue position, one round of loads.
 
 struct CmParams {
     int64_t N;
@@ -487,7 +489,9 @@ struct CmParams {
     const int32_t* roots;            // C roots in component order
     int64_t C;
     unsigned long long* claim;       // N, all ones
-    unsigned long long* prio;        // N
+    unsigned long long* qp;          // N: priority of the vertex at each queue position
+    int64_t* qb;                     // N: its first adjacency position
+    int32_t* qd;                     // N: its degree
     int32_t* Q;                      // N
     int64_t* cnt;                    // N: per frontier vertex, block-local offset of its children
     unsigned long long* agg;         // gridDim: ((level + 1) << 40) | block total, zeroed
@@ -531,9 +535,13 @@ __device__ __forceinline__ void claim_group(const CmParams& p, int64_t b, int64_
 
 constexpr int kStage = 8;  // children of one frontier vertex kept in shared memory
 
+constexpr int kChildStage = 512;  // children of a block per level kept in shared memory
+
 struct CmShared {
     int32_t sj[kStage][kCoopBlock];  // adjacency offset of a staged child
     int32_t sw[kStage][kCoopBlock];  // the child
+    int32_t cw[kChildStage];         // the block's first children of this level
+    unsigned long long cp[kChildStage];  // and their priorities
     int32_t scnt[kCoopBlock];        // children per frontier vertex of the chunk
     int64_t soff[kCoopBlock];        // their block-local offsets
     int32_t heavy[kHeavyBuf];
@@ -571,19 +579,31 @@ __device__ __forceinline__ void cm_count(const CmParams& p, CmShared& sh, int64_
     }
 }
 
-__device__ __forceinline__ void cm_place(const CmParams& p, int64_t pos, int32_t w, int64_t k, int64_t idx)
+// the idx-th child w of the vertex at queue position k goes to position pos;
+// the block's first kChildStage children are also kept in shared memory
+__device__ __forceinline__ void cm_place(const CmParams& p, CmShared& sh, int64_t base_pos, int64_t pos, int32_t w,
+                                         int64_t k, int64_t idx)
 {
-    if (pos < p.N) p.Q[pos] = w;
-    else atomicCAS(p.gb.err, 0, (int)kDevOverflow);
-    p.prio[w] = ((unsigned long long)(k + 1) << 32) | (unsigned long long)idx;
+    unsigned long long pw = ((unsigned long long)(k + 1) << 32) | (unsigned long long)idx;
+    if (pos < p.N) {
+        p.Q[pos] = w;
+        p.qp[pos] = pw;
+    } else {
+        atomicCAS(p.gb.err, 0, (int)kDevOverflow);
+    }
+    int64_t l = pos - base_pos;
+    if (l >= 0 && l < kChildStage) {
+        sh.cw[l] = w;
+        sh.cp[l] = pw;
+    }
 }
 
 // Children of frontier vertex k in rank (adjacency) order, found again from
 // the claims by one thread.
-__device__ void cm_rescan_thread(const CmParams& p, int64_t k, int32_t u, int64_t o)
+__device__ void cm_rescan_thread(const CmParams& p, CmShared& sh, int64_t base_pos, int64_t k, int64_t o)
 {
-    unsigned long long pu = p.prio[u];
-    int64_t b = p.gp[u], e = p.gp[u + 1];
+    unsigned long long pu = p.qp[k];
+    int64_t b = p.qb[k], e = b + p.qd[k];
     int64_t i = 0;
     for (int64_t q0 = b; q0 < e; q0 += 2 * kNbRound) {
         int32_t w[2 * kNbRound];
@@ -595,18 +615,18 @@ __device__ void cm_rescan_thread(const CmParams& p, int64_t k, int32_t u, int64_
 #pragma unroll
         for (int t = 0; t < 2 * kNbRound; ++t)
             if (w[t] >= 0 && c[t] == pu) {
-                cm_place(p, o + i, w[t], k, i);
+                cm_place(p, sh, base_pos, o + i, w[t], k, i);
                 ++i;
             }
     }
 }
 
 // The same by a whole warp (ballots keep the order).
-__device__ void cm_rescan_warp(const CmParams& p, int64_t k, int32_t u, int64_t o, int lane)
+__device__ void cm_rescan_warp(const CmParams& p, CmShared& sh, int64_t base_pos, int64_t k, int64_t o, int lane)
 {
     unsigned lt = (1u << lane) - 1u;
-    unsigned long long pu = p.prio[u];
-    int64_t b = p.gp[u], e = p.gp[u + 1];
+    unsigned long long pu = p.qp[k];
+    int64_t b = p.qb[k], e = b + p.qd[k];
     int64_t i = 0;
     for (int64_t base = b; base < e; base += 32) {
         int64_t q = base + lane;
@@ -617,7 +637,7 @@ __device__ void cm_rescan_warp(const CmParams& p, int64_t k, int32_t u, int64_t 
             child = ld_relaxed_u64(p.claim + w) == pu;
         }
         unsigned m = __ballot_sync(0xffffffffu, child);
-        if (child) cm_place(p, o + i + __popc(m & lt), w, k, i + __popc(m & lt));
+        if (child) cm_place(p, sh, base_pos, o + i + __popc(m & lt), w, k, i + __popc(m & lt));
         i += __popc(m);
     }
 }
@@ -641,7 +661,9 @@ __global__ void __launch_bounds__(kCoopBlock) cm_levels(CmParams p)
     for (int64_t c = tid; c < p.C; c += nth) {
         int32_t r = p.roots[c];
         p.Q[c] = r;
-        p.prio[r] = (unsigned long long)c;
+        p.qp[c] = (unsigned long long)c;
+        p.qb[c] = p.gp[r];
+        p.qd[c] = (int32_t)(p.gp[r + 1] - p.gp[r]);
         p.claim[r] = (unsigned long long)c;
     }
     if (!grid_sync(p.gb)) return;
@@ -671,9 +693,8 @@ __global__ void __launch_bounds__(kCoopBlock) cm_levels(CmParams p)
             const int ipp = blockDim.x / G;
             for (int64_t k = c0 + threadIdx.x / G; k < c1; k += ipp) {
                 int kl = (int)(k - c0);
-                int32_t u = p.Q[k];
-                unsigned long long pu = p.prio[u];
-                int64_t b = p.gp[u], e = p.gp[u + 1];
+                unsigned long long pu = p.qp[k];
+                int64_t b = p.qb[k], e = b + p.qd[k];
                 if (heavy_for(e - b, G) && kl < kHeavyBuf) {
                     if (lg == 0) sh.heavy[atomicAdd(&sh.s_nheavy, 1)] = kl;
                     continue;
@@ -685,8 +706,7 @@ __global__ void __launch_bounds__(kCoopBlock) cm_levels(CmParams p)
         for (int h = wid; h < sh.s_nheavy; h += wpb) {
             int kl = sh.heavy[h];
             int64_t k = c0 + kl;
-            int32_t u = p.Q[k];
-            cm_count(p, sh, p.gp[u], p.gp[u + 1], 32, lane, p.prio[u], k, kl, staged);
+            cm_count(p, sh, p.qb[k], p.qb[k] + p.qd[k], 32, lane, p.qp[k], k, kl, staged);
         }
         __syncthreads();
         // block-local exclusive scan of the child counts
@@ -781,26 +801,26 @@ __global__ void __launch_bounds__(kCoopBlock) cm_levels(CmParams p)
                     for (int i = r & 1; i + 1 < kStage; i += 2) cswap(j[i], w[i], j[i + 1], w[i + 1]);
 #pragma unroll
                 for (int i = 0; i < kStage; ++i)
-                    if (i < n) cm_place(p, o + i, w[i], k, i);
+                    if (i < n) cm_place(p, sh, base_pos, o + i, w[i], k, i);
                 continue;
             }
-            int32_t u = p.Q[k];
             int64_t o = base_pos + (staged ? sh.soff[kl] : p.cnt[k]);
-            if (p.gp[u + 1] - p.gp[u] > kHeavyDeg && kl < kHeavyBuf) {
+            if (p.qd[k] > kHeavyDeg && kl < kHeavyBuf) {
                 sh.heavy[atomicAdd(&sh.s_nheavy, 1)] = kl;
                 continue;
             }
-            cm_rescan_thread(p, k, u, o);
+            cm_rescan_thread(p, sh, base_pos, k, o);
         }
         __syncthreads();
         for (int h = wid; h < sh.s_nheavy; h += wpb) {
             int kl = sh.heavy[h];
             int64_t k = c0 + kl;
             int64_t o = base_pos + (staged ? sh.soff[kl] : p.cnt[k]);
-            cm_rescan_warp(p, k, p.Q[k], o, lane);
+            cm_rescan_warp(p, sh, base_pos, k, o, lane);
         }
         __syncthreads();
-        // (C) the new vertices of this block claim their neighbours
+        // (C) the new vertices of this block record their adjacency range at
+        //     their queue position and claim their neighbours
         if (threadIdx.x == 0) sh.s_nheavy = 0;
         __syncthreads();
         {
@@ -808,19 +828,32 @@ __global__ void __launch_bounds__(kCoopBlock) cm_levels(CmParams p)
             const int lg = threadIdx.x & (G - 1);
             const int ipp = blockDim.x / G;
             for (int64_t j = threadIdx.x / G; j < carry; j += ipp) {
-                int32_t w = p.Q[base_pos + j];
+                int32_t w;
+                unsigned long long pw;
+                if (j < kChildStage) {
+                    w = sh.cw[j];
+                    pw = sh.cp[j];
+                } else {
+                    w = p.Q[base_pos + j];
+                    pw = p.qp[base_pos + j];
+                }
                 int64_t b = p.gp[w], e = p.gp[w + 1];
+                if (lg == 0) {
+                    p.qb[base_pos + j] = b;
+                    p.qd[base_pos + j] = (int32_t)(e - b);
+                }
                 if (heavy_for(e - b, G) && j < kHeavyBuf) {
                     if (lg == 0) sh.heavy[atomicAdd(&sh.s_nheavy, 1)] = (int32_t)j;
                     continue;
                 }
-                claim_group(p, b, e, G, lg, p.prio[w]);
+                claim_group(p, b, e, G, lg, pw);
             }
         }
         __syncthreads();
         for (int h = wid; h < sh.s_nheavy; h += wpb) {
-            int32_t w = p.Q[base_pos + sh.heavy[h]];
-            claim_group(p, p.gp[w], p.gp[w + 1], 32, lane, p.prio[w]);
+            int64_t q = base_pos + sh.heavy[h];
+            int64_t b = p.qb[q];
+            claim_group(p, b, b + p.qd[q], 32, lane, p.qp[q]);
         }
         if (!grid_sync(p.gb)) return;
         int64_t nf = *(volatile int64_t*)(p.ntot + (L & 1));
@@ -1020,14 +1053,16 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
     // roots once a round has moved them (the next BFS usually confirms them).
     // buffers of one Cuthill-McKee pass
     struct CmBufs {
-        DBuf<unsigned long long> claim, prio, agg;
-        DBuf<int64_t> cnt, nl, ntot;
-        DBuf<int32_t> q, roots;
+        DBuf<unsigned long long> claim, qp, agg;
+        DBuf<int64_t> cnt, nl, ntot, qb;
+        DBuf<int32_t> q, qd, roots;
         DBuf<unsigned> bar;
         void alloc(int64_t n, int64_t c, int agg_n, cudaStream_t s)
         {
             claim.alloc(n, s);
-            prio.alloc(n, s);
+            qp.alloc(n, s);
+            qb.alloc(n, s);
+            qd.alloc(n, s);
             agg.alloc(agg_n, s);
             cnt.alloc(n, s);
             nl.alloc(2, s);
@@ -1061,8 +1096,8 @@ void rcm_reorder(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, i
         OBK_CUDA(cudaMemsetAsync(b.claim.p, 0xff, N * sizeof(unsigned long long), s));
         OBK_CUDA(cudaMemsetAsync(b.bar.p, 0, kBarrierWords * sizeof(unsigned), s));
         OBK_CUDA(cudaMemsetAsync(b.agg.p, 0, grid * sizeof(unsigned long long), s));
-        CmParams cp{N, gp.p, adj_r, b.roots.p, C, b.claim.p, b.prio.p, b.q.p, b.cnt.p, b.agg.p, b.ntot.p, b.nl.p,
-                    GridBarrier{b.bar.p, d_err, spin_limit}};
+        CmParams cp{N, gp.p, adj_r, b.roots.p, C, b.claim.p, b.qp.p, b.qb.p, b.qd.p, b.q.p, b.cnt.p, b.agg.p,
+                    b.ntot.p, b.nl.p, GridBarrier{b.bar.p, d_err, spin_limit}};
         void* args[] = {&cp};
         OBK_COOP_LAUNCH(cm_levels, grid, kCoopBlock, args, s);
     };
