@@ -191,7 +191,10 @@ OBK_API obk_status obk_solve_blocks(obk_handle* h, obk_block_opts* bo, const dou
  * units of 2^-32, so the total is exact whatever the order of summation),
  * zn = (N^2 - nonzero_entries) / N^2 (Definition 1, the orthogonality
  * proportion) and nn = abs_cos_sum 2^-32 / N^2 (Definition 2, the
- * non-orthogonality severity).  The groups fields describe the built groups. */
+ * non-orthogonality severity).  The groups fields describe the built groups;
+ * conflicts is the number of row pairs with |cos| >= thr and color_rounds the
+ * number of in-place rounds the first-fit grouping took to reach its fixed
+ * point (the last round changes nothing). */
 typedef struct {
     int64_t N;
     int64_t nonzero_entries;
@@ -201,7 +204,9 @@ typedef struct {
     int64_t groups;
     int64_t min_group_rows;
     int64_t max_group_rows;
-    int64_t reserved[4];
+    int64_t conflicts;
+    int64_t color_rounds;
+    int64_t reserved[2];
 } obk_gstats;
 
 /* Computes the statistics above for a prepared system (recomputes the pair

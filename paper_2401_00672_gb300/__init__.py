@@ -55,7 +55,7 @@ class _GStats(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("nonzero_entries", ctypes.c_int64), ("abs_cos_sum", ctypes.c_uint64),
                 ("zn", ctypes.c_double), ("nn", ctypes.c_double), ("groups", ctypes.c_int64),
                 ("min_group_rows", ctypes.c_int64), ("max_group_rows", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 4)]
+                ("conflicts", ctypes.c_int64), ("color_rounds", ctypes.c_int64), ("reserved", ctypes.c_int64 * 2)]
 
 
 class BlockOpts(ctypes.Structure):
@@ -228,7 +228,8 @@ class Handle:
         return rc, ko, _info(info), bo
 
     def grouping_stats(self) -> dict:
-        """obk_grouping_stats: Definitions 1-2 (zn, nn) of the row cosine table and group sizes."""
+        """obk_grouping_stats: Definitions 1-2 (zn, nn) of the row cosine table, group sizes,
+        conflict count and grouping rounds."""
         g = _GStats()
         _check(lib.obk_grouping_stats(self._h, ctypes.byref(g)), "obk_grouping_stats")
         return {k: getattr(g, k) for k, _ in _GStats._fields_ if k != "reserved"}

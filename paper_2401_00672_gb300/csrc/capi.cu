@@ -627,6 +627,8 @@ obk_status obk_grouping_stats(obk_handle* h, obk_gstats* out)
     r.zn = num > 0 ? (num - (double)nz) / num : 0.0;
     r.nn = num > 0 ? (double)sum * 0x1p-32 / num : 0.0;
     r.groups = h->L.G;
+    r.conflicts = h->L.n_conflicts;
+    r.color_rounds = h->L.color_rounds;
     r.min_group_rows = h->L.G ? INT64_MAX : 0;
     for (int64_t g = 0; g < h->L.G; ++g) {
         int64_t c = h->L.h_gptr[g + 1] - h->L.h_gptr[g];

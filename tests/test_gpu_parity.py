@@ -542,6 +542,11 @@ def test_cosine_stats_bit_exact(obk, name):
     assert g["nonzero_entries"] == nz and g["abs_cos_sum"] == tot
     assert g["zn"] == pytest.approx(zn, rel=1e-15) and g["nn"] == pytest.approx(nn, rel=1e-15)
     assert g["groups"] == su.G
+    # conflicting pairs as the oracle's grouping counts them; the fixed point
+    # needs at least one round (and a last one that changes nothing)
+    _, _, n_conf = oracle.group_build(N, rp, ci, v, nsq, 0.1)
+    assert g["conflicts"] == n_conf
+    assert g["color_rounds"] >= (2 if n_conf else 1)
 
 
 def test_underdetermined_min_norm(obk):
