@@ -578,21 +578,48 @@ __global__ void seg_lengths(int64_t nseg, const uint32_t* order, const int64_t* 
     GRID_STRIDE(t, nseg) len[t] = seg_ptr[order[t] + 1] - seg_ptr[order[t]];
 }
 
-// copy the entries of each segment to its new place (one thread per segment;
-// segments hold a few entries)
+// copy the entries of each segment to its new place.  A warp takes 32
+// consecutive destination segments (one contiguous destination range) and its
+// lanes walk that range together: coalesced writes, gathered reads.
 template <class T>
 __global__ void seg_move(int64_t nseg, const uint32_t* order, const int64_t* seg_ptr, const int64_t* new_ptr,
                          const int32_t* seg_col, int32_t* new_col, const int32_t* mrow, const T* mval,
                          const float* mval32, int32_t* nrow, T* nval, float* nval32)
 {
-    GRID_STRIDE(t, nseg)
-    {
-        int64_t s = order[t], b = seg_ptr[s], e = seg_ptr[s + 1], d = new_ptr[t];
-        new_col[t] = seg_col[s];
-        for (int64_t q = 0; q < e - b; ++q) {
-            nrow[d + q] = mrow[b + q];
-            nval[d + q] = mval[b + q];
-            if (nval32) nval32[d + q] = mval32[b + q];
+    int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t0 = w * 32; t0 < nseg; t0 += nw * 32) {
+        int64_t t = t0 + lane;
+        int64_t src = 0, d = 0;
+        if (t < nseg) {
+            int64_t s = order[t];
+            src = seg_ptr[s];
+            d = new_ptr[t];
+            new_col[t] = seg_col[s];
+        }
+        int64_t d0 = new_ptr[t0];
+        int64_t d1 = t0 + 32 < nseg ? new_ptr[t0 + 32] : new_ptr[nseg];
+        int nlive = (int)(nseg - t0 < 32 ? nseg - t0 : 32);
+        // entry q of the range belongs to the last segment of the warp whose
+        // destination start is <= q
+        for (int64_t q0 = d0; q0 < d1; q0 += 32) {
+            int64_t q = q0 + lane;
+            int lo = 0;  // branch-free search, the same steps in every lane
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                int cand = lo + step;
+                int64_t dm = __shfl_sync(0xffffffffu, d, cand < nlive ? cand : nlive - 1);
+                if (cand < nlive && dm <= q) lo = cand;
+            }
+            int64_t ds = __shfl_sync(0xffffffffu, d, lo);
+            int64_t ss = __shfl_sync(0xffffffffu, src, lo);
+            if (q < d1) {
+                int64_t from = ss + (q - ds);
+                nrow[q] = mrow[from];
+                nval[q] = mval[from];
+                if (nval32) nval32[q] = mval32[from];
+            }
         }
     }
 }
@@ -610,7 +637,14 @@ __global__ void max_row_len(int64_t n, const int64_t* ptr, unsigned long long* m
         unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
         m = t > m ? t : m;
     }
-    if ((threadIdx.x & 31) == 0 && m) atomicMax(mx, m);
+    __shared__ unsigned long long wmax[kBlock / 32];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long b = 0;
+        for (int w = 0; w < kBlock / 32; ++w) b = wmax[w] > b ? wmax[w] : b;
+        if (b) atomicMax(mx, b);  // one atomic per block
+    }
 }
 
 // histogram of colours; colours below 256 are counted in shared memory first
@@ -678,24 +712,40 @@ __global__ void expand_cols(int64_t N, const int64_t* cptr, int32_t* col_of)
     for (int64_t p = cptr[c]; p < cptr[c + 1]; ++p) col_of[p] = (int32_t)c;
 }
 
-// mirror entries in (group, column, row) order; seg flags mark (group, column) starts
+// mirror entries in (group, column, row) order; seg flags mark (group, column)
+// starts.  A warp takes 32 consecutive entries: each lane's predecessor's
+// (column, group) comes from the lane before it by shuffle.
 __global__ void mirror_fill(int64_t M, const uint32_t* order, const int32_t* crow, const double* cval,
                             const int32_t* col_of, const int32_t* color, const int32_t* gm_of_row,
                             int32_t* mrow, double* mval, float* mval32, int32_t* flag)
 {
-    GRID_STRIDE(q, M)
-    {
-        uint32_t pp = order[q];
-        int32_t i = crow[pp];
-        mrow[q] = gm_of_row[i];
-        mval[q] = cval[pp];
-        if (mval32) mval32[q] = (float)cval[pp];
-        bool start = q == 0;
-        if (!start) {
-            uint32_t pr = order[q - 1];
-            start = col_of[pr] != col_of[pp] || color[crow[pr]] != color[i];
+    int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q0 = w * 32; q0 < M; q0 += nw * 32) {
+        int64_t q = q0 + lane;
+        bool valid = q < M;
+        int32_t c = -1, g = -1;
+        if (valid) {
+            uint32_t pp = order[q];
+            int32_t i = crow[pp];
+            c = col_of[pp];
+            g = color[i];
+            mrow[q] = gm_of_row[i];
+            double a = cval[pp];
+            mval[q] = a;
+            if (mval32) mval32[q] = (float)a;
         }
-        flag[q] = start ? 1 : 0;
+        int32_t pc = __shfl_up_sync(0xffffffffu, c, 1);
+        int32_t pg = __shfl_up_sync(0xffffffffu, g, 1);
+        if (valid) {
+            if (lane == 0 && q > 0) {
+                uint32_t pr = order[q - 1];
+                pc = col_of[pr];
+                pg = color[crow[pr]];
+            }
+            flag[q] = (q == 0 || pc != c || pg != g) ? 1 : 0;
+        }
     }
 }
 
