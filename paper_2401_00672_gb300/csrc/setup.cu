@@ -539,13 +539,18 @@ __global__ void max_color(int64_t N, const int32_t* color, int* gmax)
 // Row order of the sweep layout: by group, then by row length, then by index
 // (stable sort on (group, length) over rows in index order).  Equal lengths
 // inside a warp keep every lane of every FP64 instruction busy.
+// Rows (and column segments) of a group are ordered by length in buckets of
+// 2^kLenBucketShift, then by index: slices of 32 stay nearly free of padding
+// while neighbouring lanes keep nearby indices (and so nearby columns).
+constexpr int kLenBucketShift = 1;
+
 __global__ void color_keys(int64_t N, const int32_t* color, const int64_t* rp, int32_t G, int lbits,
                            uint64_t* keys, uint32_t* vals)
 {
     GRID_STRIDE(i, N)
     {
         uint64_t g = (uint64_t)(color[i] >= 0 ? color[i] : G);
-        uint64_t len = (uint64_t)(rp[i + 1] - rp[i]);
+        uint64_t len = (uint64_t)(rp[i + 1] - rp[i]) >> kLenBucketShift;
         uint64_t lmax = (1ull << lbits) - 1;
         keys[i] = (g << lbits) | (len < lmax ? len : lmax);
         vals[i] = (uint32_t)i;
@@ -566,7 +571,7 @@ __global__ void seg_keys(int64_t nseg, const int64_t* seg_ptr, const int64_t* gs
             if (gseg_ptr[mid] <= t) lo = mid;
             else hi = mid;
         }
-        uint64_t len = (uint64_t)(seg_ptr[t + 1] - seg_ptr[t]);
+        uint64_t len = (uint64_t)(seg_ptr[t + 1] - seg_ptr[t]) >> kLenBucketShift;
         uint64_t lmax = (1ull << lbits) - 1;
         keys[t] = ((uint64_t)lo << lbits) | (len < lmax ? len : lmax);
         vals[t] = (uint32_t)t;
