@@ -604,3 +604,45 @@ def test_block_form_parity(obk, name, k):
     assert st == st_o == 0
     assert abs(info.sweeps - io.sweeps) <= 1
     assert np.linalg.norm(x - x_o) / max(np.linalg.norm(x_o), 1e-300) <= 1e-8
+
+
+def _dense_conflicts(N=2000, hubs=6, per_row=4, seed=61):
+    # every row has entries in per_row of a few shared columns: each row
+    # conflicts with hundreds of earlier rows (whole-warp conflict lists and
+    # more than 64 groups)
+    rng = np.random.default_rng(seed)
+    rows, cols = [], []
+    for i in range(N):
+        c = rng.choice(np.arange(N - hubs, N), per_row, replace=False)
+        c = c[c != i]
+        rows += [i] * len(c)
+        cols += list(c)
+    r = np.array(rows, np.int64)
+    c = np.array(cols, np.int64)
+    v = rng.standard_normal(len(r))
+    off = np.bincount(r, weights=np.abs(v), minlength=N)
+    r = np.concatenate([r, np.arange(N)])
+    c = np.concatenate([c, np.arange(N)])
+    v = np.concatenate([v, 1.0 + off])
+    A = synth.csr_from_coo(N, N, r, c, v)
+    xs = rng.standard_normal(N)
+    return synth.System(A, xs, A.matvec(xs), "dense_conflicts")
+
+
+def test_dense_conflicts_wide_lanes(obk):
+    """Conflict lists of hundreds of rows (the grouping's whole-warp path, more
+    than 64 colours): setup bit-exact and a fixed number of sweeps in parity."""
+    s = _dense_conflicts()
+    A = s.A
+    su = oracle.setup(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1)
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
+        g = h.grouping_stats()
+        assert g["conflicts"] > 96 * su.N  # more than 96 per row: 32 lanes per row
+        assert h.G == su.G and su.G > 64
+        assert np.array_equal(h.perm(), su.perm)
+        assert np.array_equal(h.groups(), su.group_of)
+        assert h.info().n_conflicts == su.info.n_conflicts
+        st, x, info = h.solve(s.f, tol=1e-300, maxit=5)
+    st_o, x_o, io = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1, tol=1e-300, maxit=5)
+    assert info.sweeps == io.sweeps == 5
+    assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) <= XTOL
