@@ -73,9 +73,10 @@ def _zero_rows():
 
 
 def _hubs():
-    # sparse diagonally dominant rows plus three hub rows/columns of degree 2000:
-    # heavy frontier vertices in the RCM kernels and slices whose rows differ
-    # in length by two orders of magnitude
+    # sparse diagonally dominant rows plus three hub rows/columns of degree 2000,
+    # 2000 and 2600: heavy frontier vertices in the RCM kernels, slices whose rows
+    # differ in length by two orders of magnitude, and segment sorts of every
+    # size class (the last hub's lists exceed one block's 2048)
     rng = np.random.default_rng(21)
     N = 6000
     rows, cols = [], []
@@ -84,8 +85,8 @@ def _hubs():
         c[c >= i] += 1
         rows += [i] * 5
         cols += list(c)
-    for h in (17, 3001, 5998):
-        nb = rng.choice(N, 2000, replace=False)
+    for h, deg in ((17, 2000), (3001, 2000), (5998, 2600)):
+        nb = rng.choice(N, deg, replace=False)
         nb = nb[nb != h]
         rows += [h] * len(nb) + list(nb)
         cols += list(nb) + [h] * len(nb)
