@@ -92,11 +92,38 @@ __global__ void scan_tile_apply(const Tin* in, int64_t* out, int64_t n, const in
     if (blockIdx.x == ntiles - 1 && threadIdx.x == 0) out[n] = offs[ntiles];
 }
 
+// the whole scan when it fits in one tile: one launch instead of three
+template <class Tin>
+__global__ void scan_single_tile(const Tin* in, int64_t* out, int64_t n)
+{
+    int64_t base = (int64_t)threadIdx.x * kScanItems;
+    int64_t loc[kScanItems];
+    int64_t s = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + k;
+        loc[k] = i < n ? (int64_t)in[i] : 0;
+        s += loc[k];
+    }
+    __shared__ int64_t tot;
+    int64_t ex = block_exclusive_scan(s, &tot);
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + k;
+        if (i < n) out[i] = ex;
+        ex += loc[k];
+    }
+    if (threadIdx.x == 0) out[n] = tot;
+}
+
 template <class Tin>
 void exclusive_scan_impl(const Tin* in, int64_t* out, int64_t n, cudaStream_t st)
 {
     if (n == 0) {
         OBK_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), st));
+        return;
+    }
+    if (n <= kScanTile) {
+        scan_single_tile<Tin><<<1, kScanBlock, 0, st>>>(in, out, n);
+        OBK_CHECK_LAUNCH();
         return;
     }
     int64_t ntiles = ceil_div(n, kScanTile);
