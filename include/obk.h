@@ -51,7 +51,8 @@ typedef enum {
 /* Sparse matrix in CSR form, 0-based.  row_ptr has m+1 monotone entries from 0
  * to nnz; columns strictly increase inside each row (sorted, no duplicates);
  * values are finite.  device_ptrs = 1 when the three arrays live in device
- * memory of the current device, 0 for host memory. */
+ * memory of the current device (obk_create then reads col_idx and val in place
+ * while it runs and keeps its own permuted copy), 0 for host memory. */
 typedef struct {
     const int64_t* row_ptr;
     const int32_t* col_idx;

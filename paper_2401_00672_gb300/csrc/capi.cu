@@ -375,16 +375,26 @@ obk_status obk_create_on_stream(const obk_csr* A, int64_t m, int64_t n, double t
         int64_t N = h->N, nnz = A->nnz;
         h->err.alloc(1, st);
         OBK_CUDA(cudaMemsetAsync(h->err.p, 0, sizeof(int), st));
-        // device copy of A with the extended row pointer (Algorithms 5-6)
+        // A on the device with the extended row pointer (Algorithms 5-6); column
+        // indices and values already in device memory are read in place (they
+        // are only read, and only during this call)
         bool dev = A->device_ptrs != 0;
         DBuf<int64_t> rp(N + 1, st);
-        DBuf<int32_t> ci(std::max<int64_t>(nnz, 1), st);
-        DBuf<double> v(std::max<int64_t>(nnz, 1), st);
+        DBuf<int32_t> ci_copy;
+        DBuf<double> v_copy;
         to_device(rp.p, A->row_ptr, m + 1, dev, st);
-        to_device(ci.p, A->col_idx, nnz, dev, st);
-        to_device(v.p, A->val, nnz, dev, st);
+        const int32_t* ci_p = A->col_idx;
+        const double* v_p = A->val;
+        if (!dev || nnz == 0) {
+            ci_copy.alloc(std::max<int64_t>(nnz, 1), st);
+            v_copy.alloc(std::max<int64_t>(nnz, 1), st);
+            to_device(ci_copy.p, A->col_idx, nnz, dev, st);
+            to_device(v_copy.p, A->val, nnz, dev, st);
+            ci_p = ci_copy.p;
+            v_p = v_copy.p;
+        }
         DBuf<int> bad(1, st);
-        validate_csr(m, n, rp.p, ci.p, v.p, nnz, bad.p, st);
+        validate_csr(m, n, rp.p, ci_p, v_p, nnz, bad.p, st);
         check_rowptr_ends<<<1, 32, 0, st>>>(rp.p, m, nnz, bad.p);
         OBK_CHECK_LAUNCH();
         int b = read_scalar(bad.p, st);
@@ -396,20 +406,20 @@ obk_status obk_create_on_stream(const obk_csr* A, int64_t m, int64_t n, double t
             OBK_CHECK_LAUNCH();
         }
         clock.mark(st);  // upload, validation, extension
-        h->info.bandwidth_before = half_bandwidth(N, rp.p, ci.p, nnz, st);
+        h->info.bandwidth_before = half_bandwidth(N, rp.p, ci_p, nnz, st);
         clock.mark(st);  // bandwidth of the input
         // Reverse Cuthill-McKee (Section 3.2) and A~ = P A^ P^T (Eq. 3.1)
         h->perm.alloc(N, st);
-        rcm_reorder(N, rp.p, ci.p, nnz, h->perm.p, kDefaultSpins, h->err.p, &h->rcm, st, &clock);
+        rcm_reorder(N, rp.p, ci_p, nnz, h->perm.p, kDefaultSpins, h->err.p, &h->rcm, st, &clock);
         clock.mark(st);  // Cuthill-McKee order, reversed
         DBuf<int32_t> iperm(N, st);
         DBuf<int64_t> rpt(N + 1, st);
         DBuf<int32_t> cit(std::max<int64_t>(nnz, 1), st);
         DBuf<double> vt(std::max<int64_t>(nnz, 1), st);
-        permute_csr(N, rp.p, ci.p, v.p, nnz, h->perm.p, iperm.p, rpt.p, cit.p, vt.p, st);
+        permute_csr(N, rp.p, ci_p, v_p, nnz, h->perm.p, iperm.p, rpt.p, cit.p, vt.p, st);
         rp.release();
-        ci.release();
-        v.release();
+        ci_copy.release();
+        v_copy.release();
         h->info.bandwidth_after = half_bandwidth(N, rpt.p, cit.p, nnz, st);
         clock.mark(st);  // permutation and its bandwidth
         // norms, groups and sweep layout (Section 3.3)
