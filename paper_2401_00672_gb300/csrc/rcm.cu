@@ -522,14 +522,12 @@ __device__ __forceinline__ void claim_group(const CmParams& p, int64_t b, int64_
 {
     for (int64_t q0 = b + lg; q0 < e; q0 += (int64_t)kNbRound * G) {
         int32_t x[kNbRound];
-        unsigned long long c[kNbRound];
 #pragma unroll
         for (int t = 0; t < kNbRound; ++t) x[t] = q0 + (int64_t)t * G < e ? p.adj_r[q0 + (int64_t)t * G] : -1;
-#pragma unroll
-        for (int t = 0; t < kNbRound; ++t) c[t] = x[t] >= 0 ? ld_relaxed_u64(p.claim + x[t]) : 0ull;
+        // reductions without a result: nothing waits for them before the barrier
 #pragma unroll
         for (int t = 0; t < kNbRound; ++t)
-            if (x[t] >= 0 && c[t] > pw) atomicMin(p.claim + x[t], pw);
+            if (x[t] >= 0) atomicMin(p.claim + x[t], pw);
     }
 }
 
