@@ -293,8 +293,11 @@ __device__ __forceinline__ void bfs_reach(const BfsParams& p, int32_t w, int L, 
 }
 
 // lanes lg, lg + G, ... of a group of G over the neighbours [b, e) of a vertex
+// (direct: narrow levels claim every neighbour with a compare-and-swap, one
+// round trip to discovery; wide levels first read dist and skip the visited
+// ones, sparing the atomics)
 __device__ __forceinline__ void bfs_expand(const BfsParams& p, int64_t b, int64_t e, int G, int lg, int L,
-                                           int32_t* sbuf, int* s_cnt, int64_t* cnext, int32_t* nxt)
+                                           int32_t* sbuf, int* s_cnt, int64_t* cnext, int32_t* nxt, bool direct)
 {
     for (int64_t q0 = b + lg; q0 < e; q0 += (int64_t)kNbRound * G) {
         int32_t w[kNbRound];
@@ -302,7 +305,8 @@ __device__ __forceinline__ void bfs_expand(const BfsParams& p, int64_t b, int64_
 #pragma unroll
         for (int t = 0; t < kNbRound; ++t) w[t] = q0 + (int64_t)t * G < e ? p.adj[q0 + (int64_t)t * G] : -1;
 #pragma unroll
-        for (int t = 0; t < kNbRound; ++t) d[t] = w[t] >= 0 ? ld_volatile_i32(p.dist + w[t]) : 0;
+        for (int t = 0; t < kNbRound; ++t)
+            d[t] = (w[t] >= 0 && !direct) ? ld_volatile_i32(p.dist + w[t]) : kUnvisited;
 #pragma unroll
         for (int t = 0; t < kNbRound; ++t)
             if (w[t] >= 0 && d[t] == kUnvisited) bfs_reach(p, w[t], L, sbuf, s_cnt, cnext, nxt);
@@ -344,6 +348,8 @@ __global__ void __launch_bounds__(kCoopBlock) bfs_levels(BfsParams p)
         const int G = group_lanes(c1 - c0);
         const int lg = threadIdx.x & (G - 1);
         const int ipp = blockDim.x / G;
+        // a frontier of at most a quarter of the threads counts as narrow
+        const bool direct = ncur * 4 <= nth;
         for (int64_t k = c0 + threadIdx.x / G; k < c1; k += ipp) {
             int32_t u = cur[k];
             int64_t b = p.gp[u], e = p.gp[u + 1];
@@ -351,12 +357,12 @@ __global__ void __launch_bounds__(kCoopBlock) bfs_levels(BfsParams p)
                 if (lg == 0) heavy[atomicAdd(&s_nheavy, 1)] = u;
                 continue;
             }
-            bfs_expand(p, b, e, G, lg, L, sbuf, &s_cnt, cnext, nxt);
+            bfs_expand(p, b, e, G, lg, L, sbuf, &s_cnt, cnext, nxt, direct);
         }
         __syncthreads();
         for (int h = wid; h < s_nheavy; h += wpb) {
             int32_t u = heavy[h];
-            bfs_expand(p, p.gp[u], p.gp[u + 1], 32, lane, L, sbuf, &s_cnt, cnext, nxt);
+            bfs_expand(p, p.gp[u], p.gp[u + 1], 32, lane, L, sbuf, &s_cnt, cnext, nxt, direct);
         }
         __syncthreads();
         int nb = s_cnt < kBfsBuf ? s_cnt : kBfsBuf;
