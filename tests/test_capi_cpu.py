@@ -56,3 +56,20 @@ def test_invalid_arguments_rejected_before_any_device_work(libpath):
     assert obk.lib.obk_create(ctypes.byref(csr), 0, 3, 0.1, ctypes.byref(h)) == obk.OBK_ERR_INVALID
     assert obk.lib.obk_create(ctypes.byref(csr), 3, 3, 1.5, ctypes.byref(h)) == obk.OBK_ERR_INVALID
     assert obk.lib.obk_poll(None, 1, None, None) == obk.OBK_ERR_INVALID
+
+
+def test_request_footprint_host_only(libpath):
+    """The request loop's HBM reservation: zero for invalid sizes, grows with
+    the entries and with max(m, n), and covers at least the data it uploads."""
+    import paper_2401_00672_gb300 as obk
+
+    fp = obk.request_footprint
+    assert fp(0, 5, 10) == 0 and fp(5, 0, 10) == 0 and fp(5, 5, -1) == 0
+    base = fp(1000, 1000, 7000)
+    assert base > 0
+    assert fp(1000, 1000, 14000) > base  # more entries
+    assert fp(2000, 1000, 7000) > base and fp(1000, 2000, 7000) > base  # extended systems
+    assert fp(2000, 1000, 7000) == fp(1000, 2000, 7000)  # N = max(m, n) either way
+    for m, n, nnz in ((1000, 1000, 7000), (400_000, 200_000, 4_000_000)):
+        uploaded = (max(m, n) + 1) * 8 + nnz * (4 + 8) + max(m, n) * 16
+        assert fp(m, n, nnz) >= uploaded
