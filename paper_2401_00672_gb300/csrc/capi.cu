@@ -170,16 +170,20 @@ __global__ void sumsq_final(const double* part, double* out)
     }
 }
 
-double sum_squares(const double* a, const int32_t* idx, int64_t n, int64_t m, cudaStream_t st)
+// sum of squares into *out (device), queued on st without waiting
+void sum_squares_to(const double* a, const int32_t* idx, int64_t n, int64_t m, double* out, cudaStream_t st)
 {
-    if (n <= 0) return 0.0;
-    DBuf<double> part(kRedBlocks + 1, st);
+    if (n <= 0) {
+        OBK_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
+        return;
+    }
+    DBuf<double> part(kRedBlocks, st);
     sumsq_partial<<<kRedBlocks, kBlock, 0, st>>>(a, idx, n, m, part.p);
     OBK_CHECK_LAUNCH();
-    sumsq_final<<<1, 32, 0, st>>>(part.p, part.p + kRedBlocks);
+    sumsq_final<<<1, 32, 0, st>>>(part.p, out);
     OBK_CHECK_LAUNCH();
-    return read_scalar(part.p + kRedBlocks, st);
 }
+
 
 // ---- residual check with per-tile partial sums ----------------------------
 // Tile t covers rows [t*kResTile, (t+1)*kResTile); one block per tile, one warp
@@ -494,16 +498,29 @@ obk_status obk_solve_ex(obk_handle* h, const obk_opts* opts, const double* f, co
         check_finite<<<grid_for(n), kBlock, 0, st>>>(x0d.p, n, bad.p);
         OBK_CHECK_LAUNCH();
     }
-    if (read_scalar(bad.p, st)) throw Error{-1, "f or x0 holds NaN or Inf"};
-    // x~0 = P x^0, f in group-major order, ||f||^2 and the all-zero rows' share
+    // x~0 = P x^0, f in group-major order, ||f||^2 and the all-zero rows' share;
+    // the finiteness flag and the two sums come back in one read
     permute_x0<<<grid_for(N), kBlock, 0, st>>>(N, h->perm.p, x0 ? x0d.p : nullptr, n, xt.p);
     OBK_CHECK_LAUNCH();
     if (h->L.Ngm) {
         gather_gm<<<grid_for(h->L.Ngm), kBlock, 0, st>>>(h->L.Ngm, h->src_gm.p, fd.p, m, fgm.p);
         OBK_CHECK_LAUNCH();
     }
-    double fnorm2 = sum_squares(fd.p, nullptr, m, m, st);
-    double zero_f2 = sum_squares(fd.p, h->zero_src.p, h->n_zero, m, st);
+    DBuf<double> sums(2, st);
+    sum_squares_to(fd.p, nullptr, m, m, sums.p, st);
+    sum_squares_to(fd.p, h->zero_src.p, h->n_zero, m, sums.p + 1, st);
+    double fnorm2 = 0.0, zero_f2 = 0.0;
+    {
+        char* hs = static_cast<char*>(pinned_scratch());
+        OBK_CUDA(cudaMemcpyAsync(hs, sums.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        OBK_CUDA(cudaMemcpyAsync(hs + 2 * sizeof(double), bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        OBK_CUDA(cudaStreamSynchronize(st));
+        int b = 0;
+        std::memcpy(&fnorm2, hs, sizeof(double));
+        std::memcpy(&zero_f2, hs + sizeof(double), sizeof(double));
+        std::memcpy(&b, hs + 2 * sizeof(double), sizeof(int));
+        if (b) throw Error{-1, "f or x0 holds NaN or Inf"};
+    }
     SolveArgs a;
     a.precision = o.precision;
     a.check_every = o.check_every == 0 ? 1 : o.check_every;
