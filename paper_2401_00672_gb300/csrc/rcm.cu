@@ -24,7 +24,10 @@
 //     placed neighbour of sequential Cuthill-McKee; children are then written
 //     contiguously after an exclusive scan of per-parent child counts, in the
 //     r order of the parent's adjacency list.  This reproduces the sequential
-//     queue order exactly.
+//     queue order exactly;
+//   * the Cuthill-McKee pass overlaps the root search: it runs on a second
+//     stream, beside the search's BFS, from the roots a search round would end
+//     with, and is kept when the search ends with exactly those roots.
 #include <cooperative_groups.h>
 
 #include <algorithm>
