@@ -1,4 +1,7 @@
-// primitives.cu -- scan and stable radix sort used by the setup kernels.
+// primitives.cu -- building blocks of the setup: exclusive scans, a stable LSD
+// radix sort, per-segment sorts (register sorting networks for short segments)
+// and the CSR pattern transpose (structurally symmetric fast path or counting
+// scatter), plus the host helpers for waits and cooperative grid sizes.
 #include "common.cuh"
 
 namespace obk {
