@@ -35,6 +35,15 @@
  *   unpermute   x = P^T x~ (Algorithm 4 last step), then x = x^(1:n) for m > n.
  *   refine      FP32 inner sweeps inside FP64 iterative refinement (not in the
  *               paper; the FP32 arithmetic is done in C float, no contraction).
+ *   stats       Definitions 1-2 at the row level: the nonzero entries of the
+ *               N x N row-cosine table and the sum of their |cos|, each rounded
+ *               to a multiple of 2^-32 (zn and nn follow from the two).
+ *   pinv step   Eq. 1.3 for a near-orthogonal group: y solves the group's Gram
+ *               system (A_tau A_tau^T) y = f_tau - A_tau x by K Jacobi steps from
+ *               the simultaneous step y = r / ||A_i||^2, then x += A_tau^T y.
+ *   blocks      Algorithm 4 as printed: k blocks of consecutive rows, centroid
+ *               cosines, Oclass pairs and Nclass blocks, each block's
+ *               correction A_b^+ r as the CGLS least-squares solution from zero.
  */
 #include <math.h>
 #include <stdint.h>
