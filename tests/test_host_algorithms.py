@@ -1,0 +1,117 @@
+"""Host checks of two algorithmic facts the GPU setup relies on (CPU only):
+
+* first fit in index order is the unique fixed point of
+  c_i = mex{c_j : j < i conflicting}, reached by in-place rounds in any row
+  order and with any run structure (the grouping kernel's rounds);
+* the odd-even merge sorting networks of the per-segment sort (the product
+  source, compiled for the host) sort every input (0-1 principle for 8 and 16
+  inputs, random inputs for 32 and 64).
+"""
+import os
+import re
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _first_fit(n, earlier):
+    c = np.zeros(n, np.int64)
+    for i in range(n):
+        used = {c[j] for j in earlier[i]}
+        g = 0
+        while g in used:
+            g += 1
+        c[i] = g
+    return c
+
+
+def _rounds(n, earlier, order_rng, run):
+    c = np.zeros(n, np.int64)
+    rounds = 0
+    while True:
+        rounds += 1
+        changed = False
+        starts = np.arange(0, n, run)
+        order_rng.shuffle(starts)  # lane groups finish their runs in any order
+        for s in starts:
+            for i in range(s, min(s + run, n)):  # a run in index order
+                used = {c[j] for j in earlier[i]}
+                g = 0
+                while g in used:
+                    g += 1
+                if g != c[i]:
+                    c[i] = g
+                    changed = True
+        if not changed:
+            return c, rounds
+        assert rounds <= n + 2
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("run", [1, 3, 8])
+def test_fixed_point_rounds_reach_first_fit(seed, run):
+    rng = np.random.default_rng(seed)
+    n = 120
+    # conflicts mostly between nearby rows, a few long-range ones
+    earlier = [[] for _ in range(n)]
+    for i in range(n):
+        for j in range(max(0, i - 6), i):
+            if rng.random() < 0.4:
+                earlier[i].append(j)
+        if i > 20 and rng.random() < 0.2:
+            earlier[i].append(int(rng.integers(0, i - 10)))
+    want = _first_fit(n, earlier)
+    got, _ = _rounds(n, earlier, np.random.default_rng(seed + 100), run)
+    assert np.array_equal(got, want)
+
+
+def _network_source():
+    src = open(os.path.join(ROOT, "paper_2401_00672_gb300", "csrc", "primitives.cu")).read()
+    a = src.index("__device__ __forceinline__ void cmp_swap(")
+    b = src.index("template <int W>\n__device__ __forceinline__ void sort_segment(")
+    return re.sub(r"#pragma unroll\n", "", src[a:b])
+
+
+def test_sorting_networks(tmp_path):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        pytest.skip("no C++ compiler")
+    prog = (
+        "#include <cstdint>\n#include <cstdio>\n#include <algorithm>\n#include <random>\n"
+        "#define __device__\n#define __forceinline__ inline\n"
+        + _network_source()
+        + r"""
+template <int W> bool zero_one() {
+  for (uint32_t m = 0; m < (1u << W); ++m) {
+    uint64_t a[W]; for (int t = 0; t < W; ++t) a[t] = (m >> t) & 1;
+    oddeven_sort<W>(a);
+    for (int t = 1; t < W; ++t) if (a[t - 1] > a[t]) return false;
+  }
+  return true;
+}
+template <int W> bool random_inputs() {
+  std::mt19937_64 g(7);
+  for (int r = 0; r < 20000; ++r) {
+    uint64_t a[W], b[W];
+    for (int t = 0; t < W; ++t) a[t] = b[t] = g() % 97;
+    oddeven_sort<W>(a); std::sort(b, b + W);
+    for (int t = 0; t < W; ++t) if (a[t] != b[t]) return false;
+  }
+  return true;
+}
+int main() {
+  bool ok = zero_one<8>() && zero_one<16>() && random_inputs<32>() && random_inputs<64>();
+  std::printf("%s\n", ok ? "ok" : "fail");
+  return ok ? 0 : 1;
+}
+""")
+    cpp = tmp_path / "net.cpp"
+    cpp.write_text(prog)
+    exe = tmp_path / "net"
+    subprocess.run([cxx, "-O1", "-std=c++17", str(cpp), "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip() == "ok"
