@@ -115,3 +115,63 @@ int main() {
     subprocess.run([cxx, "-O1", "-std=c++17", str(cpp), "-o", str(exe)], check=True)
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0 and r.stdout.strip() == "ok"
+
+
+def _conflict_source():
+    src = open(os.path.join(ROOT, "paper_2401_00672_gb300", "csrc", "setup.cu")).read()
+    a = src.index("__device__ __forceinline__ bool is_conflict(")
+    b = src.index("// x == 0.0 for a row norm")
+    return src[a:b]
+
+
+def test_conflict_band_matches_ieee_division(tmp_path):
+    """The integer band test of the pair kernel decides |dot / (s_j s_i)| >= thr
+    exactly like the IEEE division, also for dot products within a few units of
+    rounding of the threshold."""
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        pytest.skip("no C++ compiler")
+    prog = (
+        "#include <cstdint>\n#include <cstdio>\n#include <cstring>\n#include <cmath>\n#include <random>\n"
+        "#define __device__\n#define __forceinline__ inline\n"
+        "static inline long long __double_as_longlong(double x) { long long r; std::memcpy(&r, &x, 8); return r; }\n"
+        "static inline double __ddiv_rn(double a, double b) { return a / b; }\n"
+        "static inline double __dmul_rn(double a, double b) { return a * b; }\n"
+        + _conflict_source()
+        + r"""
+int main() {
+  std::mt19937_64 g(11);
+  std::uniform_real_distribution<double> u(-3.0, 3.0), w(0.0, 1.0);
+  long long n = 0, bad = 0;
+  const double thrs[4] = {0.1, 0.05, 0.3, 0.7};
+  for (int r = 0; r < 200000; ++r) {
+    double si = std::pow(10.0, u(g)), sj = std::pow(10.0, u(g));
+    double thr = r % 5 == 4 ? w(g) * 0.9 + 0.01 : thrs[r % 4];
+    double thr_si = thr * si;
+    double t = thr_si * sj;
+    for (int k = -40; k <= 40; ++k) {
+      double dot = std::nextafter(t, k < 0 ? 0.0 : INFINITY);
+      for (int s = 1; s < (k < 0 ? -k : k); ++s) dot = std::nextafter(dot, k < 0 ? 0.0 : INFINITY);
+      if (k == 0) dot = t;
+      for (int sign = 0; sign < 2; ++sign) {
+        double d = sign ? -dot : dot;
+        bool want = std::fabs(d / (sj * si)) >= thr;
+        if (is_conflict(d, sj, si, thr_si, thr) != want) ++bad;
+        ++n;
+      }
+    }
+    double d = (w(g) - 0.5) * 4.0 * t;
+    if (is_conflict(d, sj, si, thr_si, thr) != (std::fabs(d / (sj * si)) >= thr)) ++bad;
+    ++n;
+  }
+  std::printf("%lld %lld\n", n, bad);
+  return bad == 0 ? 0 : 1;
+}
+""")
+    cpp = tmp_path / "band.cpp"
+    cpp.write_text(prog)
+    exe = tmp_path / "band"
+    subprocess.run([cxx, "-O2", "-std=c++17", "-ffp-contract=off", str(cpp), "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    n, bad = map(int, r.stdout.split())
+    assert n > 1_000_000 and bad == 0, r.stdout
