@@ -175,3 +175,68 @@ int main() {
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     n, bad = map(int, r.stdout.split())
     assert n > 1_000_000 and bad == 0, r.stdout
+
+
+def _cm_sequential(adj, rank, root):
+    order, seen = [root], {root}
+    k = 0
+    while k < len(order):
+        u = order[k]
+        for w in sorted(adj[u], key=lambda v: rank[v]):
+            if w not in seen:
+                seen.add(w)
+                order.append(w)
+        k += 1
+    return order
+
+
+def _cm_by_claims(adj, rank, root):
+    # the GPU formulation: every placed vertex has priority P (the root 0; the
+    # idx-th child, in rank order, of the vertex at queue position k gets
+    # (k + 1) * 2^32 + idx); each vertex of the next level is claimed by the
+    # smallest priority among its placed neighbours; a level's children are
+    # counted per parent and placed after a scan of the counts
+    INF = float("inf")
+    claim = {v: INF for v in adj}
+    prio = {root: 0}
+    Q = [root]
+    claim[root] = 0
+    for x in adj[root]:
+        claim[x] = min(claim[x], 0)
+    lo, hi = 0, 1
+    while hi > lo:
+        counts = []
+        kids = []
+        for k in range(lo, hi):
+            u = Q[k]
+            ch = [w for w in sorted(adj[u], key=lambda v: rank[v]) if claim[w] == prio[u] and w not in prio]
+            counts.append(len(ch))
+            kids.append(ch)
+        for k, ch in zip(range(lo, hi), kids):
+            for idx, w in enumerate(ch):
+                prio[w] = (k + 1) * 2**32 + idx
+                Q.append(w)
+        for w in Q[hi:]:
+            for x in adj[w]:
+                claim[x] = min(claim[x], prio[w])
+        lo, hi = hi, len(Q)
+    return Q
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_cuthill_mckee_by_claims_equals_sequential(seed):
+    rng = np.random.default_rng(seed)
+    n = 200
+    adj = {v: set() for v in range(n)}
+    for v in range(1, n):  # a random tree keeps the graph connected
+        u = int(rng.integers(0, v))
+        adj[u].add(v)
+        adj[v].add(u)
+    for _ in range(3 * n):
+        a, b = map(int, rng.integers(0, n, 2))
+        if a != b:
+            adj[a].add(b)
+            adj[b].add(a)
+    rank = {v: r for r, v in enumerate(sorted(adj, key=lambda v: (len(adj[v]), v)))}
+    root = int(rng.integers(0, n))
+    assert _cm_by_claims(adj, rank, root) == _cm_sequential(adj, rank, root)
