@@ -234,3 +234,19 @@ def test_adaptive_check_schedule_never_stops_early():
         st, _, ad = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, tol=tol, maxit=5000, check_every=-1)
         assert st == oracle.OK and ad.rel_res <= tol
         assert fixed.sweeps <= ad.sweeps <= fixed.sweeps + max(2, fixed.sweeps // 4)
+
+
+def test_all_zero_matrix():
+    """The degenerate empty matrix: every vertex is its own component, so the
+    order is the identity reversed; no row joins a group; f = 0 is solved at
+    once by x = 0 and f != 0 cannot be reached."""
+    m = n = 5
+    rp = np.zeros(m + 1, np.int64)
+    ci = np.zeros(0, np.int32)
+    v = np.zeros(0)
+    su = oracle.setup(m, n, rp, ci, v, np.zeros(m), thr=0.1)
+    assert su.G == 0 and np.array_equal(su.perm, np.arange(m)[::-1])
+    st, x, info = oracle.solve(m, n, rp, ci, v, np.zeros(m), thr=0.1, tol=1e-8, maxit=10)
+    assert st == 0 and info.sweeps == 0 and not x.any()
+    st, x, info = oracle.solve(m, n, rp, ci, v, np.ones(m), thr=0.1, tol=1e-8, maxit=10)
+    assert st == 1 and not x.any()
