@@ -1,21 +1,26 @@
 """Benchmark: OBK-RCM time to solution on one GB300 (and replicas on N GPUs).
 
 Workload (default): the symmetrised 12-nearest-neighbour matrix of n =
-1,000,000 points uniform in the unit cube (off-diagonals N(0,1), diagonal 1.2 x
+4,000,000 points uniform in the unit cube (off-diagonals N(0,1), diagonal 1.2 x
 the row's absolute off-diagonal sum, scattered by a random relabelling),
-x* ~ N(0,1), f = A x*, cosine threshold 0.1, FP64, stop at
-||f - A x|| / ||f|| <= 1e-8.
+x* ~ N(0,1), f = A x*, cosine threshold 0.1, solved with FP32 inner sweeps
+inside FP64 iterative refinement to ||f - A x|| / ||f|| <= 1e-10.
+`--workload knn1m` selects the 1,000,000-row system in FP64 to 1e-8.
 
 One step = the whole hot path through the C ABI on inputs resident in HBM:
 obk_create (extension, RCM, permutation, row norms, grouping, layout) +
 obk_solve (sweeps to tolerance with residual checks, un-permutation).
 K steps are timed with CUDA events on the library's stream between barriers.
-The matrix (190 MB) is larger than L2 (129 MB), so no explicit flush is done.
+The matrix (700 MB at n = 4M) is larger than L2 (129 MB), so no flush is done.
 
-Also reported: e2e (the same step with host buffers: H2D of A and f and D2H
-of x inside the timed region), the sweep kernel's roofline (differential CUDA
-event timing of solves with 10 and 60 sweeps), the CPU oracle's time on this
-host (cpu_baseline) and SM clocks sampled during the timed region.
+Also reported: the plain FP64 solve of the same system to the same tolerance
+(fp64_time_to_solution), e2e (the same step with host buffers: H2D of A and f
+and D2H of x inside the timed region), the sweep kernel's HBM roofline for the
+FP32 inner sweep and the FP64 sweep (differential CUDA event timing of solves
+with 10 and 60 sweeps) with their arithmetic rates against the measured
+multiply-add peaks, the precision form's error against the FP64 oracle and the
+oracle's own precision form at n = 200,000, the CPU oracle's time on this host
+(cpu_baseline) and SM clocks sampled during the timed region.
 
 `--impl reference` runs the CPU oracle on the same workload instead.
 N > 1 (torchrun): independent replicas, one system per rank, no collective on
@@ -39,17 +44,21 @@ sys.path.insert(0, ROOT)
 
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-FP64_PEAK_TFLOPS = 1.25  # 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (nominal table)
-TRAFFIC_JSON = os.path.join(ROOT, "profiles", "obk_solve_kernel_knn1m.json")
+# DRAM bytes per sweep from committed ncu captures, per workload
+TRAFFIC_JSON = {
+    "knn1m": os.path.join(ROOT, "profiles", "obk_solve_kernel_knn1m.json"),
+    "knn4m_ir": os.path.join(ROOT, "profiles", "obk_solve_kernel_fp32_knn4m.json"),
+}
 
 
-def sweep_traffic():
-    """DRAM bytes per sweep from the committed ncu capture, or None when the
-    kernel sources changed since the capture (hash mismatch)."""
+def sweep_traffic(name: str):
+    """DRAM bytes per sweep from the committed ncu capture of this workload, or
+    None when there is none or the kernel sources changed since the capture
+    (hash mismatch)."""
     import hashlib
 
     try:
-        with open(TRAFFIC_JSON) as fh:
+        with open(TRAFFIC_JSON[name]) as fh:
             d = json.load(fh)
         csrc = os.path.join(ROOT, "paper_2401_00672_gb300", "csrc")
         src = open(os.path.join(csrc, "sweep.cu"), "rb").read() + open(os.path.join(csrc, "common.cuh"), "rb").read()
@@ -60,9 +69,20 @@ def sweep_traffic():
         return None
 
 
+PRECISION = {"knn4m_ir": 1, "knn1m_ir": 1}  # workloads of the precision form; the rest run FP64
+
+
 def workload(name: str, rank: int):
     import synth
 
+    if name == "knn4m_ir":
+        s = synth.knn_dominant(4_000_000, 12, seed=replica_seed(1003, rank))
+        return s, dict(workload="knn_n4e6_12nn_fp32_sweeps_fp64_refinement", n=4_000_000, knn=12, diag_factor=1.2,
+                       thr=0.1, tol=1e-10, precision="FP32 inner sweeps inside FP64 iterative refinement")
+    if name == "knn1m_ir":
+        s = synth.knn_dominant(1_000_000, 12, seed=replica_seed(1003, rank))
+        return s, dict(workload="knn_n1e6_12nn_fp32_sweeps_fp64_refinement", n=1_000_000, knn=12, diag_factor=1.2,
+                       thr=0.1, tol=1e-10, precision="FP32 inner sweeps inside FP64 iterative refinement")
     if name == "knn1m":
         s = synth.knn_dominant(1_000_000, 12, seed=replica_seed(1001, rank))
         return s, dict(workload="knn_n1e6_12nn_fp64", n=1_000_000, knn=12, diag_factor=1.2, thr=0.1,
@@ -86,6 +106,10 @@ def workload(name: str, rank: int):
         return s, dict(workload="rect_m2e5_n8e5_10nnz_fp64", m=200_000, n=800_000, nnz_per_row=10, thr=0.1,
                        tol=1e-8, precision="fp64", variant="underdetermined consistent (UOBK, Algorithm 6)")
     raise SystemExit(f"unknown workload {name}")
+
+
+for _w in ("knn1m", "dominant2000", "knn200k", "rect800k", "rect800k_noisy", "rect_under800k"):
+    PRECISION[_w] = 0
 
 
 def min_norm_solution(A, f, tol=1e-13, maxit=5000):
@@ -186,30 +210,36 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def run_reference(args, cfg, s):
-    """The CPU oracle on the same workload (rank 0 only)."""
+def run_reference(args, cfg, s, prec):
+    """The CPU oracle on the same workload (rank 0 only): full solves, at most
+    two timed after at most one untimed, so that the run stays within minutes."""
     import oracle
 
     A = s.A
     oracle.build()
-    nrun = max(1, min(args.steps, 3))
-    nwarm = max(0, min(args.warmup, 3))
+    nrun = max(1, min(args.steps, 2))
+    nwarm = max(0, min(args.warmup, 1))
+
+    def one():
+        return oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=cfg["thr"], tol=cfg["tol"],
+                            maxit=20000, check_every=-1, precision=prec, inner_sweeps=8)
+
     for _ in range(nwarm):  # untimed, like the GPU arm's warm-up steps
-        oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=cfg["thr"], tol=cfg["tol"], maxit=10000,
-                     check_every=-1)
+        one()
     t_all = []
     info = None
     for _ in range(nrun):
         t0 = time.perf_counter()
-        st, x, info = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=cfg["thr"], tol=cfg["tol"],
-                                   maxit=10000, check_every=-1)
+        st, x, info = one()
         t_all.append(time.perf_counter() - t0)
     v = float(np.mean(t_all))
+    form = "FP32 inner sweeps (8 per step) + FP64 refinement" if prec == 1 else "FP64"
     sample = (f"{nrun} timed full oracle solve(s) of the workload (of {args.steps} requested steps) after "
-              f"{nwarm} untimed ones; {info.sweeps} sweeps, single-threaded plain C")
+              f"{nwarm} untimed one(s); {form}, {info.sweeps} sweeps, single-threaded plain C")
     line = {"metric": "time_to_solution", "value": v, "unit": "s", "higher_is_better": False,
             "impl": "reference", "n_gpus": args.gpus, "steps": nrun, "warmup": nwarm, "ms_per_step": v * 1e3,
-            "dtype": "f64", "data": "synthetic", "config": cfg, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == 1 else "f64", "data": "synthetic", "config": cfg, "scaling": "weak",
+            "vs_baseline": None,
             "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -267,23 +297,75 @@ def precision_study(args):
     print(json.dumps(out), flush=True)
 
 
+def _materialize(r):
+    """Worker: the request's system, from its own seed (synth recipes)."""
+    import synth
+
+    if r.m == 2 * r.n:
+        return synth.rect_random(r.m, r.n, 10, r.seed)
+    if r.m < r.n:
+        return synth.rect_random(r.m, r.n, 10, r.seed, full_columns=False)
+    return synth.random_dominant(r.n, 7, r.seed)
+
+
+def _oracle_request(r):
+    """Worker: one request solved by the CPU oracle (one core)."""
+    import oracle
+
+    s = _materialize(r)
+    A = s.A
+    st, x, info = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1, tol=1e-8, maxit=20000,
+                               check_every=-1, precision=r.precision, inner_sweeps=8)
+    return int(st), info.sweeps
+
+
 def serving_study(args):
     """Request loop: Poisson arrivals of independent systems (75 % square
     random_dominant, 25 % overdetermined m = 2n), n log-uniform in [1e3, 2e5],
-    precision 50/50, tol 1e-8.  First all requests at t = 0 (closed-loop
-    capacity mu), then open-loop Poisson arrivals at 0.8 mu: req/s, p50/p99."""
+    precision 50/50, tol 1e-8, HBM budget 150 GB.  First all requests at t = 0
+    (closed-loop capacity mu), then open-loop Poisson arrivals at the given
+    fractions of mu: req/s, p50/p99 latency.  The CPU baseline is the oracle on
+    every host core, one request per core, over the first --cpu-requests
+    requests of the same stream.  The process pool (spawn) does its CPU work
+    and materialises the systems before CUDA is initialised."""
+    import multiprocessing as mp
+    import platform
+
+    import oracle
+    import synth
+
+    oracle.build()
+    reqs = synth.request_stream(args.requests, rate_per_s=1.0, seed=1004, materialize=False,
+                                frac_under=args.under_frac)
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        sample = reqs[: max(1, min(args.cpu_requests, len(reqs)))]
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_request, sample, chunksize=1)
+        cpu_wall = time.perf_counter() - t0
+        systems = pool.map(_materialize, reqs, chunksize=8)
+    cpu_model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    cpu_model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    cpu = {"value": len(sample) / cpu_wall, "unit": "req/s", "cores": cores, "kind": "oracle",
+           "cpu": cpu_model, "sample": f"the first {len(sample)} requests of the stream, one per core",
+           "converged": sum(1 for st, _ in res if st == 0)}
+
     import torch  # noqa: F401  (initialises CUDA for the library)
 
     import paper_2401_00672_gb300 as obk
-    import synth
-
-    reqs = synth.request_stream(args.requests, rate_per_s=1.0, seed=1004, materialize=True,
-                                frac_under=args.under_frac)
 
     def run(rate):
         srv = obk.Server(hbm_budget_bytes=150 << 30, max_streams=args.streams)
         t0 = time.perf_counter()
-        submit_t, done_t, tickets = {}, {}, {}
+        submit_t, done_t, tickets, status = {}, {}, {}, {}
         gaps = np.random.default_rng(7).exponential(1.0 / rate, len(reqs)) if rate else np.zeros(len(reqs))
         arrive = np.cumsum(gaps) - gaps[0]
         i = 0
@@ -291,11 +373,10 @@ def serving_study(args):
         while len(done_t) < len(reqs):
             now = time.perf_counter() - t0
             while i < len(reqs) and arrive[i] <= now:
-                r = reqs[i]
-                A = r.system.A
+                r, sy = reqs[i], systems[i]
+                A = sy.A
                 opts = obk.Opts(precision=r.precision)
-                tk = srv.submit(A.row_ptr, A.col_idx, A.val, A.m, A.n, r.system.f, tol=1e-8, maxit=20000,
-                                opts=opts)
+                tk = srv.submit(A.row_ptr, A.col_idx, A.val, A.m, A.n, sy.f, tol=1e-8, maxit=20000, opts=opts)
                 tickets[tk] = i
                 submit_t[i] = time.perf_counter() - t0
                 pending.add(tk)
@@ -304,20 +385,26 @@ def serving_study(args):
                 st, x, info = srv.poll(tk, reqs[tickets[tk]].n)
                 if st != obk.OBK_PENDING:
                     done_t[tickets[tk]] = time.perf_counter() - t0
+                    status[tickets[tk]] = int(st)
                     pending.discard(tk)
             time.sleep(0.0005)
         srv.close()
         wall = max(done_t.values())
         lat = np.array([done_t[k] - submit_t[k] for k in done_t])
         return {"req_per_s": len(reqs) / wall, "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                "p99_ms": float(np.percentile(lat, 99) * 1e3), "wall_s": wall}
+                "p99_ms": float(np.percentile(lat, 99) * 1e3), "wall_s": wall,
+                "converged": sum(1 for v in status.values() if v == 0)}
 
     closed = run(None)
     mu = closed["req_per_s"]
-    opened = run(0.8 * mu)
-    print(json.dumps({"metric": "serving", "requests": len(reqs), "streams": args.streams,
-                      "under_frac": args.under_frac, "closed_loop": closed, "open_loop_0.8mu": opened}),
-          flush=True)
+    out = {"metric": "serving", "unit": "req/s", "requests": len(reqs), "streams": args.streams,
+           "under_frac": args.under_frac, "hbm_budget_gb": 150, "tol": 1e-8,
+           "mix": "75 % square (random_dominant, k = 7), 25 % overdetermined m = 2n (rect_random, k = 10); "
+                  "n log-uniform in [1e3, 2e5]; precision 50/50",
+           "closed_loop": closed, "cpu_baseline": cpu}
+    for frac in (float(t) for t in args.loads.split(",")):
+        out[f"open_loop_{frac}mu"] = run(frac * mu)
+    print(json.dumps(out), flush=True)
 
 
 def thr_sweep(args):
@@ -454,24 +541,117 @@ def blocks_study(args):
                       "rows": rows}), flush=True)
 
 
+def sweep_time(obk, h, f, x, stream, precision, rpw=0):
+    """Device time of one sweep of the prepared system h: two solves with a
+    residual only at their start and end, 10 and 60 sweeps (FP64), or one
+    refinement step of 10 and 60 FP32 inner sweeps (precision form); the
+    difference of the best of three CUDA-event timings, divided by 50."""
+    import torch
+
+    per = {}
+    for k in (10, 60):
+        if precision == 1:
+            o = obk.Opts(precision=1, inner_sweeps=k, max_outer=1, rows_per_warp=rpw)
+        else:
+            o = obk.Opts(check_every=1 << 30, rows_per_warp=rpw)
+        best = None
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.solve(f, None, tol=1e-300, maxit=k, out=x, opts=o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_ = e0.elapsed_time(e1)
+            best = t_ if best is None else min(best, t_)
+        per[k] = best
+    return (per[60] - per[10]) / 50.0
+
+
+def sweep_bytes(nnz: int, N: int, precision: int) -> float:
+    """Algorithmic bytes of one sweep: A read once, per-row vectors, x read and written.
+    FP64: 12 B per entry (8 B value + 4 B column), 4 B row pointer (int32 view),
+    8 B f, 8 B 1/||A_i||^2, 16 B x.  FP32 inner sweep: 8 B per entry (4 B value +
+    4 B column), 4 B row pointer, 4 B right-hand side, 8 B for the row norm, 8 B x."""
+    if precision == 1:
+        return 8.0 * nnz + 4.0 * (N + 1) + 4.0 * N + 8.0 * N + 8.0 * N
+    return 12.0 * nnz + 4.0 * (N + 1) + 8.0 * N + 8.0 * N + 16.0 * N
+
+
+def roofline_of(sweep_ms, nnz, N, precision, hbm_peak, hbm_src, measured, traffic):
+    """HBM roofline of the sweep (the fraction the scope table defines), with the
+    arithmetic rate against the measured multiply-add peak beside it."""
+    b = sweep_bytes(nnz, N, precision)
+    gbs = b / (sweep_ms * 1e-3) / 1e9
+    tfs = 4.0 * nnz / (sweep_ms * 1e-3) / 1e12  # one multiply-add per entry in each phase
+    alu_peak = measured["fp32_fma_tflops"] if precision == 1 else measured["fp64_fma_tflops"]
+    return {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(gbs / hbm_peak, 4), "traffic": traffic,
+            "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs, of measured)" if hbm_src == "measured"
+            else "fallback 6.8 TB/s (of fallback)",
+            "kernel": "obk_solve_kernel (sweep phases, " + ("FP32 inner sweep)" if precision == 1 else "FP64 sweep)"),
+            "unit_of_achieved": "per sweep", "sweep_ms": round(sweep_ms, 5), "bytes_per_sweep": b,
+            "flop_per_sweep": 4.0 * nnz, "alu_tflops": round(tfs, 4),
+            "alu_peak_measured_tflops": round(alu_peak, 4),
+            "alu_frac_of_measured": round(tfs / alu_peak, 4)}
+
+
+def parity_small(obk, torch, dev, stream):
+    """The precision form's error at n = 200,000 (the same kNN recipe): the GPU
+    FP64 and FP32+refinement results against the FP64 oracle and against the
+    oracle's own precision-form mode, all to rel. residual 1e-10."""
+    import oracle
+    import synth
+
+    s = synth.knn_dominant(200_000, 12, seed=1003)
+    A = s.A
+    oracle.build()
+    _, x64, i64 = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1, tol=1e-10, maxit=20000,
+                               check_every=-1)
+    _, x32, i32 = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1, tol=1e-10, maxit=20000,
+                               precision=1, inner_sweeps=8)
+    out = {"n": 200_000, "oracle_fp64_sweeps": i64.sweeps, "oracle_ir_sweeps": i32.sweeps,
+           "oracle_ir_outer": i32.outer_iters}
+    fd = torch.from_numpy(s.f).to(dev)
+    xd = torch.empty(A.n, dtype=torch.float64, device=dev)
+    h = obk.Handle(torch.from_numpy(A.row_ptr).to(dev), torch.from_numpy(A.col_idx).to(dev),
+                   torch.from_numpy(A.val).to(dev), A.m, A.n, thr=0.1, stream=stream.cuda_stream)
+    for name, o in (("gpu_fp64", obk.Opts(check_every=-1)), ("gpu_fp32_ir", obk.Opts(precision=1)),
+                    ("gpu_fp32_ir_8_inner", obk.Opts(precision=1, inner_sweeps=8))):
+        st, _, info = h.solve(fd, None, tol=1e-10, maxit=20000, out=xd, opts=o)
+        torch.cuda.synchronize()
+        xg = xd.cpu().numpy()
+        out[name] = {"status": int(st), "sweeps": info.sweeps, "outer": info.outer_iters, "rel_res": info.rel_res,
+                     "x_err_vs_fp64_oracle": float(np.linalg.norm(xg - x64) / np.linalg.norm(x64)),
+                     "x_err_vs_oracle_precision_form": float(np.linalg.norm(xg - x32) / np.linalg.norm(x32))}
+    h.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="knn1m")
+    ap.add_argument("--workload", default="knn4m_ir")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison and the n=200k parity")
+    ap.add_argument("--sweep-probe", action="store_true",
+                    help="only the 10- and 60-sweep solves of the roofline (for an ncu capture)")
     ap.add_argument("--precision-study", action="store_true", help="FP64 vs FP32+IR to 1e-10 (extra run)")
     ap.add_argument("--pn", type=int, default=4_000_000, help="n of the precision study")
     ap.add_argument("--serving", action="store_true", help="request-loop throughput and latency (extra run)")
-    ap.add_argument("--requests", type=int, default=512)
+    ap.add_argument("--requests", type=int, default=4096)
     ap.add_argument("--streams", type=int, default=8)
+    ap.add_argument("--loads", default="0.5,0.8,0.95", help="serving: open-loop rates as fractions of capacity")
+    ap.add_argument("--cpu-requests", type=int, default=256, help="serving: requests in the CPU baseline sample")
     ap.add_argument("--under-frac", type=float, default=0.0, help="serving: fraction of underdetermined requests")
     ap.add_argument("--thr-sweep", action="store_true", help="grouping threshold sweep with zn/nn (extra run)")
     ap.add_argument("--pinv-study", action="store_true", help="Eq. 1.3 group projection vs the simultaneous step")
     ap.add_argument("--blocks-study", action="store_true", help="paper-literal k-block form vs the row groups")
+    ap.add_argument("--peaks", action="store_true", help="measured FP64/FP32/L2 ceilings of this GPU")
     ap.add_argument("--tn", type=int, default=200_000, help="n of the threshold sweep")
     args = ap.parse_args()
     if args.precision_study:
@@ -484,6 +664,13 @@ def main():
         return pinv_study(args)
     if args.blocks_study:
         return blocks_study(args)
+    if args.peaks:
+        import torch  # noqa: F401  (initialises CUDA for the library)
+
+        import paper_2401_00672_gb300 as obk
+
+        print(json.dumps({"metric": "peaks", **obk.measure_peaks()}), flush=True)
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -493,7 +680,7 @@ def main():
         if rank != 0:
             return
         s, cfg = workload(args.workload, 0)
-        run_reference(args, cfg, s)
+        run_reference(args, cfg, s, PRECISION[args.workload])
         return
 
     import torch
@@ -508,6 +695,7 @@ def main():
     import paper_2401_00672_gb300 as obk
 
     s, cfg = workload(args.workload, rank)
+    prec = PRECISION[args.workload]
     A = s.A
     dev = torch.device("cuda", local_rank)
     rp = torch.from_numpy(A.row_ptr).to(dev)
@@ -518,12 +706,30 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     tol = cfg["tol"]
 
-    # adaptive residual-check schedule; stagnation stop for the inconsistent system
-    solve_opts = obk.Opts(check_every=-1, stagnation=1e-12 if "noisy" in args.workload else 0.0)
-
-    def step():
+    if args.sweep_probe:  # two launches of the sweep kernel on a prepared system
         h = obk.Handle(rp, ci, v, A.m, A.n, thr=cfg["thr"], stream=stream.cuda_stream)
-        st, _, info = h.solve(f, None, tol=tol, maxit=10000, out=x, opts=solve_opts)
+        for k in (10, 60):
+            o = (obk.Opts(precision=1, inner_sweeps=k, max_outer=1) if prec == 1
+                 else obk.Opts(check_every=1 << 30))
+            h.solve(f, None, tol=1e-300, maxit=k, out=x, opts=o)
+        torch.cuda.synchronize()
+        h.close()
+        print(json.dumps({"sweep_probe": cfg["workload"], "N": h.N, "nnz": A.nnz}), flush=True)
+        return
+
+    # FP64: adaptive residual-check schedule (stagnation stop for the inconsistent
+    # system); precision form: a residual check after every refinement step
+    if prec == 1:
+        solve_opts = obk.Opts(precision=1)
+        cfg["residual_checks"] = "after every refinement step (FP64 residual)"
+    else:
+        solve_opts = obk.Opts(check_every=-1, stagnation=1e-12 if "noisy" in args.workload else 0.0)
+        cfg["residual_checks"] = ("adaptive (check_every = -1: the next check where the observed linear rate "
+                                  "predicts tol, the gap at most doubling)")
+
+    def step(opts=solve_opts):
+        h = obk.Handle(rp, ci, v, A.m, A.n, thr=cfg["thr"], stream=stream.cuda_stream)
+        st, _, info = h.solve(f, None, tol=tol, maxit=20000, out=x, opts=opts)
         h.close()
         return st, info
 
@@ -555,9 +761,6 @@ def main():
     clocks = sampler.stop()
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, dev)
     st, info = infos[-1]
-    hp = obk.Handle(rp, ci, v, A.m, A.n, thr=cfg["thr"], stream=stream.cuda_stream)
-    setup_profile = hp.setup_profile()
-    hp.close()
     xh = x.cpu().numpy()
     err_xstar = float(np.linalg.norm(xh - s.xstar) / np.linalg.norm(s.xstar))
     err_min_norm = None
@@ -565,56 +768,43 @@ def main():
         xmn = min_norm_solution(A, s.f)
         err_min_norm = float(np.linalg.norm(xh - xmn) / np.linalg.norm(xmn))
 
-    # roofline of the sweep kernel: two solves on one prepared handle, 10 and 60
-    # sweeps with a residual only at start and end; the difference is 50 sweeps
-    h = obk.Handle(rp, ci, v, A.m, A.n, thr=cfg["thr"], stream=stream.cuda_stream)
-    N, nnz_gm = h.N, A.nnz
-
-    def sweep_time(rpw):
-        per = {}
-        for k in (10, 60):
+    # the plain FP64 solve of the same system to the same tolerance
+    fp64 = None
+    if prec == 1 and not args.no_extras:
+        o64 = obk.Opts(check_every=-1)
+        step(o64)
+        best, inf64 = None, None
+        for _ in range(3):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
-            best = None
-            for _ in range(3):
-                e0.record(stream)
-                h.solve(f, None, tol=1e-300, maxit=k, out=x, opts=obk.Opts(check_every=1 << 30, rows_per_warp=rpw))
-                e1.record(stream)
-                torch.cuda.synchronize()
-                t_ = e0.elapsed_time(e1)
-                best = t_ if best is None else min(best, t_)
-            per[k] = best
-        return (per[60] - per[10]) / 50.0
+            e0.record(stream)
+            st64, inf64 = step(o64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_ = e0.elapsed_time(e1)
+            best = t_ if best is None else min(best, t_)
+        fp64 = {"value": max_over_ranks(best, dist, dev) / 1e3, "unit": "s", "status": int(st64),
+                "sweeps": inf64.sweeps, "setup_ms": inf64.setup_ms, "solve_ms": inf64.solve_ms,
+                "rel_res": inf64.rel_res, "residual_checks": "adaptive (check_every = -1)", "best_of": 3}
 
-    by_rpw = {rpw: round(sweep_time(rpw), 5) for rpw in (32, 16, 8, 4, 2)}
-    sweep_ms = sweep_time(0)  # the default choice, as the timed solve runs it
-    h.close()
-    # algorithmic bytes of one sweep: A read once (8 B value + 4 B column per
-    # entry), row pointers (4 B/row as int32), f and 1/||A_i||^2 (8 + 8 B/row),
-    # x read and written (16 B/row)
-    bytes_sweep = 12.0 * nnz_gm + 4.0 * (N + 1) + 8.0 * N + 8.0 * N + 16.0 * N
-    flops_sweep = 4.0 * nnz_gm  # one multiply-add per entry in each of the two phases
+    hp = obk.Handle(rp, ci, v, A.m, A.n, thr=cfg["thr"], stream=stream.cuda_stream)
+    setup_profile = hp.setup_profile()
+    hp.close()
+
+    # rooflines of the sweep kernel on one prepared handle
+    measured = obk.measure_peaks()
     hbm_peak, hbm_src = peaks()
-    gbs = bytes_sweep / (sweep_ms * 1e-3) / 1e9
-    tfs = flops_sweep / (sweep_ms * 1e-3) / 1e12
-    frac_hbm = gbs / hbm_peak
-    frac_alu = tfs / FP64_PEAK_TFLOPS
-    traffic = sweep_traffic() if args.workload == "knn1m" else None
-    if frac_alu >= frac_hbm:
-        roof = {"bound": "alu", "achieved": round(tfs, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": round(frac_alu, 4), "traffic": traffic,
-                "peak_source": "FP64 derived from the nominal table (152 SMs x 2 DFMA/clk x 2 x 2.07 GHz); "
-                               "an FMA probe measured 1.197 TFLOP/s",
-                "kernel": "obk_solve_kernel (sweep phases)", "unit_of_achieved": "per sweep",
-                "hbm_frac_of_measured": round(frac_hbm, 4)}
-    else:
-        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(frac_hbm, 4), "traffic": traffic, "peak_source": hbm_src,
-                "kernel": "obk_solve_kernel (sweep phases)", "unit_of_achieved": "per sweep",
-                "alu_frac_of_nominal_fp64": round(frac_alu, 4)}
-    roof["sweep_ms"] = round(sweep_ms, 5)
+    h = obk.Handle(rp, ci, v, A.m, A.n, thr=cfg["thr"], stream=stream.cuda_stream)
+    N, nnz_gm = h.N, A.nnz
+    by_rpw = {rpw: round(sweep_time(obk, h, f, x, stream, prec, rpw), 5) for rpw in (32, 16, 8, 4, 2)}
+    sw_ms = sweep_time(obk, h, f, x, stream, prec)  # the default choice, as the timed solve runs it
+    roof = roofline_of(sw_ms, nnz_gm, N, prec, hbm_peak, hbm_src, measured, sweep_traffic(args.workload))
     roof["sweep_ms_by_rows_per_warp"] = by_rpw
-    roof["bytes_per_sweep"] = bytes_sweep
+    roof_fp64 = None
+    if prec == 1:
+        sw64 = sweep_time(obk, h, f, x, stream, 0)
+        roof_fp64 = roofline_of(sw64, nnz_gm, N, 0, hbm_peak, hbm_src, measured, None)
+    h.close()
 
     e2e = None
     if not args.no_e2e:
@@ -628,7 +818,7 @@ def main():
 
         def step_host():
             hh = obk.Handle(rp_h, ci_h, v_h, A.m, A.n, thr=cfg["thr"], stream=stream.cuda_stream)
-            hh.solve(f_h, None, tol=tol, maxit=10000, out=x_h, opts=solve_opts)
+            hh.solve(f_h, None, tol=tol, maxit=20000, out=x_h, opts=solve_opts)
             hh.close()
 
         step_host()
@@ -646,6 +836,10 @@ def main():
         e2e = {"value": ems / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(A.n * 8), "steps": k2}
 
+    parity = None
+    if rank == 0 and prec == 1 and not args.no_extras:
+        parity = parity_small(obk, torch, dev, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -653,28 +847,34 @@ def main():
         oracle.build()
         t0 = time.perf_counter()
         st_o, x_o, io = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=cfg["thr"], tol=tol,
-                                     maxit=10000, check_every=-1)
+                                     maxit=20000, check_every=-1, precision=prec, inner_sweeps=8)
         t_cpu = time.perf_counter() - t0
         par = float(np.linalg.norm(xh - x_o) / np.linalg.norm(x_o))
+        form = "FP32 inner sweeps (8 per step) + FP64 refinement" if prec == 1 else "FP64, adaptive checks"
         cpu = {"value": t_cpu, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": f"one full solve of the workload ({io.sweeps} sweeps), single-threaded plain C",
+               "sample": f"one full oracle solve of the workload ({form}; {io.sweeps} sweeps), "
+                         "single-threaded plain C",
                "x_rel_diff_vs_gpu": par, "oracle_sweeps": io.sweeps}
 
     if rank == 0:
         line = {
             "metric": "time_to_solution", "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32+f64" if prec == 1 else "f64", "data": "synthetic",
             "config": dict(cfg, parallelism=f"replicas{world}", l2="inputs larger than L2 (A = "
                            f"{(A.val.nbytes + A.col_idx.nbytes) / 1e6:.0f} MB), no flush"),
             "throughput_solves_per_s": world * 1e3 / ms,
-            "sweeps": info.sweeps, "groups": info.groups, "setup_ms": info.setup_ms, "solve_ms": info.solve_ms,
-            "setup_profile_ms": setup_profile,
+            "sweeps": info.sweeps, "outer_iters": info.outer_iters, "groups": info.groups,
+            "setup_ms": info.setup_ms, "solve_ms": info.solve_ms, "setup_profile_ms": setup_profile,
             "rel_res": info.rel_res, "status": st, "x_err_vs_xstar": err_xstar,
             **({"x_err_vs_min_norm": err_min_norm} if err_min_norm is not None else {}),
             "bandwidth": [info.bandwidth_before, info.bandwidth_after],
             "gpu_launches": int(launches // max(args.steps, 1)), "gpu_launches_timed_region": int(launches),
-            "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+            "roofline": roof, **({"roofline_fp64_sweep": roof_fp64} if roof_fp64 else {}),
+            **({"fp64_time_to_solution": fp64} if fp64 else {}),
+            "measured_peaks": {k: round(val, 4) for k, val in measured.items()},
+            "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+            **({"parity_n200k": parity} if parity else {}),
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

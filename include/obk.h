@@ -233,7 +233,12 @@ OBK_API int32_t obk_get_setup_profile(const obk_handle* h, double* ms, int32_t c
  * tiles of 4096 rows, each summed in a fixed order, then the tiles in index
  * order, so the result does not depend on the device or launch.  Allocates
  * device scratch (two doubles per tile, plus copies of host inputs).
- * Errors: OBK_ERR_INVALID (NULL pointers, m or n <= 0), OBK_ERR_NOMEM, OBK_ERR_CUDA. */
+ * A host-resident A (device_ptrs = 0) is checked first: row_ptr from 0 to nnz
+ * and monotone, every column index in [0, n).  A device-resident A is not
+ * checked (that would need a device pass and a read-back): its row_ptr must be
+ * monotone and every column index in [0, n), or the kernel reads outside x.
+ * Errors: OBK_ERR_INVALID (NULL pointers, m or n <= 0, a malformed host CSR),
+ * OBK_ERR_NOMEM, OBK_ERR_CUDA. */
 OBK_API obk_status obk_residual(const obk_csr* A, int64_t m, int64_t n, const double* f, const double* x,
                                 double* rel_res);
 
@@ -255,8 +260,11 @@ OBK_API obk_status obk_residual(const obk_csr* A, int64_t m, int64_t n, const do
  * device share the array and each call overwrites the slots it reads, so calls
  * whose GPU work overlaps (other streams, threads or processes of the same
  * library instance) race: serialise them.
- * Errors: OBK_ERR_INVALID (NULL or host pointer, m or n <= 0, m too large),
- * OBK_ERR_CUDA. */
+ * Preconditions that are not checked (checking them would need a device pass):
+ * row_ptr monotone from 0, every column index in [0, n).
+ * Errors: OBK_ERR_INVALID (a NULL pointer -- col_idx and val included, even
+ * when A has no entries --, a host pointer or memory of another device, m or
+ * n <= 0, m too large), OBK_ERR_CUDA. */
 OBK_API obk_status obk_residual_noalloc(const int64_t* row_ptr, const int32_t* col_idx, const double* val,
                                         int64_t m, int64_t n, const double* f, const double* x,
                                         double* rel_res, void* stream);
@@ -340,6 +348,25 @@ OBK_API int64_t obk_kernel_launches(void);
 
 /* Library version string. */
 OBK_API const char* obk_version(void);
+
+/* Measured throughput ceilings of the current device, for the rooflines the
+ * sweep is reported against (not part of the method; a measurement helper for
+ * benchmarks).  Each figure is the best of three timed runs (after one warm-up)
+ * of a kernel that does nothing else:
+ *   fp64_fma_tflops / fp32_fma_tflops: eight independent multiply-add chains
+ *       per thread, 2048 threads per SM (2 flop per multiply-add);
+ *   l2_gather_g_per_s: 8-byte loads at pseudo-random positions (an integer
+ *       hash, no index array) of an 8 MB array that stays in L2, in 1e9/s;
+ *   l2_read_gbs: coalesced 32-byte reads of a 32 MB L2-resident array.
+ * Takes about 50 ms; allocates 40 MB of device memory for the duration.
+ * Errors: OBK_ERR_INVALID (out is NULL), OBK_ERR_NOMEM, OBK_ERR_CUDA. */
+typedef struct {
+    double fp64_fma_tflops;
+    double fp32_fma_tflops;
+    double l2_gather_g_per_s;
+    double l2_read_gbs;
+} obk_peaks;
+OBK_API obk_status obk_measure_peaks(obk_peaks* out);
 
 #ifdef __cplusplus
 }

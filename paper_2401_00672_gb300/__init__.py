@@ -28,7 +28,7 @@ EXPORTS = [
     "obk_submit", "obk_poll", "obk_cancel", "obk_server_destroy", "obk_last_error", "obk_version",
     "obk_kernel_launches", "obk_residual", "obk_residual_noalloc", "obk_autotune", "obk_solve_batch",
     "obk_batch_max_n", "obk_get_setup_profile", "obk_grouping_stats", "obk_solve_blocks",
-    "obk_request_footprint",
+    "obk_request_footprint", "obk_measure_peaks",
 ]
 
 
@@ -130,6 +130,7 @@ def _load() -> ctypes.CDLL:
         "obk_grouping_stats": ([vp, vp], ctypes.c_int32),
         "obk_solve_blocks": ([vp, vp, vp, vp, dbl, i64, vp, vp], ctypes.c_int32),
         "obk_request_footprint": ([i64, i64, i64], ctypes.c_size_t),
+        "obk_measure_peaks": ([vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -139,6 +140,18 @@ def _load() -> ctypes.CDLL:
 
 
 lib = _load()
+
+
+class _Peaks(ctypes.Structure):
+    _fields_ = [("fp64_fma_tflops", ctypes.c_double), ("fp32_fma_tflops", ctypes.c_double),
+                ("l2_gather_g_per_s", ctypes.c_double), ("l2_read_gbs", ctypes.c_double)]
+
+
+def measure_peaks() -> dict:
+    """obk_measure_peaks: FP64/FP32 multiply-add rates, L2 gather and read rates."""
+    p = _Peaks()
+    _check(lib.obk_measure_peaks(ctypes.byref(p)), "obk_measure_peaks")
+    return {f[0]: getattr(p, f[0]) for f in _Peaks._fields_}
 
 
 def request_footprint(m: int, n: int, nnz: int) -> int:
@@ -299,14 +312,24 @@ def residual(row_ptr, col_idx, val, m, n, f, x) -> float:
 
 
 def residual_noalloc(row_ptr, col_idx, val, m, n, f, x, out, stream=None) -> int:
-    """obk_residual_noalloc: all arguments are CUDA tensors (out: one float64);
-    queued on `stream` (raw cudaStream_t handle, None = default stream)."""
-    ptrs = []
+    """obk_residual_noalloc: all arguments are CUDA tensors of the current
+    device (out: one float64); queued on `stream` (raw cudaStream_t handle,
+    None = default stream).  An empty col_idx / val (a matrix without entries)
+    is passed as a one-element device buffer: the C entry point rejects NULL."""
+    import torch
+
+    cur = torch.cuda.current_device()
+    ptrs, keep = [], []
     for a, dt in ((row_ptr, np.int64), (col_idx, np.int32), (val, np.float64), (f, np.float64),
                   (x, np.float64), (out, np.float64)):
+        if hasattr(a, "is_cuda") and a.is_cuda and a.numel() == 0:
+            a = torch.zeros(1, dtype=a.dtype, device=a.device)
+            keep.append(a)
         p, dev, _ = _ptr(a, dt)
         if not dev:
             raise TypeError("obk_residual_noalloc takes device arrays only")
+        if a.device.index != cur:
+            raise TypeError(f"obk_residual_noalloc: array on {a.device}, current device is cuda:{cur}")
         ptrs.append(p)
     return _check(lib.obk_residual_noalloc(ptrs[0], ptrs[1], ptrs[2], int(m), int(n), ptrs[3], ptrs[4], ptrs[5],
                                            ctypes.c_void_p(stream) if stream else None), "obk_residual_noalloc")

@@ -18,6 +18,7 @@
 #include "batch.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
+#include "residual.cuh"
 
 namespace obk {
 
@@ -185,43 +186,16 @@ void sum_squares_to(const double* a, const int32_t* idx, int64_t n, int64_t m, d
 }
 
 
-// ---- residual check with per-tile partial sums ----------------------------
-// Tile t covers rows [t*kResTile, (t+1)*kResTile); one block per tile, one warp
-// per row, lanes over the row's entries; the block sums its rows' r^2 and f^2
-// in a fixed order.  part[2t] = sum r^2, part[2t+1] = sum f^2.
-constexpr int kResTile = 4096;
+// ---- residual check with per-tile partial sums (residual.cuh) -------------
 __global__ void residual_tiles(int64_t m, const int64_t* rp, const int32_t* ci, const double* v, const double* f,
                                const double* x, double* part)
 {
-    __shared__ double wr[kBlock / 32], wf[kBlock / 32];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int64_t r0 = (int64_t)blockIdx.x * kResTile, r1 = r0 + kResTile < m ? r0 + kResTile : m;
-    double sr = 0.0, sf = 0.0;
-    for (int64_t i = r0 + w; i < r1; i += kBlock / 32) {
-        double acc = 0.0;
-        for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += 32) acc = fma(v[e], x[ci[e]], acc);
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        double r = f[i] - acc;
-        sr = fma(r, r, sr);
-        sf = fma(f[i], f[i], sf);
-    }
-    if (lane == 0) { wr[w] = sr; wf[w] = sf; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int k = 0; k < kBlock / 32; ++k) { a += wr[k]; b += wf[k]; }
-        part[2 * blockIdx.x] = a;
-        part[2 * blockIdx.x + 1] = b;
-    }
+    residual_tile_sums(m, rp, ci, v, f, x, part, blockIdx.x);
 }
 
 __global__ void residual_final(const double* part, int64_t ntiles, double* out)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int64_t t = 0; t < ntiles; ++t) { a += part[2 * t]; b += part[2 * t + 1]; }
-        *out = b > 0.0 ? sqrt(a) / sqrt(b) : sqrt(a);
-    }
+    if (threadIdx.x == 0 && blockIdx.x == 0) *out = residual_from_tiles(part, ntiles);
 }
 
 bool is_device_ptr(const void* p)
@@ -326,18 +300,7 @@ int tuned_or_rule(const obk_handle* h, int precision)
 }
 }  // namespace
 
-static obk_status fail(const Error& e)
-{
-    set_last_error(e.msg);
-    return (obk_status)e.status;
-}
-
-#define OBK_API_BEGIN try {
-#define OBK_API_END                                                            \
-    }                                                                          \
-    catch (const Error& e) { return fail(e); }                                 \
-    catch (const std::bad_alloc&) { return fail(Error{-2, "host allocation failed"}); } \
-    catch (...) { return fail(Error{-5, "unexpected internal error"}); }
+// OBK_API_BEGIN / OBK_API_END (common.cuh) turn exceptions into statuses at the C boundary.
 
 extern "C" {
 
@@ -853,7 +816,13 @@ obk_status obk_residual(const obk_csr* A, int64_t m, int64_t n, const double* f,
         const int64_t* prp = A->row_ptr;
         const int32_t* pci = A->col_idx;
         const double* pv = A->val;
-        if (!adev) {
+        if (!adev) {  // host-resident CSR: check its structure before any device read
+            if (A->row_ptr[0] != 0 || A->row_ptr[m] != nnz) throw Error{-1, "row_ptr must run from 0 to nnz"};
+            for (int64_t i = 0; i < m; ++i)
+                if (A->row_ptr[i + 1] < A->row_ptr[i]) throw Error{-1, "row_ptr is not monotone"};
+            for (int64_t e = 0; e < nnz; ++e)
+                if (A->col_idx[e] < 0 || (int64_t)A->col_idx[e] >= n)
+                    throw Error{-1, "column index out of range at entry " + std::to_string(e)};
             rp.alloc(m + 1, st);
             ci.alloc(std::max<int64_t>(nnz, 1), st);
             v.alloc(std::max<int64_t>(nnz, 1), st);
@@ -868,7 +837,7 @@ obk_status obk_residual(const obk_csr* A, int64_t m, int64_t n, const double* f,
         const double* px = x;
         if (!fdev) { fd.alloc(m, st); to_device(fd.p, f, m, false, st); pf = fd.p; }
         if (!xdev) { xd.alloc(n, st); to_device(xd.p, x, n, false, st); px = xd.p; }
-        residual_tiles<<<(unsigned)ntiles, kBlock, 0, st>>>(m, prp, pci, pv, pf, px, part.p);
+        residual_tiles<<<(unsigned)ntiles, kResBlock, 0, st>>>(m, prp, pci, pv, pf, px, part.p);
         OBK_CHECK_LAUNCH();
         residual_final<<<1, 32, 0, st>>>(part.p, ntiles, part.p + 2 * ntiles);
         OBK_CHECK_LAUNCH();

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <new>
 #include <string>
 
 namespace obk {
@@ -17,6 +18,23 @@ struct Error {
 };
 
 void set_last_error(const std::string& msg);
+
+// Every extern "C" entry point wraps its body in OBK_API_BEGIN / OBK_API_END:
+// no exception crosses the C boundary; each becomes an obk_status and a
+// message for obk_last_error().
+inline int api_fail(const Error& e)
+{
+    set_last_error(e.msg);
+    return e.status;
+}
+#define OBK_API_BEGIN try {
+#define OBK_API_END                                                                          \
+    }                                                                                        \
+    catch (const ::obk::Error& e) { return (obk_status)::obk::api_fail(e); }                 \
+    catch (const std::bad_alloc&) {                                                          \
+        return (obk_status)::obk::api_fail(::obk::Error{-2, "host allocation failed"});      \
+    }                                                                                        \
+    catch (...) { return (obk_status)::obk::api_fail(::obk::Error{-5, "unexpected internal error"}); }
 
 #define OBK_CUDA(call)                                                                 \
     do {                                                                               \

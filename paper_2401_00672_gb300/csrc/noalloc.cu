@@ -16,11 +16,12 @@
 
 #include "../../include/obk.h"
 #include "common.cuh"
+#include "residual.cuh"
 
 namespace {
 
-constexpr int kBlock = 256;
-constexpr int kTile = 4096;                 // rows per partial sum (as in obk_residual)
+constexpr int kBlock = obk::kResBlock;
+constexpr int kTile = obk::kResTile;        // rows per partial sum (as in obk_residual)
 constexpr int64_t kMaxTiles = 16384;        // -> at most 67,108,864 rows
 constexpr int64_t kMaxRows = kMaxTiles * kTile;
 constexpr int kMaxDevices = 64;
@@ -31,51 +32,34 @@ constexpr int kMaxDevices = 64;
 // stand-in; kernels receive the device address from cudaGetSymbolAddress.
 static __device__ __align__(256) double g_residual_scratch[2 * kMaxTiles];
 
+// The same per-tile body and final sum as obk_residual (residual.cuh), so the
+// two entry points return identical values.
 __global__ void residual_tiles_static(int64_t m, const int64_t* rp, const int32_t* ci, const double* v,
                                       const double* f, const double* x, double* part)
 {
-    __shared__ double wr[kBlock / 32], wf[kBlock / 32];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int64_t r0 = (int64_t)blockIdx.x * kTile, r1 = r0 + kTile < m ? r0 + kTile : m;
-    double sr = 0.0, sf = 0.0;
-    for (int64_t i = r0 + w; i < r1; i += kBlock / 32) {
-        double acc = 0.0;
-        for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += 32) acc = fma(v[e], x[ci[e]], acc);
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        double r = f[i] - acc;
-        sr = fma(r, r, sr);
-        sf = fma(f[i], f[i], sf);
-    }
-    if (lane == 0) { wr[w] = sr; wf[w] = sf; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int k = 0; k < kBlock / 32; ++k) { a += wr[k]; b += wf[k]; }
-        part[2 * blockIdx.x] = a;      // every tile of this call writes both of its
-        part[2 * blockIdx.x + 1] = b;  // slots, so nothing needs clearing first
-    }
+    obk::residual_tile_sums(m, rp, ci, v, f, x, part, blockIdx.x);
 }
 
 __global__ void residual_final_static(const double* part, int64_t ntiles, double* out)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int64_t t = 0; t < ntiles; ++t) { a += part[2 * t]; b += part[2 * t + 1]; }
-        *out = b > 0.0 ? sqrt(a) / sqrt(b) : sqrt(a);
-    }
+    if (threadIdx.x == 0 && blockIdx.x == 0) *out = obk::residual_from_tiles(part, ntiles);
 }
 
 std::mutex g_mu;
 double* g_scratch_of_device[kMaxDevices] = {};
 
-bool on_device(const void* p)
+// True when p is memory that kernels on device `dev` can address directly:
+// device memory of that device, or managed memory.
+bool on_device(const void* p, int dev)
 {
+    if (!p) return false;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         (void)cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -84,26 +68,24 @@ extern "C" obk_status obk_residual_noalloc(const int64_t* row_ptr, const int32_t
                                            int64_t m, int64_t n, const double* f, const double* x,
                                            double* rel_res, void* stream)
 {
-    if (!row_ptr || !f || !x || !rel_res || m <= 0 || n <= 0) {
-        obk::set_last_error("obk_residual_noalloc: NULL pointer or non-positive size");
-        return OBK_ERR_INVALID;
-    }
-    if (m > kMaxRows) {
-        obk::set_last_error("obk_residual_noalloc: m = " + std::to_string(m) + " exceeds the maximum of " +
-                            std::to_string(kMaxRows) + " rows of its fixed scratch");
-        return OBK_ERR_INVALID;
-    }
-    if (!on_device(row_ptr) || !on_device(f) || !on_device(x) || !on_device(rel_res) ||
-        (col_idx && !on_device(col_idx)) || (val && !on_device(val))) {
-        obk::set_last_error("obk_residual_noalloc: every array must be in device memory");
-        return OBK_ERR_INVALID;
-    }
+    OBK_API_BEGIN
+    obk::set_last_error("");
+    if (!row_ptr || !col_idx || !val || !f || !x || !rel_res || m <= 0 || n <= 0)
+        throw obk::Error{OBK_ERR_INVALID, "obk_residual_noalloc: NULL pointer or non-positive size"};
+    if (m > kMaxRows)
+        throw obk::Error{OBK_ERR_INVALID, "obk_residual_noalloc: m = " + std::to_string(m) +
+                                              " exceeds the maximum of " + std::to_string(kMaxRows) +
+                                              " rows of its fixed scratch"};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        obk::set_last_error("obk_residual_noalloc: no usable current device");
-        return OBK_ERR_CUDA;
+        (void)cudaGetLastError();
+        throw obk::Error{OBK_ERR_CUDA, "obk_residual_noalloc: no usable current device"};
     }
+    if (!on_device(row_ptr, dev) || !on_device(col_idx, dev) || !on_device(val, dev) || !on_device(f, dev) ||
+        !on_device(x, dev) || !on_device(rel_res, dev))
+        throw obk::Error{OBK_ERR_INVALID,
+                         "obk_residual_noalloc: every array must be in device memory of the current device"};
     double* scratch = nullptr;
     {
         // set-up, once per device with that device current: the device address
@@ -114,9 +96,8 @@ extern "C" obk_status obk_residual_noalloc(const int64_t* row_ptr, const int32_t
             e = cudaGetSymbolAddress(&p, g_residual_scratch);
             if (e != cudaSuccess || !p) {
                 (void)cudaGetLastError();
-                obk::set_last_error(std::string("obk_residual_noalloc: cudaGetSymbolAddress failed: ") +
-                                    cudaGetErrorString(e));
-                return OBK_ERR_CUDA;
+                throw obk::Error{OBK_ERR_CUDA, std::string("obk_residual_noalloc: cudaGetSymbolAddress failed: ") +
+                                                   cudaGetErrorString(e)};
             }
             g_scratch_of_device[dev] = static_cast<double*>(p);
         }
@@ -129,9 +110,8 @@ extern "C" obk_status obk_residual_noalloc(const int64_t* row_ptr, const int32_t
     residual_final_static<<<1, 32, 0, st>>>(scratch, ntiles, rel_res);
     obk::count_launch();
     e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        obk::set_last_error(std::string("obk_residual_noalloc: launch failed: ") + cudaGetErrorString(e));
-        return OBK_ERR_CUDA;
-    }
+    if (e != cudaSuccess)
+        throw obk::Error{OBK_ERR_CUDA, std::string("obk_residual_noalloc: launch failed: ") + cudaGetErrorString(e)};
     return OBK_OK;
+    OBK_API_END
 }

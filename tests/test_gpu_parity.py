@@ -353,6 +353,37 @@ def test_precision_form_reaches_1e10(obk):
     assert err <= 1e-8, err
 
 
+def test_precision_form_n200k_against_both_oracle_forms(obk):
+    """The precision form on the 4M benchmark recipe at n = 200,000 (seed
+    1003), to rel. residual 1e-10 with 8 FP32 inner sweeps per refinement step
+    on both sides: the GPU result against the FP64 oracle and against the
+    oracle's own precision form.  Both sides stop on the same refinement step;
+    both results have a residual below 1e-10 on a diagonally dominant system
+    (||A^-1|| ||A|| about 5), so they agree with each other and with the FP64
+    solve far inside the FP64 parity bound."""
+    import torch
+
+    s = synth.knn_dominant(200_000, 12, seed=1003)
+    A = s.A
+    _, x64, _ = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1, tol=1e-10, maxit=20000,
+                             check_every=-1)
+    st32, x32, i32 = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1, tol=1e-10, maxit=20000,
+                                  precision=1, inner_sweeps=8)
+    assert st32 == oracle.OK
+    dev = torch.device("cuda")
+    with obk.Handle(torch.from_numpy(A.row_ptr).to(dev), torch.from_numpy(A.col_idx).to(dev),
+                    torch.from_numpy(A.val).to(dev), A.m, A.n, thr=0.1) as h:
+        out = torch.empty(A.n, dtype=torch.float64, device=dev)
+        st, _, info = h.solve(torch.from_numpy(s.f).to(dev), tol=1e-10, maxit=20000, out=out,
+                              opts=obk.Opts(precision=1, inner_sweeps=8))
+        x = out.cpu().numpy()
+    assert st == obk.OBK_OK and info.rel_res <= 1e-10
+    assert info.outer_iters == i32.outer_iters and info.sweeps == i32.sweeps
+    e64 = np.linalg.norm(x - x64) / np.linalg.norm(x64)
+    e32 = np.linalg.norm(x - x32) / np.linalg.norm(x32)
+    assert e64 <= XTOL and e32 <= XTOL, (e64, e32)
+
+
 def test_overdetermined_inconsistent_stagnates(obk):
     s = synth.rect_random(3000, 1000, 10, seed=12, noise=1e-3)
     A = s.A
@@ -417,38 +448,57 @@ def test_bounded_wait_times_out_and_context_survives(obk):
         assert st == obk.OBK_OK
 
 
-def test_request_loop_alone_equals_mixed(obk):
-    systems = [synth.random_dominant(n, 7, seed=900 + k) for k, n in enumerate((1200, 3000, 800, 5000))]
-    systems += [synth.rect_random(2 * n, n, 10, seed=950 + k) for k, n in enumerate((700, 1500))]
-    alone = []
-    for s in systems:
-        A = s.A
-        st, x, info = obk.solve(A.row_ptr, A.col_idx, A.val, A.m, A.n, s.f, tol=1e-8, maxit=5000)
-        alone.append((st, x))
-    srv = obk.Server(hbm_budget_bytes=0, max_streams=4)
-    tickets = []
-    for k, s in enumerate(systems):
-        A = s.A
-        opts = obk.Opts(precision=0)
-        tickets.append(srv.submit(A.row_ptr, A.col_idx, A.val, A.m, A.n, s.f, tol=1e-8, maxit=5000, opts=opts))
+def _serve(obk, srv, reqs, limit_s=300):
+    """Submit every (system, opts) of reqs to srv at once; wait for all results."""
     import time
 
+    tickets = []
+    for s, o in reqs:
+        A = s.A
+        tickets.append(srv.submit(A.row_ptr, A.col_idx, A.val, A.m, A.n, s.f, tol=1e-8, maxit=20000, opts=o))
     results = {}
     t0 = time.time()
-    while len(results) < len(tickets) and time.time() - t0 < 120:
-        for t, s in zip(tickets, systems):
+    while len(results) < len(tickets) and time.time() - t0 < limit_s:
+        for t, (s, _) in zip(tickets, reqs):
             if t in results:
                 continue
             st, x, info = srv.poll(t, s.A.n)
             if st != obk.OBK_PENDING:
-                results[t] = (st, x)
-        time.sleep(0.01)
+                results[t] = (st, x, info)
+        time.sleep(0.005)
+    assert len(results) == len(tickets), "requests did not finish"
+    return [results[t] for t in tickets]
+
+
+def test_request_loop_alone_equals_mixed(obk):
+    """Each request's result is the same whether it runs alone in the request
+    loop or mixed with others that overlap it on the device: small square
+    systems (the one-block batch path), overdetermined (Algorithm 5) and
+    underdetermined (Algorithm 6) systems, FP64 and FP32 + FP64 refinement
+    requests, and kNN systems of 60,000 and 120,000 rows that take the
+    cooperative grid path while the small ones run."""
+    P64, P32 = obk.Opts(precision=0), obk.Opts(precision=1)
+    reqs = []
+    for k, n in enumerate((1200, 3000, 800, 5000)):
+        reqs.append((synth.random_dominant(n, 7, seed=900 + k), P64 if k % 2 == 0 else P32))
+    for k, n in enumerate((700, 1500)):
+        reqs.append((synth.rect_random(2 * n, n, 10, seed=950 + k), P32 if k == 0 else P64))
+    for k, n in enumerate((4000, 9000)):
+        reqs.append((synth.rect_random(n // 2, n, 10, seed=970 + k, full_columns=False), P64 if k == 0 else P32))
+    reqs.append((synth.knn_dominant(60_000, 12, seed=980), P32))
+    reqs.append((synth.knn_dominant(120_000, 12, seed=981), P64))
+    alone = []
+    for r in reqs:
+        srv = obk.Server(hbm_budget_bytes=0, max_streams=4)
+        alone.append(_serve(obk, srv, [r])[0])
+        srv.close()
+    srv = obk.Server(hbm_budget_bytes=0, max_streams=4)
+    mixed = _serve(obk, srv, reqs)
     srv.close()
-    assert len(results) == len(tickets)
-    for t, (st_a, x_a) in zip(tickets, alone):
-        st_m, x_m = results[t]
-        assert st_m == st_a
-        assert np.linalg.norm(x_m - x_a) <= XTOL * np.linalg.norm(x_a)
+    for k, ((st_a, x_a, i_a), (st_m, x_m, i_m)) in enumerate(zip(alone, mixed)):
+        assert st_a == st_m == obk.OBK_OK, (k, st_a, st_m)
+        assert i_m.sweeps == i_a.sweeps, (k, i_a.sweeps, i_m.sweeps)
+        assert np.linalg.norm(x_m - x_a) <= XTOL * np.linalg.norm(x_a), k
 
 
 def _wait(srv, ticket, n, limit_s=120):

@@ -213,6 +213,33 @@ def test_precision_form_reaches_1e10_and_matches_fp64():
     assert np.linalg.norm(x - x64) <= 1e-8 * np.linalg.norm(x64)
 
 
+def test_refinement_step_gains_fp32_precision_on_diagonal_system():
+    """Pin of the precision form's outer step against what the arithmetic
+    fixes.  For a diagonal A every row is one group, so one FP32 sweep solves
+    A d = r / beta up to FP32 rounding: the right-hand side (float)(r / beta),
+    the FP32 inverse norm and the product each carry a relative error of at
+    most 2^-24, so after x += beta d the new residual is at most about
+    4 * 2^-24 of the old one, until the FP64 floor (~1e-16).  A residual or a
+    correction accumulated in FP32 would stall near 1e-7; a dropped beta or a
+    wrong sign would not contract at all."""
+    rng = np.random.default_rng(15)
+    n = 4000
+    d = rng.uniform(0.5, 3.0, n) * rng.choice([-1.0, 1.0], n)
+    A = synth.csr_from_coo(n, n, np.arange(n), np.arange(n), d)
+    f = d * rng.standard_normal(n)
+    rr = [1.0]
+    for outer in (1, 2, 3):
+        st, x, info = oracle.solve(n, n, A.row_ptr, A.col_idx, A.val, f, tol=1e-300, maxit=100, precision=1,
+                                   inner_sweeps=1, max_outer=outer)
+        assert info.outer_iters == outer and info.sweeps == outer
+        rr.append(info.rel_res)
+    bound = 4 * 2.0 ** -24
+    assert rr[1] <= bound, rr
+    assert rr[2] <= max(bound * rr[1], 1e-15), rr
+    assert rr[3] <= 1e-15, rr
+    assert np.linalg.norm(x - f / d) <= 1e-15 * np.linalg.norm(f / d)
+
+
 def test_validate_rejects_bad_csr():
     rp = np.array([0, 2, 3], np.int64)
     assert oracle.validate(2, 2, rp, np.array([0, 1, 1], np.int32), np.ones(3)) == 0
