@@ -541,7 +541,7 @@ def blocks_study(args):
                       "rows": rows}), flush=True)
 
 
-def sweep_time(obk, h, f, x, stream, precision, rpw=0):
+def sweep_time(obk, h, f, x, stream, precision, rpw=0, sync_mode=0, staging=0):
     """Device time of one sweep of the prepared system h: two solves with a
     residual only at their start and end, 10 and 60 sweeps (FP64), or one
     refinement step of 10 and 60 FP32 inner sweeps (precision form); the
@@ -551,9 +551,10 @@ def sweep_time(obk, h, f, x, stream, precision, rpw=0):
     per = {}
     for k in (10, 60):
         if precision == 1:
-            o = obk.Opts(precision=1, inner_sweeps=k, max_outer=1, rows_per_warp=rpw)
+            o = obk.Opts(precision=1, inner_sweeps=k, max_outer=1, rows_per_warp=rpw, sync_mode=sync_mode,
+                         staging=staging)
         else:
-            o = obk.Opts(check_every=1 << 30, rows_per_warp=rpw)
+            o = obk.Opts(check_every=1 << 30, rows_per_warp=rpw, sync_mode=sync_mode, staging=staging)
         best = None
         for _ in range(3):
             e0 = torch.cuda.Event(enable_timing=True)
@@ -640,6 +641,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison and the n=200k parity")
     ap.add_argument("--sweep-probe", action="store_true",
                     help="only the 10- and 60-sweep solves of the roofline (for an ncu capture)")
+    ap.add_argument("--sync-mode", type=int, default=0, help="sweep-probe: 0 band-local waits, 1 grid barriers")
+    ap.add_argument("--staging", type=int, default=0, help="sweep-probe: 1 = staged windows")
     ap.add_argument("--precision-study", action="store_true", help="FP64 vs FP32+IR to 1e-10 (extra run)")
     ap.add_argument("--pn", type=int, default=4_000_000, help="n of the precision study")
     ap.add_argument("--serving", action="store_true", help="request-loop throughput and latency (extra run)")
@@ -709,8 +712,8 @@ def main():
     if args.sweep_probe:  # two launches of the sweep kernel on a prepared system
         h = obk.Handle(rp, ci, v, A.m, A.n, thr=cfg["thr"], stream=stream.cuda_stream)
         for k in (10, 60):
-            o = (obk.Opts(precision=1, inner_sweeps=k, max_outer=1) if prec == 1
-                 else obk.Opts(check_every=1 << 30))
+            o = (obk.Opts(precision=1, inner_sweeps=k, max_outer=1, sync_mode=args.sync_mode, staging=args.staging)
+                 if prec == 1 else obk.Opts(check_every=1 << 30, sync_mode=args.sync_mode, staging=args.staging))
             h.solve(f, None, tol=1e-300, maxit=k, out=x, opts=o)
         torch.cuda.synchronize()
         h.close()
@@ -800,10 +803,14 @@ def main():
     sw_ms = sweep_time(obk, h, f, x, stream, prec)  # the default choice, as the timed solve runs it
     roof = roofline_of(sw_ms, nnz_gm, N, prec, hbm_peak, hbm_src, measured, sweep_traffic(args.workload))
     roof["sweep_ms_by_rows_per_warp"] = by_rpw
+    roof["sweep_ms_grid_barriers"] = round(sweep_time(obk, h, f, x, stream, prec, sync_mode=1), 5)
+    roof["sweep_ms_staged_windows"] = round(sweep_time(obk, h, f, x, stream, prec, staging=1), 5)
     roof_fp64 = None
     if prec == 1:
         sw64 = sweep_time(obk, h, f, x, stream, 0)
         roof_fp64 = roofline_of(sw64, nnz_gm, N, 0, hbm_peak, hbm_src, measured, None)
+        roof_fp64["sweep_ms_grid_barriers"] = round(sweep_time(obk, h, f, x, stream, 0, sync_mode=1), 5)
+        roof_fp64["sweep_ms_staged_windows"] = round(sweep_time(obk, h, f, x, stream, 0, staging=1), 5)
     h.close()
 
     e2e = None

@@ -91,6 +91,21 @@ typedef struct {
                                group; the steps converge when every row's sum of |cos|
                                to the rest of its group is below one.  Ignored by
                                precision 1.  Negative values are OBK_ERR_INVALID.     */
+    int32_t sync_mode;      /* ordering of the group steps on the device: 0 (default) =
+                               band-local step counters: after RCM a block's rows and
+                               columns touch only nearby blocks' tiles, so each phase
+                               waits only for those blocks to finish the earlier
+                               phases (same arithmetic, same results); 1 = a grid-wide
+                               barrier after every phase.  pinv_iters > 0 and
+                               rows_per_warp < 32 always use barriers.               */
+    int32_t staging;        /* where the band-local sweep reads x and y: 0 (default) or 2 =
+                               gathers from global memory through L1 and L2; 1 = each
+                               step copies the window it reads (x for the columns of the
+                               block's band, y for the group's rows in it) into shared
+                               memory when the window fits and holds no more values
+                               than the step's gathers (the shared memory this takes is
+                               no longer L1, which the other steps' gathers lose).  Same
+                               results either way.                                    */
 } obk_opts;
 
 typedef struct {

@@ -48,7 +48,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("inner_sweeps", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("stagnation", ctypes.c_double), ("timeout_spins", ctypes.c_int64),
-                ("rows_per_warp", ctypes.c_int32), ("pinv_iters", ctypes.c_int32)]
+                ("rows_per_warp", ctypes.c_int32), ("pinv_iters", ctypes.c_int32),
+                ("sync_mode", ctypes.c_int32), ("staging", ctypes.c_int32)]
 
 
 class _GStats(ctypes.Structure):

@@ -441,6 +441,8 @@ obk_status obk_solve_ex(obk_handle* h, const obk_opts* opts, const double* f, co
     if (o.check_every < -1 || o.inner_sweeps < 0 || o.max_outer < 0 || o.timeout_spins < 0)
         throw Error{-1, "negative option"};
     if (o.pinv_iters < 0) throw Error{-1, "pinv_iters must be >= 0"};
+    if (o.sync_mode != 0 && o.sync_mode != 1) throw Error{-1, "sync_mode must be 0 or 1"};
+    if (o.staging < 0 || o.staging > 2) throw Error{-1, "staging must be 0, 1 or 2"};
     if (o.rows_per_warp != 0 && o.rows_per_warp != 1 && o.rows_per_warp != 2 && o.rows_per_warp != 4 &&
         o.rows_per_warp != 8 && o.rows_per_warp != 16 && o.rows_per_warp != 32)
         throw Error{-1, "rows_per_warp must be 0, 1, 2, 4, 8, 16 or 32"};
@@ -495,6 +497,8 @@ obk_status obk_solve_ex(obk_handle* h, const obk_opts* opts, const double* f, co
     a.spin_limit = o.timeout_spins > 0 ? o.timeout_spins : kDefaultSpins;
     a.sub = o.rows_per_warp > 0 ? 32 / o.rows_per_warp : tuned_or_rule(h, o.precision);
     a.pinv_iters = o.precision == 0 ? o.pinv_iters : 0;
+    a.sync_mode = o.sync_mode;
+    a.staging = o.staging;
     if (a.pinv_iters > 0 && !h->L.has_gram) build_group_gram(h->L, h->err.p, st);
     SolveResult r = run_solve(h->L, fgm.p, fnorm2, zero_f2, xt.p, a, h->err.p, st);
     // x = P^T x~, then x^(1:n)

@@ -129,6 +129,22 @@ struct SweepLayout {
     DBuf<int32_t> mrow;              // msell_nnz, group-major row index
     DBuf<double> mv;                 // msell_nnz
     DBuf<float> mv32;                // msell_nnz
+    // Tiles: T ranges of B consecutive permuted rows (and columns).  The layout
+    // is ordered by (group, tile) first: rows of group g in tile t are the
+    // group-major rows [gt_ptr[g*T + t], gt_ptr[g*T + t + 1]) and their slices
+    // [sl_tptr[g*T + t], sl_tptr[g*T + t + 1]); the mirror segments of the
+    // columns of tile t likewise (gts_ptr, ml_tptr).  reach_lo/hi[t] = the
+    // lowest/highest tile with a column of a row of tile t or a row of a column
+    // of tile t (t itself included): the tiles whose work a step of tile t
+    // depends on.
+    int64_t T = 1, B = 1;
+    DBuf<int64_t> gt_ptr, gts_ptr;          // G*T + 1 (device)
+    std::vector<int64_t> h_sl_tptr, h_ml_tptr;  // G*T + 1
+    DBuf<int64_t> sl_tptr, ml_tptr;         // device copies
+    DBuf<int32_t> reach_lo, reach_hi;       // T
+    // largest staging windows of a one-tile block: x columns of its reach, and
+    // group-major rows of one group in its reach
+    int64_t xwin_max = 0, ywin_max = 0;
     // permuted-order results kept for inspection
     DBuf<double> nsq;       // N
     DBuf<int32_t> group_of; // N
@@ -190,6 +206,8 @@ struct SolveArgs {
     int64_t maxit = 1000;
     long long spin_limit = kDefaultSpins;
     int sub = 0;  // lanes per row (0 = choose)
+    int sync_mode = 0;  // 0 = band-local step counters between the phases, 1 = grid barriers
+    int staging = 0;    // band-local sweep: 1 = x and y windows in shared memory when worth it, 0 or 2 = never
 };
 
 struct SolveResult {
@@ -206,6 +224,11 @@ double time_sweep(const SweepLayout& L, int sub, int precision, int* d_err, cuda
 
 // Lanes per row chosen by the fixed rule from the mean row length.
 int choose_sub(double avg_row);
+
+// Number of tiles of the sweep layout of an N-row system on the current device:
+// the thread blocks of the persistent sweep (each owns one tile), fewer for
+// small systems (one per 4096 rows).
+int64_t sweep_tiles(int64_t N);
 
 // x (N, permuted order) is updated in place; f_gm (Ngm) is f in group-major
 // order; fnorm2 = ||f~||^2 and zero_f2 = sum of f_i^2 over all-zero rows.

@@ -541,31 +541,83 @@ __global__ void max_color(int64_t N, const int32_t* color, int* gmax)
 
 // ---- group layout -------------------------------------------------------------
 
-// Row order of the sweep layout: by group, then by row length, then by index
-// (stable sort on (group, length) over rows in index order).  Equal lengths
-// inside a warp keep every lane of every FP64 instruction busy.
-// Rows (and column segments) of a group are ordered by length in buckets of
-// 2^kLenBucketShift, then by index: slices of 32 stay nearly free of padding
-// while neighbouring lanes keep nearby indices (and so nearby columns).
+// Row order of the sweep layout: by group, then by tile (a fixed range of
+// B consecutive permuted rows; the sweep gives each thread block the tiles of
+// one contiguous range, so that a block's rows of every group touch one band of
+// x), then by row length, then by index (stable sort on (group, tile, length)
+// over rows in index order).  Equal lengths inside a warp keep every lane of
+// every FP64 instruction busy.  Rows (and column segments, by the tile of their
+// column) are ordered by length in buckets of 2^kLenBucketShift, then by
+// index: slices of 32 stay nearly free of padding while neighbouring lanes keep
+// nearby indices (and so nearby columns).
 constexpr int kLenBucketShift = 1;
 
-__global__ void color_keys(int64_t N, const int32_t* color, const int64_t* rp, int32_t G, int lbits,
-                           uint64_t* keys, uint32_t* vals)
+// key = ((group * T + tile) << lbits) | length class; rows of no group take group G
+__global__ void color_keys(int64_t N, const int32_t* color, const int64_t* rp, int32_t G, int64_t tile_rows,
+                           int64_t T, int lbits, uint64_t* keys, uint32_t* vals)
 {
     GRID_STRIDE(i, N)
     {
         uint64_t g = (uint64_t)(color[i] >= 0 ? color[i] : G);
         uint64_t len = (uint64_t)(rp[i + 1] - rp[i]) >> kLenBucketShift;
         uint64_t lmax = (1ull << lbits) - 1;
-        keys[i] = (g << lbits) | (len < lmax ? len : lmax);
+        uint64_t seg = g * (uint64_t)T + (uint64_t)(i / tile_rows);
+        keys[i] = (seg << lbits) | (len < lmax ? len : lmax);
         vals[i] = (uint32_t)i;
     }
 }
 
-// Segment order inside each group: by length, then by column (stable sort of
-// the (group, column)-ordered segments on (group, length)).
-__global__ void seg_keys(int64_t nseg, const int64_t* seg_ptr, const int64_t* gseg_ptr, int64_t G, int lbits,
-                         uint64_t* keys, uint32_t* vals)
+// ptr[s] = first position k of the sorted keys with (keys[k] >> shift) >= s,
+// for s in [0, nseg]; keys at or beyond segment nseg (rows of no group) count
+// as nseg.  Each entry of ptr is written by exactly one k.
+__global__ void segment_starts(int64_t n, const uint64_t* keys, int shift, int64_t nseg, int64_t* ptr)
+{
+    GRID_STRIDE(k, n + 1)
+    {
+        int64_t lo = k == 0 ? 0 : (int64_t)(keys[k - 1] >> shift) + 1;
+        int64_t hi = k == n ? nseg : (int64_t)(keys[k] >> shift);
+        if (hi > nseg) hi = nseg;
+        for (int64_t q = lo; q <= hi; ++q) ptr[q] = k;
+    }
+}
+
+// Dependency reach of each tile of rows/columns [t * B, (t + 1) * B): the
+// lowest and highest tile holding a column of one of its rows or a row of one
+// of its columns (the tile itself included).  One block per tile.
+__global__ void tile_reach(int64_t N, int64_t B, const int64_t* rp, const int32_t* ci, const int64_t* cptr,
+                           const int32_t* crow, int32_t* reach_lo, int32_t* reach_hi)
+{
+    __shared__ int64_t slo[kBlock / 32], shi[kBlock / 32];
+    int64_t t = blockIdx.x;
+    int64_t k0 = t * B, k1 = k0 + B < N ? k0 + B : N;
+    int64_t lo = t, hi = t;
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        if (rp[k + 1] > rp[k]) {  // columns ascend inside a row
+            lo = min(lo, (int64_t)ci[rp[k]] / B);
+            hi = max(hi, (int64_t)ci[rp[k + 1] - 1] / B);
+        }
+        if (cptr[k + 1] > cptr[k]) {  // rows ascend inside a column
+            lo = min(lo, (int64_t)crow[cptr[k]] / B);
+            hi = max(hi, (int64_t)crow[cptr[k + 1] - 1] / B);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) { slo[threadIdx.x >> 5] = lo; shi[threadIdx.x >> 5] = hi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { lo = min(lo, slo[w]); hi = max(hi, shi[w]); }
+        reach_lo[t] = (int32_t)lo;
+        reach_hi[t] = (int32_t)hi;
+    }
+}
+
+// Segment order inside each group: by tile of the column, then by length,
+// then by column (stable sort of the (group, column)-ordered segments).
+__global__ void seg_keys(int64_t nseg, const int64_t* seg_ptr, const int64_t* gseg_ptr, const int32_t* seg_col,
+                         int64_t G, int64_t tile_rows, int64_t T, int lbits, uint64_t* keys, uint32_t* vals)
 {
     GRID_STRIDE(t, nseg)
     {
@@ -578,7 +630,8 @@ __global__ void seg_keys(int64_t nseg, const int64_t* seg_ptr, const int64_t* gs
         }
         uint64_t len = (uint64_t)(seg_ptr[t + 1] - seg_ptr[t]) >> kLenBucketShift;
         uint64_t lmax = (1ull << lbits) - 1;
-        keys[t] = ((uint64_t)lo << lbits) | (len < lmax ? len : lmax);
+        uint64_t sq = (uint64_t)lo * (uint64_t)T + (uint64_t)(seg_col[t] / tile_rows);
+        keys[t] = (sq << lbits) | (len < lmax ? len : lmax);
         vals[t] = (uint32_t)t;
     }
 }
@@ -777,8 +830,8 @@ __global__ void mirror_segments(int64_t M, const uint32_t* order, const int32_t*
 
 // ---- sliced ELL (SELL-32) copies of the group-major rows and the mirror ----------
 
-// 32 * (longest row of the slice) for every slice; slices of group g start at
-// slice index sg[g]
+// 32 * (longest row of the slice) for every slice; slices of segment q (a
+// group, or a (group, tile) pair) start at slice index sg[q], its items at item_g[q]
 __global__ void sell_lengths(int64_t ns, int64_t G, const int64_t* sg, const int64_t* item_g,
                              const int64_t* ptr, int64_t* slen, int64_t* row0, int32_t* nrow)
 {
@@ -800,11 +853,14 @@ __global__ void sell_lengths(int64_t ns, int64_t G, const int64_t* sg, const int
     }
 }
 
-// entries of slice s, lane l: item row0[s] + l (rows) with the padding zeros
+// entries of slice s, lane l: item row0[s] + l (rows) with the padding zeros.
+// A padding entry (value 0) repeats the lane's last index, or the first index
+// of the slice's first item for a lane without an item, so that its load
+// stays inside the band the slice's step waits for.
 template <class TI>
 __global__ void sell_fill(int64_t ns, const int64_t* sl_ptr, const int64_t* row0, const int32_t* nrow,
                           const int64_t* ptr, const TI* idx, const double* val, TI* sidx, double* sval,
-                          float* sval32, TI pad_idx)
+                          float* sval32)
 {
     GRID_STRIDE(t, ns * 32)
     {
@@ -814,6 +870,7 @@ __global__ void sell_fill(int64_t ns, const int64_t* sl_ptr, const int64_t* row0
         bool valid = lane < nrow[s];
         int64_t k = row0[s] + lane;
         int64_t b = valid ? ptr[k] : 0, rl = valid ? ptr[k + 1] - b : 0;
+        TI pad_idx = rl > 0 ? idx[b + rl - 1] : idx[ptr[row0[s]]];
         for (int64_t j = 0; j < len; ++j) {
             int64_t q = base + 32 * j + lane;
             bool live = j < rl;
@@ -1077,36 +1134,37 @@ void build_group_gram(SweepLayout& L, int* d_err, cudaStream_t st)
     L.has_gram = true;
 }
 
-namespace {
-
-// slices of each group: host prefix over the (few) groups
-std::vector<int64_t> slice_starts(const std::vector<int64_t>& item_g)
-{
-    int64_t G = (int64_t)item_g.size() - 1;
-    std::vector<int64_t> sg(G + 1, 0);
-    for (int64_t g = 0; g < G; ++g) sg[g + 1] = sg[g] + ceil_div(item_g[g + 1] - item_g[g], (int64_t)32);
-    return sg;
-}
-
-}  // namespace
-
+// Sliced copies of the group-major rows and of the mirror segments: slices of
+// 32 are cut inside each (group, tile) segment, so the slices of one block's
+// tiles are contiguous in every group.
 void build_sell(SweepLayout& L, bool want_fp32, cudaStream_t st)
 {
-    int64_t G = L.G;
+    int64_t G = L.G, T = L.T, nsegs = G * T;
+    // first slice of each group (slice index of segment g * T)
+    L.h_sl_gptr.resize(G + 1);
+    L.h_ml_gptr.resize(G + 1);
+    for (int64_t g = 0; g <= G; ++g) {
+        L.h_sl_gptr[g] = L.h_sl_tptr[g * T];
+        L.h_ml_gptr[g] = L.h_ml_tptr[g * T];
+    }
+    auto upload = [&](DBuf<int64_t>& d, const std::vector<int64_t>& h) {
+        d.alloc(h.size(), st);
+        OBK_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    };
+    upload(L.sl_gptr, L.h_sl_gptr);
+    upload(L.ml_gptr, L.h_ml_gptr);
+    upload(L.sl_tptr, L.h_sl_tptr);
+    upload(L.ml_tptr, L.h_ml_tptr);
     // rows
-    L.h_sl_gptr = slice_starts(L.h_gptr);
-    int64_t ns = L.h_sl_gptr[G];
+    int64_t ns = L.h_sl_tptr[nsegs];
     L.ns = ns;
-    L.sl_gptr.alloc(G + 1, st);
-    DBuf<int64_t>& sg = L.sl_gptr;
     DBuf<int64_t> slen(std::max<int64_t>(ns, 1), st);
-    OBK_CUDA(cudaMemcpyAsync(sg.p, L.h_sl_gptr.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     L.sl_ptr.alloc(ns + 1, st);
     L.sl_row0.alloc(std::max<int64_t>(ns, 1), st);
     L.sl_nrow.alloc(std::max<int64_t>(ns, 1), st);
     if (ns) {
-        sell_lengths<<<grid_for(ns), kBlock, 0, st>>>(ns, G, sg.p, L.gptr.p, L.grp_rp.p, slen.p, L.sl_row0.p,
-                                                      L.sl_nrow.p);
+        sell_lengths<<<grid_for(ns), kBlock, 0, st>>>(ns, nsegs, L.sl_tptr.p, L.gt_ptr.p, L.grp_rp.p, slen.p,
+                                                      L.sl_row0.p, L.sl_nrow.p);
         OBK_CHECK_LAUNCH();
     }
     exclusive_scan_i64(slen.p, L.sl_ptr.p, ns, st);
@@ -1117,22 +1175,18 @@ void build_sell(SweepLayout& L, bool want_fp32, cudaStream_t st)
     if (ns) {
         sell_fill<int32_t><<<grid_for(ns * 32), kBlock, 0, st>>>(ns, L.sl_ptr.p, L.sl_row0.p, L.sl_nrow.p,
                                                                  L.grp_rp.p, L.grp_ci.p, L.grp_v.p, L.sci.p,
-                                                                 L.sv.p, want_fp32 ? L.sv32.p : nullptr, 0);
+                                                                 L.sv.p, want_fp32 ? L.sv32.p : nullptr);
         OBK_CHECK_LAUNCH();
     }
     // mirror segments
-    L.h_ml_gptr = slice_starts(L.h_gseg_ptr);
-    int64_t nms = L.h_ml_gptr[G];
+    int64_t nms = L.h_ml_tptr[nsegs];
     L.nms = nms;
-    L.ml_gptr.alloc(G + 1, st);
-    DBuf<int64_t>& mg = L.ml_gptr;
     DBuf<int64_t> mlen(std::max<int64_t>(nms, 1), st), mrow0(std::max<int64_t>(nms, 1), st);
     DBuf<int32_t> mnrow(std::max<int64_t>(nms, 1), st);
-    OBK_CUDA(cudaMemcpyAsync(mg.p, L.h_ml_gptr.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     L.ml_ptr.alloc(nms + 1, st);
     if (nms) {
-        sell_lengths<<<grid_for(nms), kBlock, 0, st>>>(nms, G, mg.p, L.gseg_ptr.p, L.seg_ptr.p, mlen.p, mrow0.p,
-                                                       mnrow.p);
+        sell_lengths<<<grid_for(nms), kBlock, 0, st>>>(nms, nsegs, L.ml_tptr.p, L.gts_ptr.p, L.seg_ptr.p, mlen.p,
+                                                       mrow0.p, mnrow.p);
         OBK_CHECK_LAUNCH();
     }
     exclusive_scan_i64(mlen.p, L.ml_ptr.p, nms, st);
@@ -1146,7 +1200,7 @@ void build_sell(SweepLayout& L, bool want_fp32, cudaStream_t st)
         OBK_CHECK_LAUNCH();
         sell_fill<int32_t><<<grid_for(nms * 32), kBlock, 0, st>>>(nms, L.ml_ptr.p, mrow0.p, mnrow.p, L.seg_ptr.p,
                                                                   L.mir_row.p, L.mir_val.p, L.mrow.p, L.mv.p,
-                                                                  want_fp32 ? L.mv32.p : nullptr, 0);
+                                                                  want_fp32 ? L.mv32.p : nullptr);
         OBK_CHECK_LAUNCH();
     }
 }
@@ -1256,27 +1310,55 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
     conf_off.release();
 
     mark();
-    // 5. group-major rows
+    // 5. group-major rows, ordered by (group, tile, length, index)
+    const int64_t T = sweep_tiles(N);
+    const int64_t B = ceil_div(N, T);
+    L.T = T;
+    L.B = B;
+    const int64_t nsegs = (int64_t)G * T;
+    const int sbits = bits_for((uint64_t)(nsegs + T));  // (group, tile) index, rows of no group included
     DBuf<uint64_t> gk(N, st);
     DBuf<uint32_t> gorder(N, st);
     // length classes: every length up to the longest row (capped at 1023, longer
     // rows share the last class)
     int lbits = std::min(10, bits_for((uint64_t)max_segment_length(N, rp, st)));
-    color_keys<<<grid_for(N), kBlock, 0, st>>>(N, L.group_of.p, rp, G, lbits, gk.p, gorder.p);
+    color_keys<<<grid_for(N), kBlock, 0, st>>>(N, L.group_of.p, rp, G, B, T, lbits, gk.p, gorder.p);
     OBK_CHECK_LAUNCH();
-    radix_sort_pairs(gk.p, gorder.p, N, bits_for((uint64_t)G) + lbits, st);
+    radix_sort_pairs(gk.p, gorder.p, N, sbits + lbits, st);
+    DBuf<int64_t> gt_ptr(nsegs + 1, st);
+    segment_starts<<<grid_for(N + 1), kBlock, 0, st>>>(N, gk.p, lbits, nsegs, gt_ptr.p);
+    OBK_CHECK_LAUNCH();
     gk.release();
-    DBuf<int64_t> gcnt(G + 1, st);
-    OBK_CUDA(cudaMemsetAsync(gcnt.p, 0, (G + 1) * sizeof(int64_t), st));
-    group_hist<<<grid_for(N), kBlock, 0, st>>>(N, L.group_of.p, gcnt.p);
-    OBK_CHECK_LAUNCH();
-    L.gptr.alloc(G + 1, st);
-    exclusive_scan_i64(gcnt.p, L.gptr.p, G, st);
-    L.h_gptr.resize(G + 1);
-    OBK_CUDA(cudaMemcpyAsync(L.h_gptr.data(), L.gptr.p, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    std::vector<int64_t> h_gt(nsegs + 1);
+    OBK_CUDA(cudaMemcpyAsync(h_gt.data(), gt_ptr.p, (nsegs + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     OBK_CUDA(cudaStreamSynchronize(st));
+    L.h_gptr.resize(G + 1);
+    for (int64_t g = 0; g <= G; ++g) L.h_gptr[g] = h_gt[g * T];
+    L.gptr.alloc(G + 1, st);
+    OBK_CUDA(cudaMemcpyAsync(L.gptr.p, L.h_gptr.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     int64_t Ngm = L.h_gptr[G];
     L.Ngm = Ngm;
+    // slices of 32 rows inside each (group, tile) segment
+    L.h_sl_tptr.assign(nsegs + 1, 0);
+    for (int64_t q = 0; q < nsegs; ++q) L.h_sl_tptr[q + 1] = L.h_sl_tptr[q] + ceil_div(h_gt[q + 1] - h_gt[q], (int64_t)32);
+    L.gt_ptr = std::move(gt_ptr);
+    // tile dependency reach (rows of the tile -> tiles of their columns, and back)
+    L.reach_lo.alloc(T, st);
+    L.reach_hi.alloc(T, st);
+    tile_reach<<<(unsigned)T, kBlock, 0, st>>>(N, B, rp, ci, cptr.p, crow.p, L.reach_lo.p, L.reach_hi.p);
+    OBK_CHECK_LAUNCH();
+    {
+        std::vector<int32_t> hlo(T), hhi(T);
+        OBK_CUDA(cudaMemcpyAsync(hlo.data(), L.reach_lo.p, T * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        OBK_CUDA(cudaMemcpyAsync(hhi.data(), L.reach_hi.p, T * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        OBK_CUDA(cudaStreamSynchronize(st));
+        L.xwin_max = L.ywin_max = 0;
+        for (int64_t t = 0; t < T; ++t) {
+            L.xwin_max = std::max<int64_t>(L.xwin_max, std::min<int64_t>((int64_t)(hhi[t] + 1) * B, N) - (int64_t)hlo[t] * B);
+            for (int64_t g = 0; g < G; ++g)
+                L.ywin_max = std::max<int64_t>(L.ywin_max, h_gt[g * T + hhi[t] + 1] - h_gt[g * T + hlo[t]]);
+        }
+    }
     DBuf<int32_t> gm_of_row(N, st);
     OBK_CUDA(cudaMemsetAsync(gm_of_row.p, 0xff, N * sizeof(int32_t), st));
     L.grp_row.alloc(Ngm, st);
@@ -1336,14 +1418,19 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
                                                        fscan.p, L.seg_ptr.p, L.seg_col.p, L.gseg_ptr.p);
         OBK_CHECK_LAUNCH();
     }
-    // 7. segments of each group ordered by length (then column), entries moved along
-    if (nseg > 1) {
+    // 7. segments of each group ordered by (tile of the column, length, column),
+    // entries moved along; (group, tile) segment starts for the sliced copy
+    DBuf<int64_t> gts_ptr(nsegs + 1, st);
+    if (nseg >= 1) {
         DBuf<uint64_t> sk(nseg, st);
         DBuf<uint32_t> sorder(nseg, st);
-        int sbits = std::min(10, bits_for((uint64_t)max_segment_length(nseg, L.seg_ptr.p, st)));
-        seg_keys<<<grid_for(nseg), kBlock, 0, st>>>(nseg, L.seg_ptr.p, L.gseg_ptr.p, G, sbits, sk.p, sorder.p);
+        int slbits = std::min(10, bits_for((uint64_t)max_segment_length(nseg, L.seg_ptr.p, st)));
+        seg_keys<<<grid_for(nseg), kBlock, 0, st>>>(nseg, L.seg_ptr.p, L.gseg_ptr.p, L.seg_col.p, G, B, T, slbits,
+                                                    sk.p, sorder.p);
         OBK_CHECK_LAUNCH();
-        radix_sort_pairs(sk.p, sorder.p, nseg, bits_for((uint64_t)G) + sbits, st);
+        radix_sort_pairs(sk.p, sorder.p, nseg, sbits + slbits, st);
+        segment_starts<<<grid_for(nseg + 1), kBlock, 0, st>>>(nseg, sk.p, slbits, nsegs, gts_ptr.p);
+        OBK_CHECK_LAUNCH();
         sk.release();
         DBuf<int64_t> slen(nseg, st), nptr(nseg + 1, st);
         seg_lengths<<<grid_for(nseg), kBlock, 0, st>>>(nseg, sorder.p, L.seg_ptr.p, slen.p);
@@ -1362,6 +1449,18 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
         L.mir_row = std::move(nrow);
         L.mir_val = std::move(nval);
         if (want_fp32) L.mir_val32 = std::move(nval32);
+    } else {
+        OBK_CUDA(cudaMemsetAsync(gts_ptr.p, 0, (nsegs + 1) * sizeof(int64_t), st));
+    }
+    {
+        std::vector<int64_t> h_gts(nsegs + 1);
+        OBK_CUDA(cudaMemcpyAsync(h_gts.data(), gts_ptr.p, (nsegs + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                 st));
+        OBK_CUDA(cudaStreamSynchronize(st));
+        L.h_ml_tptr.assign(nsegs + 1, 0);
+        for (int64_t q = 0; q < nsegs; ++q)
+            L.h_ml_tptr[q + 1] = L.h_ml_tptr[q] + ceil_div(h_gts[q + 1] - h_gts[q], (int64_t)32);
+        L.gts_ptr = std::move(gts_ptr);
     }
     mark();
     L.h_gseg_ptr.resize(G + 1);

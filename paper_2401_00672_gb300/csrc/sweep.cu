@@ -10,7 +10,17 @@
 //   phase 2  x_c += sum_k A_kc y_k over the group's rows, one thread per
 //            (group, column) segment of the column mirror (sliced the same
 //            way): a deterministic gather, no floating-point atomics.
-// A grid barrier separates the phases.  For an exactly orthogonal group the
+// Between the phases (by default) no grid barrier: each thread block owns a
+// range of tiles -- consecutive permuted rows, and the columns with the same
+// numbers -- and the layout keeps every (group, tile) piece of the rows and of
+// the column mirror contiguous.  After RCM a tile's rows touch only columns of
+// nearby tiles, so a step (one phase of one group on the block's tiles) waits
+// only until the blocks owning those tiles have finished every earlier step:
+// a per-block step counter published with a release store and polled with
+// bounded waits.  Blocks then run ahead into later groups and sweeps as far as
+// their band allows, and every x or y value is still read exactly when the
+// group-after-group order of the method says (see flow_wait).  The grid
+// barrier of each phase remains selectable.  For an exactly orthogonal group the
 // update equals x + A_tau^+ (f_tau - A_tau x) (Eq. 1.3); with pinv_iters > 0,
 // Jacobi steps on the group's Gram system make it that projection for
 // near-orthogonal groups too.
@@ -32,8 +42,8 @@
 namespace obk {
 namespace {
 
-constexpr int kBlock = 512;       // threads per block of the persistent kernel
-constexpr int kBlocksPerSm = 2;   // co-resident blocks per SM
+constexpr int kBlock = 1024;      // threads per block of the persistent kernel
+constexpr int kBlocksPerSm = 1;   // co-resident blocks per SM (one tile each)
 constexpr int kBatch = 8;         // independent loads issued before their uses
 
 struct SweepParams {
@@ -83,6 +93,18 @@ struct SweepParams {
     double fnorm, zero_f2, tol, stagnation;
     int64_t maxit;
     int check_every, precision, inner_sweeps, max_outer;  // check_every < 0: adaptive schedule
+    // band-local step counters instead of grid barriers (SUB == 1, no Jacobi steps)
+    int dataflow;
+    int64_t T;                  // tiles of the layout
+    const int64_t* sl_tptr;     // G*T + 1: first row slice of each (group, tile)
+    const int64_t* ml_tptr;     // G*T + 1: first mirror slice of each (group, tile)
+    const int32_t* reach_lo;    // T: lowest tile a step of the tile depends on
+    const int32_t* reach_hi;    // T: highest such tile
+    unsigned long long* flow;   // gridDim.x step counters, zeroed before the launch
+    const int64_t* gt_ptr;      // G*T + 1: first group-major row of each (group, tile)
+    int64_t tile_rows;          // B
+    int64_t smem_bytes;         // dynamic shared memory of the launch (staging windows)
+    int staging;                // 1 = stage windows in shared memory when worth it, 0 or 2 = never
     double* partial;  // gridDim.x
     double* ctrl;     // [0] rr, [1] beta, [2..11] history
     int64_t* out;     // [0] sweeps, [1] status, [2] outer, [3] stop, [4] sweep ns, [5] inner,
@@ -206,9 +228,11 @@ __device__ __forceinline__ void phase1(const SweepParams& p, int64_t r0, int64_t
 // rows), and the residual f_k starts the accumulator: no shuffle reduction
 // and no separate subtraction.
 
-// acc + S * sum_{j<B} a[q + 32 j] * v[idx[q + 32 j]]   (S = -1 or +1)
+// acc + S * sum_{j<B} a[q + 32 j] * v[idx[q + 32 j] - off]   (S = -1 or +1; off
+// is the first index held by v when v is a window staged in shared memory)
 template <int B, int S, class T>
-__device__ __forceinline__ T sell_batch(const int32_t* idx, const T* vals, const T* v, int64_t q, T acc)
+__device__ __forceinline__ T sell_batch(const int32_t* idx, const T* vals, const T* v, int64_t q, T acc,
+                                        int32_t off)
 {
     int32_t c[B];
     T a[B];
@@ -219,7 +243,7 @@ __device__ __forceinline__ T sell_batch(const int32_t* idx, const T* vals, const
     }
     T g[B];
 #pragma unroll
-    for (int j = 0; j < B; ++j) g[j] = v[c[j]];
+    for (int j = 0; j < B; ++j) g[j] = v[c[j] - off];
 #pragma unroll
     for (int j = 0; j < B; ++j) acc = fma(S > 0 ? a[j] : -a[j], g[j], acc);
     return acc;
@@ -227,18 +251,19 @@ __device__ __forceinline__ T sell_batch(const int32_t* idx, const T* vals, const
 
 // one lane's row (or segment) of a slice: len entries from position q
 template <int S, class T>
-__device__ __forceinline__ T sell_lane(const int32_t* idx, const T* vals, const T* v, int64_t q, int64_t len, T acc)
+__device__ __forceinline__ T sell_lane(const int32_t* idx, const T* vals, const T* v, int64_t q, int64_t len, T acc,
+                                       int32_t off = 0)
 {
     int64_t j = 0;
-    for (; j + kBatch <= len; j += kBatch, q += 32 * kBatch) acc = sell_batch<kBatch, S, T>(idx, vals, v, q, acc);
+    for (; j + kBatch <= len; j += kBatch, q += 32 * kBatch) acc = sell_batch<kBatch, S, T>(idx, vals, v, q, acc, off);
     switch ((int)(len - j)) {  // the same for the whole warp
-        case 7: acc = sell_batch<7, S, T>(idx, vals, v, q, acc); break;
-        case 6: acc = sell_batch<6, S, T>(idx, vals, v, q, acc); break;
-        case 5: acc = sell_batch<5, S, T>(idx, vals, v, q, acc); break;
-        case 4: acc = sell_batch<4, S, T>(idx, vals, v, q, acc); break;
-        case 3: acc = sell_batch<3, S, T>(idx, vals, v, q, acc); break;
-        case 2: acc = sell_batch<2, S, T>(idx, vals, v, q, acc); break;
-        case 1: acc = sell_batch<1, S, T>(idx, vals, v, q, acc); break;
+        case 7: acc = sell_batch<7, S, T>(idx, vals, v, q, acc, off); break;
+        case 6: acc = sell_batch<6, S, T>(idx, vals, v, q, acc, off); break;
+        case 5: acc = sell_batch<5, S, T>(idx, vals, v, q, acc, off); break;
+        case 4: acc = sell_batch<4, S, T>(idx, vals, v, q, acc, off); break;
+        case 3: acc = sell_batch<3, S, T>(idx, vals, v, q, acc, off); break;
+        case 2: acc = sell_batch<2, S, T>(idx, vals, v, q, acc, off); break;
+        case 1: acc = sell_batch<1, S, T>(idx, vals, v, q, acc, off); break;
         default: break;
     }
     return acc;
@@ -254,38 +279,50 @@ __device__ __forceinline__ int64_t sell_warp()
     return (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
 }
 
-// phase 1 over the row slices of group g: y_k = (rhs_k - A_k . xv) * inv_k
+// one row slice s: y_k = (rhs_k - A_k . xv) * inv_k for its (up to) 32 rows
+template <class T, class TR>
+__device__ __forceinline__ void row_slice(const SweepParams& p, int64_t s, const T* sval, const T* inv,
+                                          const TR* rhs, const T* xv, T* y, int32_t xoff = 0)
+{
+    int lane = threadIdx.x & 31;
+    int64_t base = p.sl_ptr[s], len = (p.sl_ptr[s + 1] - base) >> 5;
+    bool valid = lane < p.sl_nrow[s];
+    int64_t k = p.sl_row0[s] + lane;
+    T acc = valid ? (T)rhs[k] : T(0);
+    acc = sell_lane<-1, T>(p.sci, sval, xv, base + lane, len, acc, xoff);
+    if (valid) y[k] = acc * inv[k];
+}
+
+// one mirror slice s: xv_c += sum_k A_kc y_k for its (up to) 32 columns
+template <class T>
+__device__ __forceinline__ void col_slice(const SweepParams& p, int64_t s, const T* mval, const T* y, T* xv,
+                                          int32_t yoff = 0)
+{
+    int lane = threadIdx.x & 31;
+    int64_t base = p.ml_ptr[s], len = (p.ml_ptr[s + 1] - base) >> 5;
+    int32_t c = p.mcol[s * 32 + lane];
+    T acc = c >= 0 ? xv[c] : T(0);
+    acc = sell_lane<1, T>(p.mrow, mval, y, base + lane, len, acc, yoff);
+    if (c >= 0) xv[c] = acc;
+}
+
+// phase 1 over all row slices of group g (whole grid)
 template <class T, class TR>
 __device__ __forceinline__ void phase1_sell(const SweepParams& p, int64_t g, const T* sval, const T* inv,
                                             const TR* rhs, const T* xv, T* y)
 {
-    int lane = threadIdx.x & 31;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int64_t s1 = p.sl_gptr[g + 1];
-    for (int64_t s = p.sl_gptr[g] + sell_warp(); s < s1; s += nw) {
-        int64_t base = p.sl_ptr[s], len = (p.sl_ptr[s + 1] - base) >> 5;
-        bool valid = lane < p.sl_nrow[s];
-        int64_t k = p.sl_row0[s] + lane;
-        T acc = valid ? (T)rhs[k] : T(0);
-        acc = sell_lane<-1, T>(p.sci, sval, xv, base + lane, len, acc);
-        if (valid) y[k] = acc * inv[k];
-    }
+    for (int64_t s = p.sl_gptr[g] + sell_warp(); s < s1; s += nw) row_slice<T, TR>(p, s, sval, inv, rhs, xv, y);
 }
 
-// phase 2 over the mirror slices of group g: xv_c += sum_k A_kc y_k
+// phase 2 over all mirror slices of group g (whole grid)
 template <class T>
 __device__ __forceinline__ void phase2_sell(const SweepParams& p, int64_t g, const T* mval, const T* y, T* xv)
 {
-    int lane = threadIdx.x & 31;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int64_t s1 = p.ml_gptr[g + 1];
-    for (int64_t s = p.ml_gptr[g] + sell_warp(); s < s1; s += nw) {
-        int64_t base = p.ml_ptr[s], len = (p.ml_ptr[s + 1] - base) >> 5;
-        int32_t c = p.mcol[s * 32 + lane];
-        T acc = c >= 0 ? xv[c] : T(0);
-        acc = sell_lane<1, T>(p.mrow, mval, y, base + lane, len, acc);
-        if (c >= 0) xv[c] = acc;
-    }
+    for (int64_t s = p.ml_gptr[g] + sell_warp(); s < s1; s += nw) col_slice<T>(p, s, mval, y, xv);
 }
 
 // xv_c + sum_{j<B} a[q+j] * y[row[q+j]]
@@ -453,9 +490,230 @@ __device__ __forceinline__ void group_phase2(const SweepParams& p, int64_t g, co
     else phase2<T>(p, p.gseg_ptr[g], p.gseg_ptr[g + 1], mvals, y, xv);
 }
 
+// ---- band-local step counters (dataflow between the phases) --------------------
+//
+// Steps are numbered over the whole launch: step 2 (s G + g) is phase 1 of
+// group g in the s-th sweep since the launch, step 2 (s G + g) + 1 its phase 2
+// (the same numbering on every block).  flow[b] = j means block b has finished
+// all its steps before j.  Before a step j with work, a block publishes what
+// it has finished and waits until flow[b'] >= j for every block b' owning a
+// tile in the reach of its own tiles.  That order is exactly the one the grid
+// barriers give, for every value the step touches:
+//  * phase 1 of group g on tile t reads x_c for the columns c of its rows; the
+//    tiles of those columns are in the reach of t, and their owners have
+//    finished every earlier step, so every earlier update of x_c is visible,
+//    and no later one has started: an update of x_c at a later step waits for
+//    the tiles of the rows of column c, t among them;
+//  * phase 2 of group g on tile t reads y_k for the rows k of group g that
+//    touch its columns, written by phase 1 of g on their tiles (in the reach of
+//    t), and overwrites x_c only after every earlier phase 1 reading x_c ended
+//    (same tiles);
+//  * phase 1 of the next sweep overwrites y_k only after every phase 2 reading
+//    it ended: the tiles of the columns of row k are in the reach of k's tile.
+// A block with nothing to do in a step skips it without waiting; its counter
+// moves on at its next wait.  The block with the fewest finished steps always
+// finds its waits satisfied, so the launch cannot deadlock; every wait is still
+// bounded (as in grid_sync) and checks the error word, so a block that gave up
+// makes the others give up too.
+struct FlowState {
+    int64_t t0, t1;          // tiles [t0, t1) owned by this block
+    int64_t tlo, thi;        // tiles its steps depend on
+    int blo, bhi;            // blocks this block's steps wait for
+    unsigned long long step; // next step
+    unsigned long long pub;  // last value published in flow[blockIdx.x]
+    int ok;
+};
+
+__device__ __forceinline__ int block_of_tile(int64_t t, int64_t T)
+{
+    return (int)(((t + 1) * (int64_t)gridDim.x - 1) / T);
+}
+
+__device__ void flow_init(const SweepParams& p, FlowState& f)
+{
+    if (threadIdx.x == 0) {
+        f.t0 = (int64_t)blockIdx.x * p.T / gridDim.x;
+        f.t1 = ((int64_t)blockIdx.x + 1) * p.T / gridDim.x;
+        int64_t lo = f.t0, hi = f.t1 - 1;
+        for (int64_t t = f.t0; t < f.t1; ++t) {
+            lo = min(lo, (int64_t)p.reach_lo[t]);
+            hi = max(hi, (int64_t)p.reach_hi[t]);
+        }
+        f.tlo = lo;
+        f.thi = hi;
+        f.blo = block_of_tile(lo, p.T);
+        f.bhi = block_of_tile(hi, p.T);
+        f.step = 0;
+        f.pub = 0;
+        f.ok = 1;
+    }
+    __syncthreads();
+}
+
+// Publish the finished steps, then wait until every block in the reach has
+// finished the steps before f.step.  Called by all threads; false on timeout.
+__device__ bool flow_wait(const SweepParams& p, FlowState& f)
+{
+    __syncthreads();  // the block's earlier writes are complete
+    if (threadIdx.x < 32) {
+        const unsigned full = 0xffffffffu;
+        int lane = threadIdx.x;
+        unsigned long long j = f.step;
+        if (lane == 0 && f.pub < j) {
+            __threadfence();
+            st_release_gpu_u64(p.flow + blockIdx.x, j);
+        }
+        long long spins = 0;
+        int ok = 1;
+        for (;;) {
+            bool mine = true;
+            for (int b = f.blo + lane; b <= f.bhi; b += 32) mine = mine && ld_volatile_u64(p.flow + b) >= j;
+            if (__all_sync(full, mine)) break;
+            ++spins;
+            bool bad = spins > p.gb.limit;
+            if ((spins & 63) == 0) bad = bad || __any_sync(full, ld_volatile_i32(p.gb.err) != 0);
+            if (bad) {
+                if (lane == 0) atomicCAS(p.gb.err, 0, (int)kDevTimeout);
+                ok = 0;
+                break;
+            }
+            if (spins > 16) __nanosleep(32);
+        }
+        // acquire the values seen (the same load the grid barrier uses), so the
+        // neighbours' writes before their release are visible to this block
+        for (int b = f.blo + lane; b <= f.bhi; b += 32) (void)ld_acquire_gpu_u64(p.flow + b);
+        __threadfence();
+        if (lane == 0) {
+            f.pub = j > f.pub ? j : f.pub;
+            f.ok = ok;
+        }
+    }
+    __syncthreads();
+    return f.ok != 0;
+}
+
+// The block finished step f.step (with work): publish it and move on.
+__device__ __forceinline__ void flow_done(const SweepParams& p, FlowState& f)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        st_release_gpu_u64(p.flow + blockIdx.x, f.step + 1);
+        f.pub = f.step + 1;
+        f.step = f.step + 1;
+    }
+    __syncthreads();
+}
+
+// Publish every step finished so far (skipped ones included), so that no
+// other block waits on this one while it is elsewhere (a grid barrier).
+__device__ __forceinline__ void flow_flush(const SweepParams& p, FlowState& f)
+{
+    __syncthreads();
+    if (threadIdx.x == 0 && f.pub < f.step) {
+        __threadfence();
+        st_release_gpu_u64(p.flow + blockIdx.x, f.step);
+        f.pub = f.step;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void flow_skip(FlowState& f)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) f.step = f.step + 1;
+    __syncthreads();
+}
+
+__device__ __forceinline__ void cp_async_16(void* dst_smem, const void* src)
+{
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" : : "r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" : : : "memory"); }
+
+// Copy src[a0, w1) into the block's shared-memory window (all threads), where
+// a0 = w0 rounded down to a 16-byte boundary of src, and return a0: the window
+// holds src[i] at win[i - a0].  Whole 16-byte chunks go by asynchronous copies
+// (all in flight at once), the ragged end element by element.  src must be
+// 16-byte aligned; the window needs w1 - a0 elements.
+template <class T>
+__device__ __forceinline__ int64_t stage(T* win, const T* src, int64_t w0, int64_t w1)
+{
+    constexpr int64_t E = 16 / sizeof(T);  // elements per chunk
+    int64_t a0 = w0 & ~(E - 1);
+    int64_t a1 = w1 & ~(E - 1);            // chunks [a0, a1), elements [a1, w1)
+    for (int64_t i = a0 + (int64_t)threadIdx.x * E; i < a1; i += (int64_t)blockDim.x * E)
+        cp_async_16(win + (i - a0), src + i);
+    for (int64_t i = max(a1, a0) + threadIdx.x; i < w1; i += blockDim.x) win[i - a0] = src[i];
+    cp_async_wait_all();
+    __syncthreads();
+    return a0;
+}
+
+// A step stages its window in shared memory when the window fits and holds
+// no more values than the step gathers (a copy of a value is a coalesced
+// load, a gather a random one); otherwise it gathers from global memory.
+__device__ __forceinline__ bool worth_staging(int64_t window, int64_t gathers, int64_t cap)
+{
+    return window <= cap && window <= gathers;
+}
+
+// One sweep (all groups) on the block's tiles with band-local waits; false on timeout.
+//  phase 1 of group g reads x at the columns of the block's rows: the columns
+//    of tiles [tlo, thi], staged as x[tlo * B, (thi + 1) * B);
+//  phase 2 reads y at the group-major rows of group g in tiles [tlo, thi] (the
+//    rows touching the block's columns), contiguous in the layout.
+template <class T, class TR>
+__device__ bool flow_sweep(const SweepParams& p, FlowState& f, const T* sval, const T* mval, const T* inv,
+                           const TR* rhs, T* xv, T* y)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    T* win = reinterpret_cast<T*>(dsm);
+    const int64_t cap = p.smem_bytes / (int64_t)sizeof(T);
+    const int nw = blockDim.x >> 5;
+    const int w = threadIdx.x >> 5;
+    const int64_t x0 = f.tlo * p.tile_rows;
+    const int64_t x1 = min((f.thi + 1) * p.tile_rows, p.N);
+    for (int64_t g = 0; g < p.G; ++g) {
+        int64_t s0 = p.sl_tptr[g * p.T + f.t0], s1 = p.sl_tptr[g * p.T + f.t1];
+        if (s0 < s1) {
+            if (!flow_wait(p, f)) return false;
+            if (p.staging == 1 && worth_staging(x1 - x0 + 4, p.sl_ptr[s1] - p.sl_ptr[s0], cap)) {
+                int64_t a0 = stage<T>(win, xv, x0, x1);
+                for (int64_t s = s0 + w; s < s1; s += nw) row_slice<T, TR>(p, s, sval, inv, rhs, win, y, (int32_t)a0);
+            } else {
+                for (int64_t s = s0 + w; s < s1; s += nw) row_slice<T, TR>(p, s, sval, inv, rhs, xv, y);
+            }
+            flow_done(p, f);
+        } else {
+            flow_skip(f);
+        }
+        int64_t m0 = p.ml_tptr[g * p.T + f.t0], m1 = p.ml_tptr[g * p.T + f.t1];
+        if (m0 < m1) {
+            if (!flow_wait(p, f)) return false;
+            int64_t y0 = p.gt_ptr[g * p.T + f.tlo], y1 = p.gt_ptr[g * p.T + f.thi + 1];
+            if (p.staging == 1 && worth_staging(y1 - y0 + 4, p.ml_ptr[m1] - p.ml_ptr[m0], cap)) {
+                int64_t a0 = stage<T>(win, y, y0, y1);
+                for (int64_t s = m0 + w; s < m1; s += nw) col_slice<T>(p, s, mval, win, xv, (int32_t)a0);
+            } else {
+                for (int64_t s = m0 + w; s < m1; s += nw) col_slice<T>(p, s, mval, y, xv);
+            }
+            flow_done(p, f);
+        } else {
+            flow_skip(f);
+        }
+    }
+    flow_flush(p, f);
+    return true;
+}
+
 template <int SUB>
 __global__ void __launch_bounds__(kBlock, kBlocksPerSm) obk_solve_kernel(SweepParams p)
 {
+    __shared__ FlowState flow;
+    const bool df = SUB == 1 && p.dataflow != 0 && p.pinv_iters == 0;
+    if (df) flow_init(p, flow);
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     volatile int64_t* vout = p.out;
     // initial residual
@@ -485,7 +743,9 @@ __global__ void __launch_bounds__(kBlock, kBlocksPerSm) obk_solve_kernel(SweepPa
         if (!grid_sync(p.gb)) return;
         while (vout[3] == 0) {
             unsigned long long t0 = lead ? globaltimer() : 0;
-            for (int64_t g = 0; g < p.G; ++g) {
+            if (df) {
+                if (!flow_sweep<double, double>(p, flow, p.sv, p.mv, p.grp_inv, p.f, p.x, p.y)) return;
+            } else for (int64_t g = 0; g < p.G; ++g) {
                 group_phase1<SUB, double, double>(p, g, p.grp_v, p.sv, p.grp_inv, p.f, p.x, p.y);
                 const double* yg = p.y;
                 if (p.pinv_iters > 0) {  // y <- solution of the group's Gram system
@@ -509,6 +769,9 @@ __global__ void __launch_bounds__(kBlock, kBlocksPerSm) obk_solve_kernel(SweepPa
             bool check = p.check_every > 0 ? ((s % p.check_every) == 0 || s >= p.maxit)
                                            : (s >= vout[6] || s >= p.maxit);
             if (check) {
+                // with band-local waits the blocks may be at different steps:
+                // the residual needs every block's sweeps finished
+                if (df && !grid_sync(p.gb)) return;
                 residual_partial<SUB>(p, false);
                 if (!grid_sync(p.gb)) return;
                 double totc = blockIdx.x == 0 ? total_partials(p) : 0.0;
@@ -553,6 +816,10 @@ __global__ void __launch_bounds__(kBlock, kBlocksPerSm) obk_solve_kernel(SweepPa
         int nin = s_in;
         if (sweeps + nin > p.maxit) nin = (int)(p.maxit - sweeps);
         for (int it = 0; it < nin; ++it) {
+            if (df) {
+                if (!flow_sweep<float, float>(p, flow, p.sv32, p.mv32, p.grp_inv32, p.b32, p.d32, p.y32)) return;
+                continue;
+            }
             for (int64_t g = 0; g < p.G; ++g) {
                 group_phase1<SUB, float, float>(p, g, p.grp_v32, p.sv32, p.grp_inv32, p.b32, p.d32, p.y32);
                 if (!grid_sync(p.gb)) return;
@@ -560,6 +827,7 @@ __global__ void __launch_bounds__(kBlock, kBlocksPerSm) obk_solve_kernel(SweepPa
                 if (!grid_sync(p.gb)) return;
             }
         }
+        if (df && !grid_sync(p.gb)) return;  // every block's inner sweeps are done
         sweeps += nin;
         if (lead) { vout[4] += (int64_t)(globaltimer() - t0); vout[0] = sweeps; }
         for (int64_t c = tid; c < p.N; c += nth) p.x[c] = fma(beta, (double)p.d32[c], p.x[c]);
@@ -604,22 +872,45 @@ __global__ void __launch_bounds__(kBlock, kBlocksPerSm) obk_solve_kernel(SweepPa
 // ---- launch ---------------------------------------------------------------------
 
 template <int SUB>
-void launch_solve(SweepParams& p, cudaStream_t st)
+void launch_solve(SweepParams& p, int64_t want_smem, cudaStream_t st)
 {
     DevInfo di = dev_info();
     const void* k = (const void*)obk_solve_kernel<SUB>;
-    // one block per 2K grouped rows, at most kBlocksPerSm per SM: small systems
-    // take a few SMs and leave the others to concurrent requests
-    int64_t want = std::min<int64_t>((int64_t)di.sms * kBlocksPerSm, ceil_div(std::max<int64_t>(p.Ngm, 1), 2048));
-    int grid = coop_grid(k, kBlock, 0, want);
+    // dynamic shared memory for the staged windows of the band-local sweep:
+    // what the largest window needs, within the opt-in limit
+    cudaFuncAttributes fa;
+    OBK_CUDA(cudaFuncGetAttributes(&fa, k));
+    int64_t room = (int64_t)di.smem_optin - (int64_t)fa.sharedSizeBytes;
+    room &= ~(int64_t)15;
+    int64_t smem = SUB == 1 && p.dataflow && p.staging == 1 ? std::max<int64_t>(0, std::min<int64_t>(want_smem, room))
+                                                             : 0;
+    smem &= ~(int64_t)15;
+    // the attribute is the same on every call (threads of the request loop may
+    // launch concurrently with different sizes, all within it)
+    OBK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)room));
+    p.smem_bytes = smem;
+    // one block per tile of the layout (one per 4K rows, at most kBlocksPerSm
+    // per SM): small systems take a few SMs and leave the others to concurrent
+    // requests; a smaller co-resident grid gives each block several tiles
+    int grid = coop_grid(k, kBlock, (size_t)smem, std::max<int64_t>(p.T, 1));
     DBuf<double> partial(grid, st);
+    DBuf<unsigned long long> flow(grid, st);
+    OBK_CUDA(cudaMemsetAsync(flow.p, 0, flow.bytes(), st));
     p.partial = partial.p;
+    p.flow = flow.p;
     void* args[] = {&p};
-    OBK_COOP_LAUNCH(k, grid, kBlock, args, st);
+    ::obk::count_launch();
+    OBK_CUDA(cudaLaunchCooperativeKernel(k, grid, kBlock, args, (size_t)smem, st));
     OBK_CUDA(cudaStreamSynchronize(st));
 }
 
 }  // namespace
+
+int64_t sweep_tiles(int64_t N)
+{
+    DevInfo di = dev_info();
+    return std::max<int64_t>(1, std::min<int64_t>((int64_t)di.sms * kBlocksPerSm, ceil_div(N, 4096)));
+}
 
 // Lanes per row in phase 1.  FP64 issue is scarce on this GPU (a warp-wide
 // FP64 instruction occupies the FP64 pipe for the same time whatever the
@@ -714,18 +1005,29 @@ SolveResult run_solve(const SweepLayout& L, const double* f_gm, double fnorm2, d
     p.precision = a.precision;
     p.inner_sweeps = a.inner_sweeps;
     p.max_outer = a.max_outer > 0 ? a.max_outer : 100;
+    p.dataflow = a.sync_mode == 0 ? 1 : 0;
+    p.T = L.T;
+    p.sl_tptr = L.sl_tptr.p;
+    p.ml_tptr = L.ml_tptr.p;
+    p.reach_lo = L.reach_lo.p;
+    p.reach_hi = L.reach_hi.p;
+    p.gt_ptr = L.gt_ptr.p;
+    p.tile_rows = L.B;
+    p.staging = a.staging;
     p.ctrl = ctrl.p;
     p.out = out.p;
     p.gb = GridBarrier{bar.p, d_err, a.spin_limit};
     int sub = a.sub;
     if (sub == 0) sub = choose_sub(L.Ngm ? (double)L.nnz_gm / (double)L.Ngm : 1.0);
+    int64_t elt = a.precision == 1 ? (int64_t)sizeof(float) : (int64_t)sizeof(double);
+    int64_t want_smem = (std::max(L.ywin_max, L.xwin_max) + 4) * elt;  // + the 16-byte rounding of a window
     switch (sub) {
-        case 1: launch_solve<1>(p, st); break;
-        case 2: launch_solve<2>(p, st); break;
-        case 4: launch_solve<4>(p, st); break;
-        case 8: launch_solve<8>(p, st); break;
-        case 16: launch_solve<16>(p, st); break;
-        default: launch_solve<32>(p, st); break;
+        case 1: launch_solve<1>(p, want_smem, st); break;
+        case 2: launch_solve<2>(p, want_smem, st); break;
+        case 4: launch_solve<4>(p, want_smem, st); break;
+        case 8: launch_solve<8>(p, want_smem, st); break;
+        case 16: launch_solve<16>(p, want_smem, st); break;
+        default: launch_solve<32>(p, want_smem, st); break;
     }
     int err = read_scalar(d_err, st);
     if (err != 0) throw Error{-4, "bounded wait expired in the sweep kernel"};

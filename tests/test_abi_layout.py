@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 STRUCTS = {
     "obk_csr": ("_Csr", ["row_ptr", "col_idx", "val", "nnz", "device_ptrs"]),
     "obk_opts": ("Opts", ["precision", "check_every", "inner_sweeps", "max_outer", "stagnation",
-                          "timeout_spins", "rows_per_warp", "pinv_iters"]),
+                          "timeout_spins", "rows_per_warp", "pinv_iters", "sync_mode", "staging"]),
     "obk_info": ("_Info", ["sweeps", "rel_res", "setup_ms", "solve_ms", "groups", "bandwidth_before",
                            "bandwidth_after", "outer_iters", "sweep_ms", "n_conflicts", "status"]),
     "obk_block_opts": ("BlockOpts", ["k", "inner_max", "thr", "inner_tol", "n_pairs", "n_nclass", "cgls_steps"]),

@@ -235,6 +235,23 @@ def test_solve_parity(obk, name):
         assert np.linalg.norm(x - x_o) / (nrm if nrm > 0 else 1.0) <= XTOL
 
 
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("precision", [0, 1])
+def test_band_waits_equal_grid_barriers(obk, name, precision):
+    """The band-local step counters change only when each block runs a step,
+    never what a step reads: x must be bit-identical to the solve with a grid
+    barrier after every phase, for the same number of sweeps (FP64 and the
+    FP32 inner sweeps of the precision form)."""
+    s, _ = _case(name)
+    A = s.A
+    base = dict(precision=precision, inner_sweeps=6) if precision else dict(check_every=1)
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
+        st0, x0, i0 = h.solve(s.f, tol=1e-9, maxit=3000, opts=obk.Opts(sync_mode=0, **base))
+        st1, x1, i1 = h.solve(s.f, tol=1e-9, maxit=3000, opts=obk.Opts(sync_mode=1, **base))
+    assert st0 == st1 and i0.sweeps == i1.sweeps and i0.outer_iters == i1.outer_iters
+    assert np.array_equal(x0.view(np.uint64), x1.view(np.uint64))
+
+
 @pytest.mark.parametrize("name", ["knn_30000", "random_dominant_2000"])
 def test_adaptive_schedule_parity(obk, name):
     s, _ = _case(name)
