@@ -98,14 +98,19 @@ typedef struct {
                                phases (same arithmetic, same results); 1 = a grid-wide
                                barrier after every phase.  pinv_iters > 0 and
                                rows_per_warp < 32 always use barriers.               */
-    int32_t staging;        /* where the band-local sweep reads x and y: 0 (default) or 2 =
-                               gathers from global memory through L1 and L2; 1 = each
+    int32_t staging;        /* where the band-local sweep reads x and y: 0 = default (the
+                               autotuned choice, else 2); 2 = gathers from global
+                               memory through L1 and L2; 1 = each
                                step copies the window it reads (x for the columns of the
                                block's band, y for the group's rows in it) into shared
                                memory when the window fits and holds no more values
                                than the step's gathers (the shared memory this takes is
                                no longer L1, which the other steps' gathers lose).  Same
                                results either way.                                    */
+    int32_t block_threads;  /* threads per block of the sweep kernel: 0 = default (the
+                               autotuned choice, else 1024), 1024 (one block per SM,
+                               owning two tiles) or 512 (two per SM, one tile each).  */
+    int32_t reserved;       /* must be 0 */
 } obk_opts;
 
 typedef struct {
@@ -306,19 +311,32 @@ OBK_API int64_t obk_batch_max_n(void);
 
 /* Result of obk_autotune. */
 typedef struct {
-    int32_t rows_per_warp;       /* chosen setting (1, 2, 4, 8, 16 or 32) */
-    int32_t reserved;
-    double sweep_ms;             /* device time of one sweep with it */
-    double candidate_ms[6];      /* sweep time for rows_per_warp 32, 16, 8, 4, 2, 1 (0 if skipped) */
+    int32_t rows_per_warp;       /* chosen rows per warp (1, 2, 4, 8, 16 or 32)                */
+    int32_t block_threads;       /* chosen threads per block of the sweep kernel: 1024 (one
+                                    block per SM, two tiles each) or 512 (two per SM)          */
+    int32_t staging;             /* chosen placement of the x / y windows: 2 = gathered from
+                                    global memory (L1/L2), 1 = staged in shared memory        */
+    int32_t n_candidates;        /* settings timed: entries of candidate_ms in use             */
+    double sweep_ms;             /* device time of one sweep with the chosen setting           */
+    double candidate_ms[12];     /* one sweep for each candidate, in this order (0 = skipped):
+                                    rows per warp 32 with (block, placement) = (1024, global),
+                                    (1024, shared), (512, global), (512, shared); then rows per
+                                    warp 16, 8, 4, 2, 1 with blocks of 1024 and of 512 in turn,
+                                    as far as they fit (a sub-warp per row reads the group-
+                                    major rows through L1/L2 only)                             */
 } obk_tune;
 
 /* Autotuner of the sweep kernel for a prepared system: times a few sweeps (on
- * zero vectors, so the handle's results are unaffected) for each rows-per-warp
- * setting, keeps the fastest for later solves of h with opts.rows_per_warp = 0
- * and records it in a process-wide table keyed by (device, size class, mean
- * row length, precision) that other handles of the same shape use until they
- * are tuned themselves.  precision: 0 (FP64 sweeps) or 1 (FP32 inner sweeps).
- * out may be NULL.  Errors: OBK_ERR_INVALID, OBK_ERR_TIMEOUT, OBK_ERR_CUDA. */
+ * zero vectors, so the handle's results are unaffected) for each candidate
+ * setting -- lanes per row, threads per block, and where the band-local sweep
+ * reads x and y (global memory through L1/L2, or windows staged in shared
+ * memory) -- and keeps the fastest for later solves of h whose opts leave
+ * rows_per_warp, block_threads and staging at 0.  The choice also goes into a
+ * process-wide table keyed by (device, size class, mean row length, bandwidth
+ * class after RCM, precision) that other handles of the same shape use until
+ * they are tuned themselves.  precision: 0 (FP64 sweeps) or 1 (FP32 inner
+ * sweeps).  out may be NULL.  Errors: OBK_ERR_INVALID, OBK_ERR_TIMEOUT,
+ * OBK_ERR_CUDA. */
 OBK_API obk_status obk_autotune(obk_handle* h, int32_t precision, obk_tune* out);
 
 /* Release every resource of h (NULL is ignored). */

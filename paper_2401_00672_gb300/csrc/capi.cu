@@ -262,7 +262,7 @@ struct obk_handle {
     SweepLayout L;
     obk_info info{};
     RcmStats rcm{};
-    int tuned_sub[2] = {0, 0};  // lanes per row chosen by obk_autotune (0 = not tuned)
+    TuneChoice tuned[2];        // per precision, chosen by obk_autotune (sub = 0: not tuned)
     double stage_ms[16] = {};    // obk_create stages (see obk_get_setup_profile)
     int n_stage = 0;
     // A~ in RCM order (rows and columns) for the block form, with its column
@@ -278,25 +278,27 @@ struct obk_handle {
 
 namespace {
 // Process-wide autotuning table: (device, log2 size class, mean row length
-// rounded, precision) -> lanes per row.
+// rounded, log2 bandwidth class after RCM, precision) -> setting.
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, int> g_tune;
+std::map<std::tuple<int, int, int, int, int>, TuneChoice> g_tune;
 
-std::tuple<int, int, int, int> tune_key(const obk_handle* h, int precision)
+std::tuple<int, int, int, int, int> tune_key(const obk_handle* h, int precision)
 {
     int szc = 0;
     while ((int64_t(1) << szc) < h->L.Ngm) ++szc;
     int avg = h->L.Ngm ? (int)((double)h->L.nnz_gm / (double)h->L.Ngm + 0.5) : 0;
-    return {h->device, szc, avg, precision};
+    int bwc = bits_for((uint64_t)std::max<int64_t>(h->info.bandwidth_after, 0));
+    return {h->device, szc, avg, bwc, precision};
 }
 
-int tuned_or_rule(const obk_handle* h, int precision)
+// The tuned setting of h (or of its shape), or all zeros (the fixed rules).
+TuneChoice tuned_or_rule(const obk_handle* h, int precision)
 {
-    if (h->tuned_sub[precision]) return h->tuned_sub[precision];
+    if (h->tuned[precision].sub) return h->tuned[precision];
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(tune_key(h, precision));
     if (it != g_tune.end()) return it->second;
-    return 0;  // the kernel's fixed rule
+    return TuneChoice{};
 }
 }  // namespace
 
@@ -443,6 +445,9 @@ obk_status obk_solve_ex(obk_handle* h, const obk_opts* opts, const double* f, co
     if (o.pinv_iters < 0) throw Error{-1, "pinv_iters must be >= 0"};
     if (o.sync_mode != 0 && o.sync_mode != 1) throw Error{-1, "sync_mode must be 0 or 1"};
     if (o.staging < 0 || o.staging > 2) throw Error{-1, "staging must be 0, 1 or 2"};
+    if (o.block_threads != 0 && o.block_threads != 512 && o.block_threads != 1024)
+        throw Error{-1, "block_threads must be 0, 512 or 1024"};
+    if (o.reserved != 0) throw Error{-1, "reserved option field must be 0"};
     if (o.rows_per_warp != 0 && o.rows_per_warp != 1 && o.rows_per_warp != 2 && o.rows_per_warp != 4 &&
         o.rows_per_warp != 8 && o.rows_per_warp != 16 && o.rows_per_warp != 32)
         throw Error{-1, "rows_per_warp must be 0, 1, 2, 4, 8, 16 or 32"};
@@ -495,10 +500,12 @@ obk_status obk_solve_ex(obk_handle* h, const obk_opts* opts, const double* f, co
     a.tol = tol;
     a.maxit = maxit;
     a.spin_limit = o.timeout_spins > 0 ? o.timeout_spins : kDefaultSpins;
-    a.sub = o.rows_per_warp > 0 ? 32 / o.rows_per_warp : tuned_or_rule(h, o.precision);
+    TuneChoice tc = tuned_or_rule(h, o.precision);
+    a.sub = o.rows_per_warp > 0 ? 32 / o.rows_per_warp : tc.sub;
     a.pinv_iters = o.precision == 0 ? o.pinv_iters : 0;
     a.sync_mode = o.sync_mode;
-    a.staging = o.staging;
+    a.staging = o.staging != 0 ? o.staging : (tc.staging != 0 ? tc.staging : 2);
+    a.block = o.block_threads != 0 ? o.block_threads : (tc.block != 0 ? tc.block : 1024);
     if (a.pinv_iters > 0 && !h->L.has_gram) build_group_gram(h->L, h->err.p, st);
     SolveResult r = run_solve(h->L, fgm.p, fnorm2, zero_f2, xt.p, a, h->err.p, st);
     // x = P^T x~, then x^(1:n)
@@ -725,23 +732,32 @@ obk_status obk_autotune(obk_handle* h, int32_t precision, obk_tune* out)
     if (!h || (precision != 0 && precision != 1)) throw Error{-1, "handle NULL or precision not 0/1"};
     OBK_CUDA(cudaSetDevice(h->device));
     obk_tune t{};
-    const int rpw[6] = {32, 16, 8, 4, 2, 1};
+    // candidates in the order documented in obk.h
+    std::vector<TuneChoice> cand = {{1, 1024, 2}, {1, 1024, 1}, {1, 512, 2}, {1, 512, 1}};
+    const double avg = h->L.Ngm ? (double)h->L.nnz_gm / (double)h->L.Ngm : 1.0;
+    for (int sub : {2, 4, 8, 16, 32})
+        for (int block : {1024, 512}) cand.push_back(TuneChoice{sub, block, 2});
     double best = 1e300;
-    int best_rpw = 16;
-    for (int k = 0; k < 6; ++k) {
-        int sub = 32 / rpw[k];
-        double avg = h->L.Ngm ? (double)h->L.nnz_gm / (double)h->L.Ngm : 1.0;
-        if (sub > 2 * avg + 2) continue;  // more lanes than entries: skip
-        double ms = time_sweep(h->L, sub, precision, h->err.p, h->st);
-        t.candidate_ms[k] = ms;
-        if (ms < best) { best = ms; best_rpw = rpw[k]; }
+    TuneChoice choice{1, 1024, 2};
+    int k = 0;
+    for (const TuneChoice& c : cand) {
+        if (k >= 12) break;
+        double ms = 0.0;
+        if (!(c.sub > 2 * avg + 2)) {  // more lanes than entries: skip
+            ms = time_sweep(h->L, c.sub, precision, c.block, c.staging, h->err.p, h->st);
+            if (ms < best) { best = ms; choice = c; }
+        }
+        t.candidate_ms[k++] = ms;
     }
-    t.rows_per_warp = best_rpw;
+    t.n_candidates = k;
+    t.rows_per_warp = 32 / choice.sub;
+    t.block_threads = choice.block;
+    t.staging = choice.staging;
     t.sweep_ms = best;
-    h->tuned_sub[precision] = 32 / best_rpw;
+    h->tuned[precision] = choice;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune[tune_key(h, precision)] = 32 / best_rpw;
+        g_tune[tune_key(h, precision)] = choice;
     }
     if (out) *out = t;
     return OBK_OK;

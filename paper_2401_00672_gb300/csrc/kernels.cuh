@@ -208,6 +208,7 @@ struct SolveArgs {
     int sub = 0;  // lanes per row (0 = choose)
     int sync_mode = 0;  // 0 = band-local step counters between the phases, 1 = grid barriers
     int staging = 0;    // band-local sweep: 1 = x and y windows in shared memory when worth it, 0 or 2 = never
+    int block = 1024;   // threads per block of the sweep kernel: 1024 (one per SM) or 512 (two per SM)
 };
 
 struct SolveResult {
@@ -219,15 +220,24 @@ struct SolveResult {
 };
 
 // Device time (ms) of one sweep with `sub` lanes per row (0 = default rule),
-// measured on zero vectors as the difference of 2- and 8-sweep solves.
-double time_sweep(const SweepLayout& L, int sub, int precision, int* d_err, cudaStream_t st);
+// `block` threads per block and the given staging mode, measured on zero
+// vectors as the difference of 2- and 8-sweep solves.
+double time_sweep(const SweepLayout& L, int sub, int precision, int block, int staging, int* d_err,
+                  cudaStream_t st);
+
+// A setting of the sweep kernel chosen by the autotuner (sub = 0: none).
+struct TuneChoice {
+    int sub = 0;      // lanes per row
+    int block = 0;    // threads per block
+    int staging = 0;  // 1 = staged windows in shared memory, 2 = global memory
+};
 
 // Lanes per row chosen by the fixed rule from the mean row length.
 int choose_sub(double avg_row);
 
 // Number of tiles of the sweep layout of an N-row system on the current device:
-// the thread blocks of the persistent sweep (each owns one tile), fewer for
-// small systems (one per 4096 rows).
+// two per SM (a block of the persistent sweep owns one or two), fewer for
+// small systems (one per 2048 rows).
 int64_t sweep_tiles(int64_t N);
 
 // x (N, permuted order) is updated in place; f_gm (Ngm) is f in group-major

@@ -42,8 +42,13 @@
 namespace obk {
 namespace {
 
-constexpr int kBlock = 1024;      // threads per block of the persistent kernel
-constexpr int kBlocksPerSm = 1;   // co-resident blocks per SM (one tile each)
+// The persistent kernel runs 1024 threads per SM (64 registers each fill the
+// register file), as one block of 1024 threads (the default) or two of 512;
+// the layout has two tiles per SM, so a block of 1024 owns two adjacent tiles
+// and a block of 512 one.
+constexpr int kThreadsPerSm = 1024;
+constexpr int kTilesPerSm = 2;
+constexpr int kMaxWarps = 32;
 constexpr int kBatch = 8;         // independent loads issued before their uses
 
 struct SweepParams {
@@ -370,7 +375,7 @@ __device__ __forceinline__ void phase2(const SweepParams& p, int64_t s0, int64_t
 // deterministic block sum (fixed shuffle tree, warps in order); result in thread 0
 __device__ double block_sum(double v)
 {
-    __shared__ double ws[kBlock / 32];
+    __shared__ double ws[kMaxWarps];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -708,8 +713,8 @@ __device__ bool flow_sweep(const SweepParams& p, FlowState& f, const T* sval, co
     return true;
 }
 
-template <int SUB>
-__global__ void __launch_bounds__(kBlock, kBlocksPerSm) obk_solve_kernel(SweepParams p)
+template <int SUB, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, kThreadsPerSm / BLOCK) obk_solve_kernel(SweepParams p)
 {
     __shared__ FlowState flow;
     const bool df = SUB == 1 && p.dataflow != 0 && p.pinv_iters == 0;
@@ -871,11 +876,11 @@ __global__ void __launch_bounds__(kBlock, kBlocksPerSm) obk_solve_kernel(SweepPa
 
 // ---- launch ---------------------------------------------------------------------
 
-template <int SUB>
+template <int SUB, int BLOCK>
 void launch_solve(SweepParams& p, int64_t want_smem, cudaStream_t st)
 {
     DevInfo di = dev_info();
-    const void* k = (const void*)obk_solve_kernel<SUB>;
+    const void* k = (const void*)obk_solve_kernel<SUB, BLOCK>;
     // dynamic shared memory for the staged windows of the band-local sweep:
     // what the largest window needs, within the opt-in limit
     cudaFuncAttributes fa;
@@ -889,10 +894,13 @@ void launch_solve(SweepParams& p, int64_t want_smem, cudaStream_t st)
     // launch concurrently with different sizes, all within it)
     OBK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)room));
     p.smem_bytes = smem;
-    // one block per tile of the layout (one per 4K rows, at most kBlocksPerSm
-    // per SM): small systems take a few SMs and leave the others to concurrent
-    // requests; a smaller co-resident grid gives each block several tiles
-    int grid = coop_grid(k, kBlock, (size_t)smem, std::max<int64_t>(p.T, 1));
+    // blocks for the tiles of the layout (one tile per 2K rows, two per SM):
+    // small systems take a few SMs and leave the others to concurrent
+    // requests; a block of 1024 threads takes two tiles, and a smaller
+    // co-resident grid gives each block more
+    constexpr int64_t kTilesPerBlock = BLOCK / (kThreadsPerSm / kTilesPerSm);
+    int64_t want = std::max<int64_t>(1, ceil_div(std::max<int64_t>(p.T, 1), kTilesPerBlock));
+    int grid = coop_grid(k, BLOCK, (size_t)smem, want);
     DBuf<double> partial(grid, st);
     DBuf<unsigned long long> flow(grid, st);
     OBK_CUDA(cudaMemsetAsync(flow.p, 0, flow.bytes(), st));
@@ -900,7 +908,7 @@ void launch_solve(SweepParams& p, int64_t want_smem, cudaStream_t st)
     p.flow = flow.p;
     void* args[] = {&p};
     ::obk::count_launch();
-    OBK_CUDA(cudaLaunchCooperativeKernel(k, grid, kBlock, args, (size_t)smem, st));
+    OBK_CUDA(cudaLaunchCooperativeKernel(k, grid, BLOCK, args, (size_t)smem, st));
     OBK_CUDA(cudaStreamSynchronize(st));
 }
 
@@ -909,7 +917,7 @@ void launch_solve(SweepParams& p, int64_t want_smem, cudaStream_t st)
 int64_t sweep_tiles(int64_t N)
 {
     DevInfo di = dev_info();
-    return std::max<int64_t>(1, std::min<int64_t>((int64_t)di.sms * kBlocksPerSm, ceil_div(N, 4096)));
+    return std::max<int64_t>(1, std::min<int64_t>((int64_t)di.sms * kTilesPerSm, ceil_div(N, 2048)));
 }
 
 // Lanes per row in phase 1.  FP64 issue is scarce on this GPU (a warp-wide
@@ -1021,13 +1029,14 @@ SolveResult run_solve(const SweepLayout& L, const double* f_gm, double fnorm2, d
     if (sub == 0) sub = choose_sub(L.Ngm ? (double)L.nnz_gm / (double)L.Ngm : 1.0);
     int64_t elt = a.precision == 1 ? (int64_t)sizeof(float) : (int64_t)sizeof(double);
     int64_t want_smem = (std::max(L.ywin_max, L.xwin_max) + 4) * elt;  // + the 16-byte rounding of a window
+    bool big = a.block != 512;
     switch (sub) {
-        case 1: launch_solve<1>(p, want_smem, st); break;
-        case 2: launch_solve<2>(p, want_smem, st); break;
-        case 4: launch_solve<4>(p, want_smem, st); break;
-        case 8: launch_solve<8>(p, want_smem, st); break;
-        case 16: launch_solve<16>(p, want_smem, st); break;
-        default: launch_solve<32>(p, want_smem, st); break;
+        case 1: big ? launch_solve<1, 1024>(p, want_smem, st) : launch_solve<1, 512>(p, want_smem, st); break;
+        case 2: big ? launch_solve<2, 1024>(p, want_smem, st) : launch_solve<2, 512>(p, want_smem, st); break;
+        case 4: big ? launch_solve<4, 1024>(p, want_smem, st) : launch_solve<4, 512>(p, want_smem, st); break;
+        case 8: big ? launch_solve<8, 1024>(p, want_smem, st) : launch_solve<8, 512>(p, want_smem, st); break;
+        case 16: big ? launch_solve<16, 1024>(p, want_smem, st) : launch_solve<16, 512>(p, want_smem, st); break;
+        default: big ? launch_solve<32, 1024>(p, want_smem, st) : launch_solve<32, 512>(p, want_smem, st); break;
     }
     int err = read_scalar(d_err, st);
     if (err != 0) throw Error{-4, "bounded wait expired in the sweep kernel"};
@@ -1055,7 +1064,8 @@ __global__ void fill_ones(double* p, int64_t n)
 }
 }  // namespace
 
-double time_sweep(const SweepLayout& L, int sub, int precision, int* d_err, cudaStream_t st)
+double time_sweep(const SweepLayout& L, int sub, int precision, int block, int staging, int* d_err,
+                  cudaStream_t st)
 {
     // scratch system state: x = 0, f = 1 (every sweep does its full work)
     DBuf<double> x(std::max<int64_t>(L.N, 1), st), f(std::max<int64_t>(L.Ngm, 1), st);
@@ -1071,6 +1081,8 @@ double time_sweep(const SweepLayout& L, int sub, int precision, int* d_err, cuda
         a.check_every = 1 << 30;
         a.tol = -1.0;  // never met: exactly maxit sweeps
         a.sub = sub;
+        a.block = block;
+        a.staging = staging;
         a.max_outer = 1;
         a.inner_sweeps = 0;
         float t2 = 0.f, t8 = 0.f;

@@ -14,13 +14,15 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 STRUCTS = {
     "obk_csr": ("_Csr", ["row_ptr", "col_idx", "val", "nnz", "device_ptrs"]),
     "obk_opts": ("Opts", ["precision", "check_every", "inner_sweeps", "max_outer", "stagnation",
-                          "timeout_spins", "rows_per_warp", "pinv_iters", "sync_mode", "staging"]),
+                          "timeout_spins", "rows_per_warp", "pinv_iters", "sync_mode", "staging", "block_threads",
+                          "reserved"]),
     "obk_info": ("_Info", ["sweeps", "rel_res", "setup_ms", "solve_ms", "groups", "bandwidth_before",
                            "bandwidth_after", "outer_iters", "sweep_ms", "n_conflicts", "status"]),
     "obk_block_opts": ("BlockOpts", ["k", "inner_max", "thr", "inner_tol", "n_pairs", "n_nclass", "cgls_steps"]),
     "obk_gstats": ("_GStats", ["N", "nonzero_entries", "abs_cos_sum", "zn", "nn", "groups", "min_group_rows",
                                "max_group_rows", "conflicts", "color_rounds"]),
-    "obk_tune": ("_Tune", ["rows_per_warp", "sweep_ms", "candidate_ms"]),
+    "obk_tune": ("_Tune", ["rows_per_warp", "block_threads", "staging", "n_candidates", "sweep_ms",
+                           "candidate_ms"]),
     "obk_peaks": ("_Peaks", ["fp64_fma_tflops", "fp32_fma_tflops", "l2_gather_g_per_s", "l2_read_gbs"]),
 }
 

@@ -278,18 +278,42 @@ def test_rows_per_warp_variants_agree(obk, rpw):
 
 
 def test_autotune_keeps_results_and_parity(obk):
+    """The autotuner times every (rows per warp, block size, x/y placement)
+    setting; whichever it keeps, and each candidate forced through the options,
+    must give the oracle's x after the same sweeps (FP64) and the same result
+    as the default setting (precision form)."""
     s, _ = _case("knn_30000")
     A = s.A
     st_o, x_o, io = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1, tol=1e-300, maxit=5)
     with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
         t = h.autotune(0)
-        assert t["rows_per_warp"] in (1, 2, 4, 8, 16, 32) and t["sweep_ms"] > 0
-        assert t["candidate_ms"][t["rows_per_warp"]] == t["sweep_ms"]
+        assert t["rows_per_warp"] in (1, 2, 4, 8, 16, 32) and t["block_threads"] in (512, 1024)
+        assert t["staging"] in ("global", "shared") and t["sweep_ms"] > 0
+        key = (t["rows_per_warp"], t["block_threads"], t["staging"])
+        assert t["candidate_ms"][key] == t["sweep_ms"]
+        timed = [k for k, ms in t["candidate_ms"].items() if ms > 0]
+        assert {(32, 1024, "global"), (32, 1024, "shared"), (32, 512, "global"), (32, 512, "shared")} <= set(timed)
         t1 = h.autotune(1)
         assert t1["rows_per_warp"] in (1, 2, 4, 8, 16, 32)
-        st, x, info = h.solve(s.f, None, tol=1e-300, maxit=5)
-    assert info.sweeps == 5
-    assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) <= XTOL
+        st, x, info = h.solve(s.f, None, tol=1e-300, maxit=5)  # the tuned FP64 setting
+        assert info.sweeps == 5
+        assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) <= XTOL
+        ref32 = {}
+        for block in (1024, 512):
+            _, ref32[block], _ = h.solve(s.f, None, tol=1e-9, maxit=3000,
+                                         opts=obk.Opts(precision=1, rows_per_warp=32, block_threads=block, staging=2))
+        # the residual's partial sums follow the grid, so the two block sizes
+        # agree to the parity bound, not bit for bit
+        assert np.linalg.norm(ref32[512] - ref32[1024]) <= XTOL * np.linalg.norm(ref32[1024])
+        for rpw, block, place in timed:
+            o = obk.Opts(rows_per_warp=rpw, block_threads=block, staging=1 if place == "shared" else 2)
+            st, x, info = h.solve(s.f, None, tol=1e-300, maxit=5, opts=o)
+            assert info.sweeps == 5
+            assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) <= XTOL, (rpw, block, place)
+            if rpw == 32:  # the sliced kernels: the placement changes no bit
+                o32 = obk.Opts(precision=1, rows_per_warp=32, block_threads=block, staging=1 if place == "shared" else 2)
+                _, x32, _ = h.solve(s.f, None, tol=1e-9, maxit=3000, opts=o32)
+                assert np.array_equal(x32.view(np.uint64), ref32[block].view(np.uint64)), (block, place)
 
 
 def test_batched_small_systems_match_single_solves(obk):
