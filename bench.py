@@ -659,7 +659,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison and the n=200k parity")
     ap.add_argument("--sweep-probe", action="store_true",
                     help="only the 10- and 60-sweep solves of the roofline (for an ncu capture)")
-    ap.add_argument("--sync-mode", type=int, default=0, help="sweep-probe: 0 band-local waits, 1 grid barriers")
+    ap.add_argument("--sync-mode", type=int, default=0, help="sweep-probe: 0 default, 1 grid barriers, 2 band-local counters")
     ap.add_argument("--staging", type=int, default=0, help="sweep-probe: 1 = staged windows")
     ap.add_argument("--precision-study", action="store_true", help="FP64 vs FP32+IR to 1e-10 (extra run)")
     ap.add_argument("--pn", type=int, default=4_000_000, help="n of the precision study")
@@ -757,8 +757,9 @@ def main():
         tune64 = ht.autotune(0)  # the FP64 comparison solve uses its own setting
     ht.close()
     tune_line = {"precision": prec, "rows_per_warp": tune["rows_per_warp"], "block_threads": tune["block_threads"],
-                 "staging": tune["staging"], "sweep_ms": round(tune["sweep_ms"], 5),
-                 "candidates_ms": {f"{k[0]}x{k[1]}_{k[2]}": round(val, 5) for k, val in tune["candidate_ms"].items()}}
+                 "sync": tune["sync"], "staging": tune["staging"], "sweep_ms": round(tune["sweep_ms"], 5),
+                 "candidates_ms": {f"rpw{k[0]}_block{k[1]}_{k[2]}_{k[3]}": round(val, 5)
+                                   for k, val in tune["candidate_ms"].items()}}
 
     def step(opts=solve_opts):
         h = obk.Handle(rp, ci, v, A.m, A.n, thr=cfg["thr"], stream=stream.cuda_stream)
@@ -842,13 +843,13 @@ def main():
     roof = roofline_of(sw_ms, nnz_gm, N, prec, hbm_peak, hbm_src, measured, sweep_traffic(args.workload))
     roof["autotune"] = tune_line
     roof["sweep_ms_grid_barriers"] = round(sweep_time(obk, h, f, x, stream, prec, sync_mode=1), 5)
-    roof["sweep_ms_staged_windows"] = round(sweep_time(obk, h, f, x, stream, prec, staging=1), 5)
+    roof["sweep_ms_band_counters"] = round(sweep_time(obk, h, f, x, stream, prec, sync_mode=2), 5)
     roof_fp64 = None
     if prec == 1:
         sw64 = sweep_time(obk, h, f, x, stream, 0)
         roof_fp64 = roofline_of(sw64, nnz_gm, N, 0, hbm_peak, hbm_src, measured, None)
         roof_fp64["sweep_ms_grid_barriers"] = round(sweep_time(obk, h, f, x, stream, 0, sync_mode=1), 5)
-        roof_fp64["sweep_ms_staged_windows"] = round(sweep_time(obk, h, f, x, stream, 0, staging=1), 5)
+        roof_fp64["sweep_ms_band_counters"] = round(sweep_time(obk, h, f, x, stream, 0, sync_mode=2), 5)
     h.close()
 
     e2e = None

@@ -91,13 +91,16 @@ typedef struct {
                                group; the steps converge when every row's sum of |cos|
                                to the rest of its group is below one.  Ignored by
                                precision 1.  Negative values are OBK_ERR_INVALID.     */
-    int32_t sync_mode;      /* ordering of the group steps on the device: 0 (default) =
-                               band-local step counters: after RCM a block's rows and
-                               columns touch only nearby blocks' tiles, so each phase
-                               waits only for those blocks to finish the earlier
-                               phases (same arithmetic, same results); 1 = a grid-wide
-                               barrier after every phase.  pinv_iters > 0 and
-                               rows_per_warp < 32 always use barriers.               */
+    int32_t sync_mode;      /* ordering of the group steps on the device: 0 = default
+                               (the autotuned choice, else band-local counters for
+                               systems that fill the GPU with few groups and grid
+                               barriers otherwise); 1 = a grid-wide barrier after every
+                               phase; 2 = band-local step counters: after RCM a
+                               block's rows and columns touch only nearby blocks'
+                               tiles, so each phase waits only for those blocks to
+                               finish the earlier phases.  Same arithmetic, same
+                               results.  pinv_iters > 0 and rows_per_warp < 32 always
+                               use barriers.                                          */
     int32_t staging;        /* where the band-local sweep reads x and y: 0 = default (the
                                autotuned choice, else 2); 2 = gathers from global
                                memory through L1 and L2; 1 = each
@@ -108,8 +111,9 @@ typedef struct {
                                no longer L1, which the other steps' gathers lose).  Same
                                results either way.                                    */
     int32_t block_threads;  /* threads per block of the sweep kernel: 0 = default (the
-                               autotuned choice, else 1024), 1024 (one block per SM,
-                               owning two tiles) or 512 (two per SM, one tile each).  */
+                               autotuned choice, else 1024 with band-local counters and
+                               512 with barriers), 1024 (one block per SM, owning two
+                               tiles) or 512 (two per SM, one tile each).             */
     int32_t reserved;       /* must be 0 */
 } obk_opts;
 
@@ -316,22 +320,28 @@ typedef struct {
                                     block per SM, two tiles each) or 512 (two per SM)          */
     int32_t staging;             /* chosen placement of the x / y windows: 2 = gathered from
                                     global memory (L1/L2), 1 = staged in shared memory        */
+    int32_t sync_mode;           /* chosen ordering: 1 = grid barriers, 2 = band-local counters */
     int32_t n_candidates;        /* settings timed: entries of candidate_ms in use             */
+    int32_t reserved;
     double sweep_ms;             /* device time of one sweep with the chosen setting           */
-    double candidate_ms[12];     /* one sweep for each candidate, in this order (0 = skipped):
-                                    rows per warp 32 with (block, placement) = (1024, global),
-                                    (1024, shared), (512, global), (512, shared); then rows per
-                                    warp 16, 8, 4, 2, 1 with blocks of 1024 and of 512 in turn,
-                                    as far as they fit (a sub-warp per row reads the group-
-                                    major rows through L1/L2 only)                             */
+    double candidate_ms[16];     /* one sweep for each candidate, in this order (0 = skipped):
+                                    rows per warp 32 with (block, ordering, placement) =
+                                    (1024, counters, global), (1024, counters, shared),
+                                    (512, counters, global), (512, counters, shared),
+                                    (1024, barriers), (512, barriers); then rows per warp
+                                    16, 8, 4, 2 with barriers and blocks of 1024 and 512 in
+                                    turn (a sub-warp per row reads the group-major rows
+                                    through L1/L2 only); candidates with more lanes per row
+                                    than twice the mean row length are skipped            */
 } obk_tune;
 
 /* Autotuner of the sweep kernel for a prepared system: times a few sweeps (on
  * zero vectors, so the handle's results are unaffected) for each candidate
- * setting -- lanes per row, threads per block, and where the band-local sweep
- * reads x and y (global memory through L1/L2, or windows staged in shared
- * memory) -- and keeps the fastest for later solves of h whose opts leave
- * rows_per_warp, block_threads and staging at 0.  The choice also goes into a
+ * setting -- lanes per row, threads per block, grid barriers or band-local
+ * counters, and where the band-local sweep reads x and y (global memory
+ * through L1/L2, or windows staged in shared memory) -- and keeps the fastest for
+ * later solves of h whose opts leave rows_per_warp, block_threads, staging and
+ * sync_mode at 0.  The choice also goes into a
  * process-wide table keyed by (device, size class, mean row length, bandwidth
  * class after RCM, precision) that other handles of the same shape use until
  * they are tuned themselves.  precision: 0 (FP64 sweeps) or 1 (FP32 inner

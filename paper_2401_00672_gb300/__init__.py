@@ -69,7 +69,8 @@ class BlockOpts(ctypes.Structure):
 
 class _Tune(ctypes.Structure):
     _fields_ = [("rows_per_warp", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("staging", ctypes.c_int32),
-                ("n_candidates", ctypes.c_int32), ("sweep_ms", ctypes.c_double), ("candidate_ms", ctypes.c_double * 12)]
+                ("sync_mode", ctypes.c_int32), ("n_candidates", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("sweep_ms", ctypes.c_double), ("candidate_ms", ctypes.c_double * 16)]
 
 
 class _Info(ctypes.Structure):
@@ -255,17 +256,22 @@ class Handle:
         n = lib.obk_get_setup_profile(self._h, ms, 16)
         return {name: round(ms[i], 4) for i, name in enumerate(self.SETUP_STAGES[:n])}
 
-    TUNE_CANDIDATES = ((32, 1024, "global"), (32, 1024, "shared"), (32, 512, "global"), (32, 512, "shared"),
-                       (16, 1024, "global"), (16, 512, "global"), (8, 1024, "global"), (8, 512, "global"),
-                       (4, 1024, "global"), (4, 512, "global"), (2, 1024, "global"), (2, 512, "global"))
+    TUNE_CANDIDATES = ((32, 1024, "counters", "global"), (32, 1024, "counters", "shared"),
+                       (32, 512, "counters", "global"), (32, 512, "counters", "shared"),
+                       (32, 1024, "barriers", "global"), (32, 512, "barriers", "global"),
+                       (16, 1024, "barriers", "global"), (16, 512, "barriers", "global"),
+                       (8, 1024, "barriers", "global"), (8, 512, "barriers", "global"),
+                       (4, 1024, "barriers", "global"), (4, 512, "barriers", "global"),
+                       (2, 1024, "barriers", "global"), (2, 512, "barriers", "global"))
 
     def autotune(self, precision: int = 0) -> dict:
-        """obk_autotune: time the (rows per warp, threads per block, x/y placement)
-        settings and keep the fastest.  candidate_ms maps each timed setting to
-        its sweep time (0 = skipped)."""
+        """obk_autotune: time the (rows per warp, threads per block, ordering,
+        x/y placement) settings and keep the fastest.  candidate_ms maps each
+        timed setting to its sweep time (0 = skipped)."""
         t = _Tune()
         _check(lib.obk_autotune(self._h, int(precision), ctypes.byref(t)), "obk_autotune")
         return {"rows_per_warp": t.rows_per_warp, "block_threads": t.block_threads,
+                "sync": "counters" if t.sync_mode == 2 else "barriers",
                 "staging": "shared" if t.staging == 1 else "global", "sweep_ms": t.sweep_ms,
                 "candidate_ms": dict(zip(self.TUNE_CANDIDATES, list(t.candidate_ms)[: t.n_candidates]))}
 

@@ -443,7 +443,7 @@ obk_status obk_solve_ex(obk_handle* h, const obk_opts* opts, const double* f, co
     if (o.check_every < -1 || o.inner_sweeps < 0 || o.max_outer < 0 || o.timeout_spins < 0)
         throw Error{-1, "negative option"};
     if (o.pinv_iters < 0) throw Error{-1, "pinv_iters must be >= 0"};
-    if (o.sync_mode != 0 && o.sync_mode != 1) throw Error{-1, "sync_mode must be 0 or 1"};
+    if (o.sync_mode < 0 || o.sync_mode > 2) throw Error{-1, "sync_mode must be 0, 1 or 2"};
     if (o.staging < 0 || o.staging > 2) throw Error{-1, "staging must be 0, 1 or 2"};
     if (o.block_threads != 0 && o.block_threads != 512 && o.block_threads != 1024)
         throw Error{-1, "block_threads must be 0, 512 or 1024"};
@@ -503,9 +503,9 @@ obk_status obk_solve_ex(obk_handle* h, const obk_opts* opts, const double* f, co
     TuneChoice tc = tuned_or_rule(h, o.precision);
     a.sub = o.rows_per_warp > 0 ? 32 / o.rows_per_warp : tc.sub;
     a.pinv_iters = o.precision == 0 ? o.pinv_iters : 0;
-    a.sync_mode = o.sync_mode;
+    a.sync_mode = o.sync_mode != 0 ? o.sync_mode : (tc.sync != 0 ? tc.sync : default_sync_mode(h->L));
     a.staging = o.staging != 0 ? o.staging : (tc.staging != 0 ? tc.staging : 2);
-    a.block = o.block_threads != 0 ? o.block_threads : (tc.block != 0 ? tc.block : 1024);
+    a.block = o.block_threads != 0 ? o.block_threads : (tc.block != 0 ? tc.block : (a.sync_mode == 2 ? 1024 : 512));
     if (a.pinv_iters > 0 && !h->L.has_gram) build_group_gram(h->L, h->err.p, st);
     SolveResult r = run_solve(h->L, fgm.p, fnorm2, zero_f2, xt.p, a, h->err.p, st);
     // x = P^T x~, then x^(1:n)
@@ -733,18 +733,19 @@ obk_status obk_autotune(obk_handle* h, int32_t precision, obk_tune* out)
     OBK_CUDA(cudaSetDevice(h->device));
     obk_tune t{};
     // candidates in the order documented in obk.h
-    std::vector<TuneChoice> cand = {{1, 1024, 2}, {1, 1024, 1}, {1, 512, 2}, {1, 512, 1}};
+    std::vector<TuneChoice> cand = {{1, 1024, 2, 2}, {1, 1024, 1, 2}, {1, 512, 2, 2}, {1, 512, 1, 2},
+                                    {1, 1024, 2, 1}, {1, 512, 2, 1}};
     const double avg = h->L.Ngm ? (double)h->L.nnz_gm / (double)h->L.Ngm : 1.0;
-    for (int sub : {2, 4, 8, 16, 32})
-        for (int block : {1024, 512}) cand.push_back(TuneChoice{sub, block, 2});
+    for (int sub : {2, 4, 8, 16})
+        for (int block : {1024, 512}) cand.push_back(TuneChoice{sub, block, 2, 1});
     double best = 1e300;
-    TuneChoice choice{1, 1024, 2};
+    TuneChoice choice{1, 512, 2, 1};
     int k = 0;
     for (const TuneChoice& c : cand) {
-        if (k >= 12) break;
+        if (k >= 16) break;
         double ms = 0.0;
         if (!(c.sub > 2 * avg + 2)) {  // more lanes than entries: skip
-            ms = time_sweep(h->L, c.sub, precision, c.block, c.staging, h->err.p, h->st);
+            ms = time_sweep(h->L, c.sub, precision, c.block, c.staging, c.sync, h->err.p, h->st);
             if (ms < best) { best = ms; choice = c; }
         }
         t.candidate_ms[k++] = ms;
@@ -753,6 +754,7 @@ obk_status obk_autotune(obk_handle* h, int32_t precision, obk_tune* out)
     t.rows_per_warp = 32 / choice.sub;
     t.block_threads = choice.block;
     t.staging = choice.staging;
+    t.sync_mode = choice.sync;
     t.sweep_ms = best;
     h->tuned[precision] = choice;
     {

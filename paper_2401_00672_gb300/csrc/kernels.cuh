@@ -206,7 +206,7 @@ struct SolveArgs {
     int64_t maxit = 1000;
     long long spin_limit = kDefaultSpins;
     int sub = 0;  // lanes per row (0 = choose)
-    int sync_mode = 0;  // 0 = band-local step counters between the phases, 1 = grid barriers
+    int sync_mode = 1;  // 1 = grid barriers between the phases, 2 = band-local step counters
     int staging = 0;    // band-local sweep: 1 = x and y windows in shared memory when worth it, 0 or 2 = never
     int block = 1024;   // threads per block of the sweep kernel: 1024 (one per SM) or 512 (two per SM)
 };
@@ -222,7 +222,7 @@ struct SolveResult {
 // Device time (ms) of one sweep with `sub` lanes per row (0 = default rule),
 // `block` threads per block and the given staging mode, measured on zero
 // vectors as the difference of 2- and 8-sweep solves.
-double time_sweep(const SweepLayout& L, int sub, int precision, int block, int staging, int* d_err,
+double time_sweep(const SweepLayout& L, int sub, int precision, int block, int staging, int sync_mode, int* d_err,
                   cudaStream_t st);
 
 // A setting of the sweep kernel chosen by the autotuner (sub = 0: none).
@@ -230,7 +230,13 @@ struct TuneChoice {
     int sub = 0;      // lanes per row
     int block = 0;    // threads per block
     int staging = 0;  // 1 = staged windows in shared memory, 2 = global memory
+    int sync = 0;     // 1 = grid barriers, 2 = band-local step counters
 };
+
+// Ordering used when neither the options nor the autotuner fix it: band-local
+// counters only for systems whose layout fills every tile of the GPU and that
+// have few groups (each counter step costs more than a barrier on a small grid).
+int default_sync_mode(const SweepLayout& L);
 
 // Lanes per row chosen by the fixed rule from the mean row length.
 int choose_sub(double avg_row);

@@ -524,32 +524,54 @@ __global__ void column_scatter(int64_t nrows, const int64_t* __restrict__ rp, co
 }
 
 // Structurally symmetric square pattern: column c lists the same rows as row c
-// lists columns, so entry e = (i, c) sits at CSC slot rp[c] + (rank of i in
-// row c).  One binary search per entry (kSymBatch of a row at a time); a
-// missing partner sets *asym and the caller falls back to the general path.
+// lists columns, so entry e = (i, c) sits at CSC slot q = rp[c] + (rank of i in
+// row c), and the entry at slot q of row c, (c, i), sits at CSC slot e.  The
+// pattern is symmetric exactly when every entry above the diagonal (c > i)
+// has its mirror (c, i) in row c and there are as many entries below the
+// diagonal as above (the mirror map is then a bijection; columns are distinct
+// in a row).  So only the entries above the diagonal search for their mirror
+// (one binary search, kSymBatch of a row in flight), each search fills both
+// slots, and a diagonal entry is its own slot.  Entries above / below the
+// diagonal are counted into cnt[0] / cnt[1]; a missing mirror sets *asym and
+// the caller falls back to the general path.
 constexpr int kSymBatch = 4;
 
 __global__ void symmetric_slots(int64_t n, int64_t stride, const int64_t* __restrict__ rp,
-                                const int32_t* __restrict__ ci, uint32_t* __restrict__ tsrc, int* asym)
+                                const int32_t* __restrict__ ci, uint32_t* __restrict__ tsrc, int* asym,
+                                unsigned long long* cnt)
 {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k * stride < n;
+    unsigned long long above = 0, below = 0;
+    bool stop = false;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k * stride < n && !stop;
          k += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = k * stride;
         int64_t e1 = rp[i + 1];
         for (int64_t e0 = rp[i]; e0 < e1; e0 += kSymBatch) {
-            if (*(volatile int*)asym) return;  // already known not to be symmetric
+            if (*(volatile int*)asym) {  // already known not to be symmetric
+                stop = true;
+                break;
+            }
+            int32_t c[kSymBatch];
             int64_t lo[kSymBatch], hi[kSymBatch];
 #pragma unroll
             for (int t = 0; t < kSymBatch; ++t) {
+                c[t] = e0 + t < e1 ? ci[e0 + t] : -1;
                 lo[t] = 0;
                 hi[t] = 0;
-                if (e0 + t < e1) {
-                    int32_t c = ci[e0 + t];
-                    lo[t] = rp[c];
-                    hi[t] = rp[c + 1];
+                if (c[t] > i) {
+                    lo[t] = rp[c[t]];
+                    hi[t] = rp[c[t] + 1];
+                    ++above;
+                } else if (c[t] == i) {
+                    tsrc[e0 + t] = (uint32_t)(e0 + t);
+                } else if (c[t] >= 0) {
+                    ++below;
                 }
             }
             // first position in [lo, hi) whose column is >= i
+            int64_t end[kSymBatch];
+#pragma unroll
+            for (int t = 0; t < kSymBatch; ++t) end[t] = hi[t];
             bool more = true;
             while (more) {
                 more = false;
@@ -564,13 +586,24 @@ __global__ void symmetric_slots(int64_t n, int64_t stride, const int64_t* __rest
             }
 #pragma unroll
             for (int t = 0; t < kSymBatch; ++t)
-                if (e0 + t < e1) {
-                    int32_t c = ci[e0 + t];
+                if (c[t] > i) {
                     int64_t q = lo[t];
-                    if (q < rp[c + 1] && (int64_t)ci[q] == i) tsrc[q] = (uint32_t)(e0 + t);
-                    else *asym = 1;
+                    if (q < end[t] && (int64_t)ci[q] == i) {
+                        tsrc[q] = (uint32_t)(e0 + t);
+                        tsrc[e0 + t] = (uint32_t)q;
+                    } else {
+                        *asym = 1;
+                    }
                 }
         }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        above += __shfl_xor_sync(0xffffffffu, above, o);
+        below += __shfl_xor_sync(0xffffffffu, below, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (above | below)) {
+        atomicAdd(cnt, above);
+        atomicAdd(cnt + 1, below);
     }
 }
 
@@ -600,16 +633,29 @@ void transpose_pattern(int64_t nrows, int64_t ncols, const int64_t* rp, const in
         // structurally symmetric patterns (the common case for square systems)
         // need no counting or sorting: the transpose has the pattern itself
         DBuf<int> asym(1, st);
+        DBuf<unsigned long long> cnt(2, st);
         OBK_CUDA(cudaMemsetAsync(asym.p, 0, sizeof(int), st));
+        OBK_CUDA(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(unsigned long long), st));
         // a sample of about 8K rows first: most asymmetric patterns fail it
         int64_t stride = std::max<int64_t>(1, nrows / 8192);
-        symmetric_slots<<<grid(ceil_div(nrows, stride)), kT, 0, st>>>(nrows, stride, rp, ci, tsrc.p, asym.p);
-        OBK_CHECK_LAUNCH();
-        if (stride > 1 && read_scalar(asym.p, st) == 0) {
-            symmetric_slots<<<grid(nrows), kT, 0, st>>>(nrows, 1, rp, ci, tsrc.p, asym.p);
+        if (stride > 1) {
+            symmetric_slots<<<grid(ceil_div(nrows, stride)), kT, 0, st>>>(nrows, stride, rp, ci, tsrc.p, asym.p,
+                                                                         cnt.p);
+            OBK_CHECK_LAUNCH();
+            OBK_CUDA(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(unsigned long long), st));
+        }
+        if (stride == 1 || read_scalar(asym.p, st) == 0) {
+            symmetric_slots<<<grid(nrows), kT, 0, st>>>(nrows, 1, rp, ci, tsrc.p, asym.p, cnt.p);
             OBK_CHECK_LAUNCH();
         }
-        if (read_scalar(asym.p, st) == 0) {
+        struct {
+            unsigned long long c[2];
+            int a;
+        } r{};
+        OBK_CUDA(cudaMemcpyAsync(&r.c, cnt.p, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        OBK_CUDA(cudaMemcpyAsync(&r.a, asym.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        OBK_CUDA(cudaStreamSynchronize(st));
+        if (r.a == 0 && r.c[0] == r.c[1]) {
             OBK_CUDA(cudaMemcpyAsync(cptr.p, rp, (nrows + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
             copy_cols_u32<<<grid(nnz), kT, 0, st>>>(ci, nnz, trow.p);
             OBK_CHECK_LAUNCH();

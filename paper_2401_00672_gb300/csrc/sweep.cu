@@ -914,6 +914,12 @@ void launch_solve(SweepParams& p, int64_t want_smem, cudaStream_t st)
 
 }  // namespace
 
+int default_sync_mode(const SweepLayout& L)
+{
+    DevInfo di = dev_info();
+    return L.T >= (int64_t)di.sms * kTilesPerSm && L.G <= 16 ? 2 : 1;
+}
+
 int64_t sweep_tiles(int64_t N)
 {
     DevInfo di = dev_info();
@@ -1013,7 +1019,7 @@ SolveResult run_solve(const SweepLayout& L, const double* f_gm, double fnorm2, d
     p.precision = a.precision;
     p.inner_sweeps = a.inner_sweeps;
     p.max_outer = a.max_outer > 0 ? a.max_outer : 100;
-    p.dataflow = a.sync_mode == 0 ? 1 : 0;
+    p.dataflow = a.sync_mode == 2 ? 1 : 0;
     p.T = L.T;
     p.sl_tptr = L.sl_tptr.p;
     p.ml_tptr = L.ml_tptr.p;
@@ -1064,7 +1070,7 @@ __global__ void fill_ones(double* p, int64_t n)
 }
 }  // namespace
 
-double time_sweep(const SweepLayout& L, int sub, int precision, int block, int staging, int* d_err,
+double time_sweep(const SweepLayout& L, int sub, int precision, int block, int staging, int sync_mode, int* d_err,
                   cudaStream_t st)
 {
     // scratch system state: x = 0, f = 1 (every sweep does its full work)
@@ -1083,6 +1089,7 @@ double time_sweep(const SweepLayout& L, int sub, int precision, int block, int s
         a.sub = sub;
         a.block = block;
         a.staging = staging;
+        a.sync_mode = sync_mode;
         a.max_outer = 1;
         a.inner_sweeps = 0;
         float t2 = 0.f, t8 = 0.f;

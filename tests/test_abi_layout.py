@@ -21,8 +21,8 @@ STRUCTS = {
     "obk_block_opts": ("BlockOpts", ["k", "inner_max", "thr", "inner_tol", "n_pairs", "n_nclass", "cgls_steps"]),
     "obk_gstats": ("_GStats", ["N", "nonzero_entries", "abs_cos_sum", "zn", "nn", "groups", "min_group_rows",
                                "max_group_rows", "conflicts", "color_rounds"]),
-    "obk_tune": ("_Tune", ["rows_per_warp", "block_threads", "staging", "n_candidates", "sweep_ms",
-                           "candidate_ms"]),
+    "obk_tune": ("_Tune", ["rows_per_warp", "block_threads", "staging", "sync_mode", "n_candidates",
+                           "sweep_ms", "candidate_ms"]),
     "obk_peaks": ("_Peaks", ["fp64_fma_tflops", "fp32_fma_tflops", "l2_gather_g_per_s", "l2_read_gbs"]),
 }
 

@@ -246,10 +246,11 @@ def test_band_waits_equal_grid_barriers(obk, name, precision):
     A = s.A
     base = dict(precision=precision, inner_sweeps=6) if precision else dict(check_every=1)
     with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
-        st0, x0, i0 = h.solve(s.f, tol=1e-9, maxit=3000, opts=obk.Opts(sync_mode=0, **base))
-        st1, x1, i1 = h.solve(s.f, tol=1e-9, maxit=3000, opts=obk.Opts(sync_mode=1, **base))
-    assert st0 == st1 and i0.sweeps == i1.sweeps and i0.outer_iters == i1.outer_iters
-    assert np.array_equal(x0.view(np.uint64), x1.view(np.uint64))
+        for block in (1024, 512):
+            st0, x0, i0 = h.solve(s.f, tol=1e-9, maxit=3000, opts=obk.Opts(sync_mode=2, block_threads=block, **base))
+            st1, x1, i1 = h.solve(s.f, tol=1e-9, maxit=3000, opts=obk.Opts(sync_mode=1, block_threads=block, **base))
+            assert st0 == st1 and i0.sweeps == i1.sweeps and i0.outer_iters == i1.outer_iters
+            assert np.array_equal(x0.view(np.uint64), x1.view(np.uint64)), block
 
 
 @pytest.mark.parametrize("name", ["knn_30000", "random_dominant_2000"])
@@ -288,11 +289,12 @@ def test_autotune_keeps_results_and_parity(obk):
     with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
         t = h.autotune(0)
         assert t["rows_per_warp"] in (1, 2, 4, 8, 16, 32) and t["block_threads"] in (512, 1024)
-        assert t["staging"] in ("global", "shared") and t["sweep_ms"] > 0
-        key = (t["rows_per_warp"], t["block_threads"], t["staging"])
+        assert t["staging"] in ("global", "shared") and t["sync"] in ("barriers", "counters") and t["sweep_ms"] > 0
+        key = (t["rows_per_warp"], t["block_threads"], t["sync"], t["staging"])
         assert t["candidate_ms"][key] == t["sweep_ms"]
         timed = [k for k, ms in t["candidate_ms"].items() if ms > 0]
-        assert {(32, 1024, "global"), (32, 1024, "shared"), (32, 512, "global"), (32, 512, "shared")} <= set(timed)
+        assert {(32, b, "counters", p) for b in (1024, 512) for p in ("global", "shared")} <= set(timed)
+        assert {(32, b, "barriers", "global") for b in (1024, 512)} <= set(timed)
         t1 = h.autotune(1)
         assert t1["rows_per_warp"] in (1, 2, 4, 8, 16, 32)
         st, x, info = h.solve(s.f, None, tol=1e-300, maxit=5)  # the tuned FP64 setting
@@ -301,19 +303,20 @@ def test_autotune_keeps_results_and_parity(obk):
         ref32 = {}
         for block in (1024, 512):
             _, ref32[block], _ = h.solve(s.f, None, tol=1e-9, maxit=3000,
-                                         opts=obk.Opts(precision=1, rows_per_warp=32, block_threads=block, staging=2))
+                                         opts=obk.Opts(precision=1, rows_per_warp=32, block_threads=block,
+                                                       sync_mode=1, staging=2))
         # the residual's partial sums follow the grid, so the two block sizes
         # agree to the parity bound, not bit for bit
         assert np.linalg.norm(ref32[512] - ref32[1024]) <= XTOL * np.linalg.norm(ref32[1024])
-        for rpw, block, place in timed:
-            o = obk.Opts(rows_per_warp=rpw, block_threads=block, staging=1 if place == "shared" else 2)
-            st, x, info = h.solve(s.f, None, tol=1e-300, maxit=5, opts=o)
+        for rpw, block, sync, place in timed:
+            knobs = dict(rows_per_warp=rpw, block_threads=block, sync_mode=2 if sync == "counters" else 1,
+                         staging=1 if place == "shared" else 2)
+            st, x, info = h.solve(s.f, None, tol=1e-300, maxit=5, opts=obk.Opts(**knobs))
             assert info.sweeps == 5
-            assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) <= XTOL, (rpw, block, place)
-            if rpw == 32:  # the sliced kernels: the placement changes no bit
-                o32 = obk.Opts(precision=1, rows_per_warp=32, block_threads=block, staging=1 if place == "shared" else 2)
-                _, x32, _ = h.solve(s.f, None, tol=1e-9, maxit=3000, opts=o32)
-                assert np.array_equal(x32.view(np.uint64), ref32[block].view(np.uint64)), (block, place)
+            assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) <= XTOL, (rpw, block, sync, place)
+            if rpw == 32:  # the sliced kernels: ordering and placement change no bit
+                _, x32, _ = h.solve(s.f, None, tol=1e-9, maxit=3000, opts=obk.Opts(precision=1, **knobs))
+                assert np.array_equal(x32.view(np.uint64), ref32[block].view(np.uint64)), (block, sync, place)
 
 
 def test_batched_small_systems_match_single_solves(obk):
