@@ -400,7 +400,9 @@ OBK_API const char* obk_version(void);
  *       per thread, 2048 threads per SM (2 flop per multiply-add);
  *   l2_gather_g_per_s: 8-byte loads at pseudo-random positions (an integer
  *       hash, no index array) of an 8 MB array that stays in L2, in 1e9/s;
- *   l2_read_gbs: coalesced 32-byte reads of a 32 MB L2-resident array.
+ *   l2_read_gbs: coalesced 32-byte reads of a 32 MB L2-resident array;
+ *   int64_mad_tops / int32_mad_tops: integer multiply-add chains (the index
+ *       arithmetic of sparse kernels), as the FP rates.
  * Takes about 50 ms; allocates 40 MB of device memory for the duration.
  * Errors: OBK_ERR_INVALID (out is NULL), OBK_ERR_NOMEM, OBK_ERR_CUDA. */
 typedef struct {
@@ -408,6 +410,8 @@ typedef struct {
     double fp32_fma_tflops;
     double l2_gather_g_per_s;
     double l2_read_gbs;
+    double int64_mad_tops;   /* 64-bit integer multiply-adds, 1e12 per second */
+    double int32_mad_tops;   /* 32-bit integer multiply-adds, 1e12 per second */
 } obk_peaks;
 OBK_API obk_status obk_measure_peaks(obk_peaks* out);
 

@@ -147,7 +147,8 @@ lib = _load()
 
 class _Peaks(ctypes.Structure):
     _fields_ = [("fp64_fma_tflops", ctypes.c_double), ("fp32_fma_tflops", ctypes.c_double),
-                ("l2_gather_g_per_s", ctypes.c_double), ("l2_read_gbs", ctypes.c_double)]
+                ("l2_gather_g_per_s", ctypes.c_double), ("l2_read_gbs", ctypes.c_double),
+                ("int64_mad_tops", ctypes.c_double), ("int32_mad_tops", ctypes.c_double)]
 
 
 def measure_peaks() -> dict:

@@ -33,6 +33,24 @@ __global__ void __launch_bounds__(kPeakBlock) fma_chains(T* out, int iters, T b,
     if (threadIdx.x == 0 && blockIdx.x == 0) out[1] = s;
 }
 
+// Integer multiply-add chains (64-bit or 32-bit): the index arithmetic of the
+// sparse kernels.
+template <class T>
+__global__ void __launch_bounds__(kPeakBlock) imad_chains(T* out, int iters, T b, T c)
+{
+    T a[kChains];
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) a[k] = (T)(threadIdx.x + k);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) a[k] = a[k] * b + c;
+    }
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) s ^= a[k];
+    if (s == (T)12345) out[0] = s;
+}
+
 // Each thread gathers `iters` 8-byte words at pseudo-random positions of an
 // array of n words (n a power of two) that fits in L2: the position comes from
 // an integer hash, so no index array is read.
@@ -114,6 +132,20 @@ extern "C" obk_status obk_measure_peaks(obk_peaks* out)
             fma_chains<float><<<blocks, kPeakBlock, 0, st>>>(sink32.p, it32, 0.9999f, 1e-4f);
             OBK_CHECK_LAUNCH();
         }, st, 3);
+        obk::DBuf<unsigned long long> isink(4, st);
+        obk::DBuf<unsigned> isink32(4, st);
+        const int iti = 8192;
+        float msi64 = best_ms([&] {
+            imad_chains<unsigned long long><<<blocks, kPeakBlock, 0, st>>>(isink.p, iti, 6364136223846793005ull,
+                                                                          1442695040888963407ull);
+            OBK_CHECK_LAUNCH();
+        }, st, 3);
+        float msi32 = best_ms([&] {
+            imad_chains<unsigned><<<blocks, kPeakBlock, 0, st>>>(isink32.p, iti, 1664525u, 1013904223u);
+            OBK_CHECK_LAUNCH();
+        }, st, 3);
+        out->int64_mad_tops = (double)threads * kChains * iti / (msi64 * 1e-3) / 1e12;
+        out->int32_mad_tops = (double)threads * kChains * iti / (msi32 * 1e-3) / 1e12;
         out->fp64_fma_tflops = 2.0 * threads * kChains * it64 / (ms64 * 1e-3) / 1e12;
         out->fp32_fma_tflops = 2.0 * threads * kChains * it32 / (ms32 * 1e-3) / 1e12;
 

@@ -710,23 +710,6 @@ __global__ void max_row_len(int64_t n, const int64_t* ptr, unsigned long long* m
     }
 }
 
-// histogram of colours; colours below 256 are counted in shared memory first
-__global__ void group_hist(int64_t N, const int32_t* color, int64_t* cnt)
-{
-    __shared__ unsigned h[256];
-    for (int t = threadIdx.x; t < 256; t += blockDim.x) h[t] = 0;
-    __syncthreads();
-    GRID_STRIDE(i, N)
-    {
-        int32_t c = color[i];
-        if (c >= 0 && c < 256) atomicAdd(&h[c], 1u);
-        else if (c >= 256) atomicAdd((unsigned long long*)&cnt[c], 1ull);
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < 256; t += blockDim.x)
-        if (h[t]) atomicAdd((unsigned long long*)&cnt[t], (unsigned long long)h[t]);
-}
-
 __global__ void gm_rows(int64_t Ngm, const uint32_t* order, const int64_t* rp, const double* nsq,
                         int32_t* grp_row, int32_t* gm_of_row, int64_t* len, double* inv, float* inv32)
 {
