@@ -239,6 +239,38 @@ typedef struct {
  * memory owned by the caller.  OBK_ERR_INVALID for NULL arguments. */
 OBK_API obk_status obk_grouping_stats(obk_handle* h, obk_gstats* out);
 
+/* One candidate of obk_select_threshold. */
+typedef struct {
+    double thr;            /* the candidate cosine threshold                              */
+    int64_t groups;        /* groups G at this threshold                                  */
+    int64_t conflicts;     /* row pairs with |cos| >= thr                                 */
+    int64_t probe_sweeps;  /* FP64 sweeps run from x0 = 0                                 */
+    double setup_ms;       /* obk_create device time                                      */
+    double probe_ms;       /* device time of the probe solve (sweeps + two residuals)     */
+    double rel_res;        /* ||f - A x|| / ||f|| after the probe sweeps                  */
+    double rate;           /* contraction per sweep, rel_res^(1 / probe_sweeps)           */
+    double predicted_ms;   /* setup_ms + probe_ms + the sweeps still needed to reach tol
+                              at that rate times probe_ms / probe_sweeps (infinite when
+                              the probe did not contract)                                 */
+} obk_thr_probe;
+
+/* Threshold selection by residual feedback: the paper leaves the choice of thr
+ * to experiment (Sec. 3.6: 0.02 as a global setting after a sweep over six
+ * values) and names its adjustment from residual feedback as future work
+ * (Sec. 5).  For each of the n_cand candidate thresholds (each in (0, 1]) this
+ * builds the system (obk_create) and runs probe_sweeps FP64 sweeps of A x = f
+ * from x0 = 0, measuring the residual after them; a run that reaches tol within
+ * the probe predicts its own time.  The candidate with the smallest predicted
+ * time to ||f - A x|| / ||f|| <= tol is chosen (ties: the earlier candidate):
+ * *out_thr receives it and, when out is not NULL, *out receives its prepared
+ * handle (the caller destroys it; the other handles are destroyed).  probes
+ * (n_cand entries, may be NULL) receive every measurement.  A and f as in
+ * obk_create / obk_solve.  Errors: OBK_ERR_INVALID (bad arguments, n_cand < 1,
+ * probe_sweeps < 1, tol <= 0), and those of obk_create and obk_solve. */
+OBK_API obk_status obk_select_threshold(const obk_csr* A, int64_t m, int64_t n, const double* f,
+                                        const double* thr_cand, int32_t n_cand, int32_t probe_sweeps,
+                                        double tol, double* out_thr, obk_handle** out, obk_thr_probe* probes);
+
 /* Device time of the stages of obk_create, in order: (0) upload, validation
  * and extension, (1) bandwidth of the input, Reverse Cuthill-McKee in four
  * parts: (2) the graph pattern(A^ + A^T), (3) the (degree, index) ranks and

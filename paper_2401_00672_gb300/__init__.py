@@ -28,7 +28,7 @@ EXPORTS = [
     "obk_submit", "obk_poll", "obk_cancel", "obk_server_destroy", "obk_last_error", "obk_version",
     "obk_kernel_launches", "obk_residual", "obk_residual_noalloc", "obk_autotune", "obk_solve_batch",
     "obk_batch_max_n", "obk_get_setup_profile", "obk_grouping_stats", "obk_solve_blocks",
-    "obk_request_footprint", "obk_measure_peaks",
+    "obk_request_footprint", "obk_measure_peaks", "obk_select_threshold",
 ]
 
 
@@ -134,6 +134,7 @@ def _load() -> ctypes.CDLL:
         "obk_solve_blocks": ([vp, vp, vp, vp, dbl, i64, vp, vp], ctypes.c_int32),
         "obk_request_footprint": ([i64, i64, i64], ctypes.c_size_t),
         "obk_measure_peaks": ([vp], ctypes.c_int),
+        "obk_select_threshold": ([vp, i64, i64, vp, vp, i32, i32, dbl, vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -156,6 +157,43 @@ def measure_peaks() -> dict:
     p = _Peaks()
     _check(lib.obk_measure_peaks(ctypes.byref(p)), "obk_measure_peaks")
     return {f[0]: getattr(p, f[0]) for f in _Peaks._fields_}
+
+
+class _ThrProbe(ctypes.Structure):
+    _fields_ = [("thr", ctypes.c_double), ("groups", ctypes.c_int64), ("conflicts", ctypes.c_int64),
+                ("probe_sweeps", ctypes.c_int64), ("setup_ms", ctypes.c_double), ("probe_ms", ctypes.c_double),
+                ("rel_res", ctypes.c_double), ("rate", ctypes.c_double), ("predicted_ms", ctypes.c_double)]
+
+
+def select_threshold(row_ptr, col_idx, val, m, n, f, candidates=(0.02, 0.05, 0.1, 0.2, 0.3), probe_sweeps=6,
+                     tol=1e-8, keep_handle=True):
+    """obk_select_threshold: the candidate thr with the smallest predicted time
+    to tol from a short FP64 probe solve at each.  Returns (thr, Handle or None,
+    list of per-candidate dicts)."""
+    p_rp, dev, k1 = _ptr(row_ptr, np.int64)
+    p_ci, _, k2 = _ptr(col_idx, np.int32)
+    p_v, _, k3 = _ptr(val, np.float64)
+    nnz = int(k1[-1]) if not dev else int(k1[-1].item())
+    csr = _Csr(p_rp, p_ci, p_v, nnz, 1 if dev else 0)
+    pf, _, kf = _ptr(f, np.float64)
+    cand = np.ascontiguousarray(candidates, dtype=np.float64)
+    probes = (_ThrProbe * len(cand))()
+    thr = ctypes.c_double()
+    hv = ctypes.c_void_p()
+    _check(lib.obk_select_threshold(ctypes.byref(csr), int(m), int(n), pf, cand.ctypes.data_as(ctypes.c_void_p),
+                                    len(cand), int(probe_sweeps), float(tol), ctypes.byref(thr),
+                                    ctypes.byref(hv) if keep_handle else None, probes), "obk_select_threshold")
+    h = None
+    if keep_handle:
+        h = Handle.__new__(Handle)
+        h._h = hv
+        h._csr = csr
+        h.m, h.n = m, n
+        N, nz, G = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        lib.obk_get_dims(hv, ctypes.byref(N), ctypes.byref(nz), ctypes.byref(G))
+        h.N, h.nnz, h.G = N.value, nz.value, G.value
+    rows = [{k: getattr(pr, k) for k, _ in _ThrProbe._fields_} for pr in probes]
+    return thr.value, h, rows
 
 
 def request_footprint(m: int, n: int, nnz: int) -> int:

@@ -611,6 +611,73 @@ obk_status obk_solve_blocks(obk_handle* h, obk_block_opts* bo, const double* f, 
     OBK_API_END
 }
 
+obk_status obk_select_threshold(const obk_csr* A, int64_t m, int64_t n, const double* f, const double* thr_cand,
+                                int32_t n_cand, int32_t probe_sweeps, double tol, double* out_thr, obk_handle** out,
+                                obk_thr_probe* probes)
+{
+    OBK_API_BEGIN
+    set_last_error("");
+    if (out) *out = nullptr;
+    if (!A || !f || !thr_cand || !out_thr || n_cand < 1 || probe_sweeps < 1 || !(tol > 0.0))
+        throw Error{-1, "NULL argument, n_cand < 1, probe_sweeps < 1 or tol <= 0"};
+    for (int32_t k = 0; k < n_cand; ++k)
+        if (!(thr_cand[k] > 0.0 && thr_cand[k] <= 1.0)) throw Error{-1, "every candidate must lie in (0, 1]"};
+    obk_handle* best = nullptr;
+    double best_ms = 0.0;
+    int32_t best_k = -1;
+    std::vector<double> x;
+    try {
+        for (int32_t k = 0; k < n_cand; ++k) {
+            obk_handle* h = nullptr;
+            obk_status rc = obk_create(A, m, n, thr_cand[k], &h);
+            if (rc != OBK_OK) throw Error{(int)rc, obk_last_error()};
+            x.assign((size_t)std::max<int64_t>(n, 1), 0.0);
+            obk_opts o{};
+            o.check_every = probe_sweeps;  // residuals at the start and after the probe
+            obk_info info{};
+            rc = obk_solve_ex(h, &o, f, nullptr, tol, probe_sweeps, x.data(), &info);
+            if (rc != OBK_OK && rc != OBK_NOT_CONVERGED) {
+                std::string msg = obk_last_error();
+                obk_destroy(h);
+                throw Error{(int)rc, msg};
+            }
+            obk_thr_probe pr{};
+            pr.thr = thr_cand[k];
+            pr.groups = h->info.groups;
+            pr.conflicts = h->info.n_conflicts;
+            pr.probe_sweeps = info.sweeps;
+            pr.setup_ms = h->info.setup_ms;
+            pr.probe_ms = info.solve_ms;
+            pr.rel_res = info.rel_res;
+            double sweeps = (double)std::max<int64_t>(info.sweeps, 1);
+            pr.rate = info.rel_res > 0.0 ? pow(info.rel_res, 1.0 / sweeps) : 0.0;
+            if (info.rel_res <= tol) pr.predicted_ms = pr.setup_ms + pr.probe_ms;
+            else if (pr.rate > 0.0 && pr.rate < 1.0)
+                pr.predicted_ms = pr.setup_ms + pr.probe_ms +
+                                  ceil(log(tol / info.rel_res) / log(pr.rate)) * (pr.probe_ms / sweeps);
+            else pr.predicted_ms = HUGE_VAL;
+            if (probes) probes[k] = pr;
+            if (best_k < 0 || pr.predicted_ms < best_ms) {
+                if (best) obk_destroy(best);
+                best = h;
+                best_ms = pr.predicted_ms;
+                best_k = k;
+            } else {
+                obk_destroy(h);
+            }
+        }
+    } catch (...) {
+        if (best) obk_destroy(best);
+        throw;
+    }
+    *out_thr = thr_cand[best_k];
+    if (out) *out = best;
+    else obk_destroy(best);
+    set_last_error("");
+    return OBK_OK;
+    OBK_API_END
+}
+
 obk_status obk_grouping_stats(obk_handle* h, obk_gstats* out)
 {
     OBK_API_BEGIN

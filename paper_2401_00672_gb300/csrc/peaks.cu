@@ -74,14 +74,14 @@ __global__ void __launch_bounds__(kPeakBlock) l2_gather(const double* __restrict
 
 // Grid-stride coalesced reads of an L2-resident array, `reps` times over.
 // (the words are combined with integer XOR, so no FP64 add bounds the rate)
-__global__ void __launch_bounds__(kPeakBlock) l2_stream(const ulonglong4* __restrict__ x, int64_t n4, int reps,
+__global__ void __launch_bounds__(kPeakBlock) l2_stream(const ulonglong4_32a* __restrict__ x, int64_t n4, int reps,
                                                         double* out)
 {
     unsigned long long s = 0;
     int64_t tid = (int64_t)blockIdx.x * kPeakBlock + threadIdx.x, nth = (int64_t)gridDim.x * kPeakBlock;
     for (int r = 0; r < reps; ++r)
         for (int64_t i = tid; i < n4; i += nth) {
-            ulonglong4 v = x[i];
+            ulonglong4_32a v = x[i];
             s ^= v.x ^ v.y ^ v.z ^ v.w;
         }
     if (s == 0x123456789abcdefull) out[0] = (double)s;
@@ -162,7 +162,7 @@ extern "C" obk_status obk_measure_peaks(obk_peaks* out)
         out->l2_gather_g_per_s = (double)threads * git / (msg * 1e-3) / 1e9;
         const int reps = 200;
         float mss = best_ms([&] {
-            l2_stream<<<blocks, kPeakBlock, 0, st>>>(reinterpret_cast<const ulonglong4*>(xs.p), ns / 4, reps, sink.p);
+            l2_stream<<<blocks, kPeakBlock, 0, st>>>(reinterpret_cast<const ulonglong4_32a*>(xs.p), ns / 4, reps, sink.p);
             OBK_CHECK_LAUNCH();
         }, st, 3);
         out->l2_read_gbs = (double)ns * 8.0 * reps / (mss * 1e-3) / 1e9;

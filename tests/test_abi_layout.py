@@ -23,6 +23,8 @@ STRUCTS = {
                                "max_group_rows", "conflicts", "color_rounds"]),
     "obk_tune": ("_Tune", ["rows_per_warp", "block_threads", "staging", "sync_mode", "n_candidates",
                            "sweep_ms", "candidate_ms"]),
+    "obk_thr_probe": ("_ThrProbe", ["thr", "groups", "conflicts", "probe_sweeps", "setup_ms", "probe_ms", "rel_res",
+                                     "rate", "predicted_ms"]),
     "obk_peaks": ("_Peaks", ["fp64_fma_tflops", "fp32_fma_tflops", "l2_gather_g_per_s", "l2_read_gbs",
                              "int64_mad_tops", "int32_mad_tops"]),
 }

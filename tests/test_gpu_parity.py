@@ -428,6 +428,36 @@ def test_precision_form_n200k_against_both_oracle_forms(obk):
     assert e64 <= XTOL and e32 <= XTOL, (e64, e32)
 
 
+@pytest.mark.parametrize("name", ["knn_30000", "rect_over_3000x1000"])
+def test_select_threshold_probes_match_oracle(obk, name):
+    """The residual-feedback threshold choice: for every candidate the groups
+    and the residual after the probe sweeps match the oracle's (setup, the same
+    number of sweeps from x0 = 0, residual); the choice is the candidate with
+    the smallest predicted time; the returned handle is prepared with it."""
+    s, _ = _case(name)
+    A = s.A
+    cands = (0.02, 0.1, 0.3)
+    probe = 4
+    thr, h, rows = obk.select_threshold(A.row_ptr, A.col_idx, A.val, A.m, A.n, s.f, cands, probe_sweeps=probe,
+                                        tol=1e-8)
+    try:
+        for r in rows:
+            su = oracle.setup(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=r["thr"])
+            gptr, grows = oracle.group_lists(su.group_of, su.G)
+            x = oracle.sweep(su.N, su.rp, su.ci, su.v, su.nsq, su.f, gptr, grows, np.zeros(su.N), nsweeps=probe)
+            rr = oracle.residual(su.N, su.rp, su.ci, su.v, su.f, x)
+            assert r["groups"] == su.G and r["conflicts"] == su.info.n_conflicts
+            assert r["probe_sweeps"] == probe
+            assert abs(r["rel_res"] - rr) <= 1e-8 * rr, (r["thr"], r["rel_res"], rr)
+            assert abs(r["rate"] - rr ** (1.0 / probe)) <= 1e-8
+        best = min(range(len(rows)), key=lambda k: (rows[k]["predicted_ms"], k))
+        assert thr == cands[best] and h.G == rows[best]["groups"]
+        st, x, info = h.solve(s.f, tol=1e-8, maxit=20000)
+        assert st == obk.OBK_OK
+    finally:
+        h.close()
+
+
 def test_overdetermined_inconsistent_stagnates(obk):
     s = synth.rect_random(3000, 1000, 10, seed=12, noise=1e-3)
     A = s.A
