@@ -99,6 +99,49 @@ __global__ void permute_gather(int64_t N, const int64_t* rp, const int32_t* ci, 
     }
 }
 
+// Rows of at most 32 entries in one pass: one warp per new row k gathers the
+// entries of old row perm[k], relabels their columns, sorts them by the new
+// column with a bitonic network across the lanes (columns of a row are
+// distinct, so the order is unique) and writes them.  Lanes past the row's
+// end carry the largest key and sort last.
+__global__ void permute_rows_warp(int64_t N, const int64_t* rp, const int32_t* ci, const double* v,
+                                  const int32_t* perm, const int32_t* iperm, const int64_t* rp_t, int32_t* ci_t,
+                                  double* v_t)
+{
+    const unsigned full = 0xffffffffu;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = w; k < N; k += nw) {
+        int64_t o = rp[perm[k]], len = rp[perm[k] + 1] - o, d = rp_t[k];
+        uint32_t key = 0xffffffffu;
+        double val = 0.0;
+        if (lane < len) {
+            key = (uint32_t)iperm[ci[o + lane]];
+            val = v[o + lane];
+        }
+#pragma unroll
+        for (int m = 2; m <= 32; m <<= 1) {
+#pragma unroll
+            for (int j = m >> 1; j > 0; j >>= 1) {
+                uint32_t ok = __shfl_xor_sync(full, key, j);
+                double ov = __shfl_xor_sync(full, val, j);
+                bool up = (lane & m) == 0;      // this run sorts ascending
+                bool low = (lane & j) == 0;     // the lower lane keeps the smaller key of an ascending run
+                bool take = (low == up) ? ok < key : ok > key;
+                if (take) {
+                    key = ok;
+                    val = ov;
+                }
+            }
+        }
+        if (lane < len) {
+            ci_t[d + lane] = (int32_t)key;
+            v_t[d + lane] = val;
+        }
+    }
+}
+
 __global__ void permute_finish(int64_t nnz, const uint32_t* keys, const uint32_t* src, const double* v,
                                int32_t* ci_t, double* v_t)
 {
@@ -916,6 +959,11 @@ void permute_csr(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
     OBK_CHECK_LAUNCH();
     exclusive_scan_i64(len.p, rp_t, N, st);
     if (nnz == 0) return;
+    if (max_segment_length(N, rp, st) <= 32) {
+        permute_rows_warp<<<grid_for(N * 32), kBlock, 0, st>>>(N, rp, ci, v, perm, iperm, rp_t, ci_t, v_t);
+        OBK_CHECK_LAUNCH();
+        return;
+    }
     DBuf<uint32_t> keys(nnz, st), src(nnz, st);
     permute_gather<<<grid_for(N * 32), kBlock, 0, st>>>(N, rp, ci, perm, iperm, rp_t, keys.p, src.p);
     OBK_CHECK_LAUNCH();
