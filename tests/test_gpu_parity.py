@@ -717,7 +717,15 @@ def test_pinv_iters_rejected_where_unsupported(obk):
                                     ("rect_under_400x1000", 4), ("components", 3), ("diag", 7)])
 def test_block_form_parity(obk, name, k):
     """Algorithm 4 as printed (k uniform blocks, centroid-cosine classes, CGLS
-    projections): the same classes as the oracle, and x to the parity bound."""
+    projections): the same classes as the oracle, and x within 1e-8.
+
+    The bound is looser than the row-group form's 1e-9 because each block
+    projection is itself an iteration: both sides stop their CGLS runs when the
+    normal-equation residual fell below 1e-13 of its start, and the two runs
+    (different summation orders of the same FP64 arithmetic) can stop a step
+    apart, so each projection is reproduced only to that inner tolerance times
+    the block's conditioning; over ~10 iterations of the outer loop, a few 1e-9
+    of x separate the two results, not rounding."""
     s, _ = _case(name)
     A = s.A
     tol = 1e-9
