@@ -502,6 +502,8 @@ obk_status obk_solve_ex(obk_handle* h, const obk_opts* opts, const double* f, co
     a.spin_limit = o.timeout_spins > 0 ? o.timeout_spins : kDefaultSpins;
     TuneChoice tc = tuned_or_rule(h, o.precision);
     a.sub = o.rows_per_warp > 0 ? 32 / o.rows_per_warp : tc.sub;
+    if (a.sub == 0) a.sub = choose_sub(h->L.Ngm ? (double)h->L.nnz_gm / (double)h->L.Ngm : 1.0);
+    if (a.sub > 1) ensure_gm_csr(h->L, st);  // the sub-warp sweeps read the group-major rows
     a.pinv_iters = o.precision == 0 ? o.pinv_iters : 0;
     a.sync_mode = o.sync_mode != 0 ? o.sync_mode : (tc.sync != 0 ? tc.sync : default_sync_mode(h->L));
     a.staging = o.staging != 0 ? o.staging : (tc.staging != 0 ? tc.staging : 2);
@@ -751,8 +753,15 @@ obk_status obk_solve_batch(obk_handle* const* hs, int32_t count, const obk_opts*
     cudaStream_t st = hs[0]->st;
     DBuf<double> res(3 * (size_t)count, st);
     for (int32_t i = 0; i < count; ++i) {
-        const obk_handle* h = hs[i];
+        obk_handle* h = hs[i];
         if (!h || h->device != dev) throw Error{-1, "every handle must be non-NULL and on one device"};
+        // the batch kernel reads the group-major rows; they are built on the
+        // handle's own stream (their buffers are freed there) and finished
+        // before the batch's stream uses them
+        if (!h->L.has_gm_csr) {
+            ensure_gm_csr(h->L, h->st);
+            OBK_CUDA(cudaStreamSynchronize(h->st));
+        }
         if (!f[i] || !x_out[i] || !is_device_ptr(f[i]) || !is_device_ptr(x_out[i]) ||
             (x0 && x0[i] && !is_device_ptr(x0[i])))
             throw Error{-1, "f, x0 and x_out of a batch must be device memory"};
@@ -805,6 +814,7 @@ obk_status obk_autotune(obk_handle* h, int32_t precision, obk_tune* out)
     const double avg = h->L.Ngm ? (double)h->L.nnz_gm / (double)h->L.Ngm : 1.0;
     for (int sub : {2, 4, 8, 16})
         for (int block : {1024, 512}) cand.push_back(TuneChoice{sub, block, 2, 1});
+    ensure_gm_csr(h->L, h->st);  // for the sub-warp candidates
     double best = 1e300;
     TuneChoice choice{1, 512, 2, 1};
     int k = 0;

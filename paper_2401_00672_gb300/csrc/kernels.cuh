@@ -84,17 +84,28 @@ struct SweepLayout {
     int64_t nnz_gm = 0;     // entries of grouped rows
     int64_t n_conflicts = 0;
     int64_t color_rounds = 0;  // rounds of the fixed-point colouring
-    // group-major CSR: rows of group 0, then group 1, ...
+    // group-major CSR: rows of group 0, then group 1, ...  The row pointers
+    // are always built; the entries (grp_ci, grp_v, grp_v32) only on first use
+    // by ensure_gm_csr (the sub-warp sweeps, the batch kernel, the Gram entries
+    // and the cosine statistics read them; the sliced sweep does not), copied
+    // from the permuted matrix src_* that the handle keeps.
     DBuf<int64_t> grp_rp;   // Ngm+1
     DBuf<int32_t> grp_ci;   // nnz_gm (columns in permuted numbering)
     DBuf<double> grp_v;     // nnz_gm
     DBuf<float> grp_v32;    // nnz_gm (precision form)
+    bool has_gm_csr = false;
+    bool want_fp32 = false;
+    const int64_t* src_rp = nullptr;  // the permuted matrix A~ (owned by the handle)
+    const int32_t* src_ci = nullptr;
+    const double* src_v = nullptr;
     DBuf<double> grp_inv;   // Ngm, 1 / ||A_i||^2
     DBuf<float> grp_inv32;  // Ngm
     DBuf<int32_t> grp_row;  // Ngm, permuted row index of each group-major row
     DBuf<int64_t> gptr;     // G+1 (device)
     std::vector<int64_t> h_gptr;
-    // column mirror for the x update: entries ordered by (group, column, row)
+    // column mirror for the x update: entries ordered by (group, column, row);
+    // seg_order lists the segments in the order of the sliced copy (group,
+    // tile of the column, length, column)
     DBuf<int64_t> gseg_ptr; // G+1, first segment of each group
     std::vector<int64_t> h_gseg_ptr;
     DBuf<int64_t> seg_ptr;  // nseg+1, first mirror entry of each segment
@@ -102,6 +113,7 @@ struct SweepLayout {
     DBuf<int32_t> mir_row;  // nnz_gm, group-major row index
     DBuf<double> mir_val;   // nnz_gm
     DBuf<float> mir_val32;  // nnz_gm
+    DBuf<uint32_t> seg_order;  // nseg
     // Sliced ELL (SELL-32) copies for the persistent sweep.  Inside each group
     // the rows (and the mirror segments) are cut into slices of 32 in their
     // (length, index) order; a slice stores entry j of its 32 rows next to each
@@ -186,12 +198,15 @@ BlockResult run_blocks(int64_t N, const int64_t* rp, const int32_t* ci, const do
                        const int32_t* crow, const double* cval, const double* ft, double* xt, const BlockArgs& a,
                        int* d_err, cudaStream_t st);
 
+// Builds the entries of the group-major CSR if not yet built (setup.cu).
+void ensure_gm_csr(SweepLayout& L, cudaStream_t st);
+
 // Off-diagonal Gram entries of every group of a built layout (setup.cu).
 void build_group_gram(SweepLayout& L, int* d_err, cudaStream_t st);
 
 // Row cosine-table statistics of a built layout (Definitions 1-2 at the row
 // level): nonzero entries and the sum of |cos| in units of 2^-32 (setup.cu).
-void cosine_stats(const SweepLayout& L, int64_t* nz, uint64_t* sum, int* d_err, cudaStream_t st);
+void cosine_stats(SweepLayout& L, int64_t* nz, uint64_t* sum, int* d_err, cudaStream_t st);
 
 // ---- sweep.cu -----------------------------------------------------------------
 

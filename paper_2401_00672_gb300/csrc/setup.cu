@@ -679,57 +679,6 @@ __global__ void seg_keys(int64_t nseg, const int64_t* seg_ptr, const int64_t* gs
     }
 }
 
-__global__ void seg_lengths(int64_t nseg, const uint32_t* order, const int64_t* seg_ptr, int64_t* len)
-{
-    GRID_STRIDE(t, nseg) len[t] = seg_ptr[order[t] + 1] - seg_ptr[order[t]];
-}
-
-// copy the entries of each segment to its new place.  A warp takes 32
-// consecutive destination segments (one contiguous destination range) and its
-// lanes walk that range together: coalesced writes, gathered reads.
-template <class T>
-__global__ void seg_move(int64_t nseg, const uint32_t* order, const int64_t* seg_ptr, const int64_t* new_ptr,
-                         const int32_t* seg_col, int32_t* new_col, const int32_t* mrow, const T* mval,
-                         const float* mval32, int32_t* nrow, T* nval, float* nval32)
-{
-    int lane = threadIdx.x & 31;
-    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t t0 = w * 32; t0 < nseg; t0 += nw * 32) {
-        int64_t t = t0 + lane;
-        int64_t src = 0, d = 0;
-        if (t < nseg) {
-            int64_t s = order[t];
-            src = seg_ptr[s];
-            d = new_ptr[t];
-            new_col[t] = seg_col[s];
-        }
-        int64_t d0 = new_ptr[t0];
-        int64_t d1 = t0 + 32 < nseg ? new_ptr[t0 + 32] : new_ptr[nseg];
-        int nlive = (int)(nseg - t0 < 32 ? nseg - t0 : 32);
-        // entry q of the range belongs to the last segment of the warp whose
-        // destination start is <= q
-        for (int64_t q0 = d0; q0 < d1; q0 += 32) {
-            int64_t q = q0 + lane;
-            int lo = 0;  // branch-free search, the same steps in every lane
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                int cand = lo + step;
-                int64_t dm = __shfl_sync(0xffffffffu, d, cand < nlive ? cand : nlive - 1);
-                if (cand < nlive && dm <= q) lo = cand;
-            }
-            int64_t ds = __shfl_sync(0xffffffffu, d, lo);
-            int64_t ss = __shfl_sync(0xffffffffu, src, lo);
-            if (q < d1) {
-                int64_t from = ss + (q - ds);
-                nrow[q] = mrow[from];
-                nval[q] = mval[from];
-                if (nval32) nval32[q] = mval32[from];
-            }
-        }
-    }
-}
-
 // longest row of a CSR (max over i of ptr[i+1] - ptr[i])
 __global__ void max_row_len(int64_t n, const int64_t* ptr, unsigned long long* mx)
 {
@@ -858,8 +807,20 @@ __global__ void mirror_segments(int64_t M, const uint32_t* order, const int32_t*
 
 // 32 * (longest row of the slice) for every slice; slices of segment q (a
 // group, or a (group, tile) pair) start at slice index sg[q], its items at item_g[q]
+// The items of the sliced copies are CSR rows read through an order: item k
+// is row order[k] of (ptr, idx, val), or row k when order is NULL.  Rows go in
+// (group, tile, length) order straight from the permuted matrix; mirror
+// segments in (group, tile, length, column) order from the (group, column)
+// ordered mirror.
+template <class TO>
+__device__ __forceinline__ int64_t item_row(const TO* order, int64_t k)
+{
+    return order ? (int64_t)order[k] : k;
+}
+
+template <class TO>
 __global__ void sell_lengths(int64_t ns, int64_t G, const int64_t* sg, const int64_t* item_g,
-                             const int64_t* ptr, int64_t* slen, int64_t* row0, int32_t* nrow)
+                             const int64_t* ptr, const TO* order, int64_t* slen, int64_t* row0, int32_t* nrow)
 {
     GRID_STRIDE(s, ns)
     {
@@ -872,7 +833,10 @@ __global__ void sell_lengths(int64_t ns, int64_t G, const int64_t* sg, const int
         int64_t k0 = item_g[lo] + (s - sg[lo]) * 32;
         int64_t k1 = k0 + 32 < item_g[lo + 1] ? k0 + 32 : item_g[lo + 1];
         int64_t mx = 0;
-        for (int64_t k = k0; k < k1; ++k) mx = max(mx, ptr[k + 1] - ptr[k]);
+        for (int64_t k = k0; k < k1; ++k) {
+            int64_t r = item_row(order, k);
+            mx = max(mx, ptr[r + 1] - ptr[r]);
+        }
         slen[s] = 32 * mx;
         if (row0) row0[s] = k0;
         if (nrow) nrow[s] = (int32_t)(k1 - k0);
@@ -883,10 +847,10 @@ __global__ void sell_lengths(int64_t ns, int64_t G, const int64_t* sg, const int
 // A padding entry (value 0) repeats the lane's last index, or the first index
 // of the slice's first item for a lane without an item, so that its load
 // stays inside the band the slice's step waits for.
-template <class TI>
+template <class TI, class TO>
 __global__ void sell_fill(int64_t ns, const int64_t* sl_ptr, const int64_t* row0, const int32_t* nrow,
-                          const int64_t* ptr, const TI* idx, const double* val, TI* sidx, double* sval,
-                          float* sval32)
+                          const int64_t* ptr, const TO* order, const TI* idx, const double* val, TI* sidx,
+                          double* sval, float* sval32)
 {
     GRID_STRIDE(t, ns * 32)
     {
@@ -895,8 +859,9 @@ __global__ void sell_fill(int64_t ns, const int64_t* sl_ptr, const int64_t* row0
         int64_t base = sl_ptr[s], len = (sl_ptr[s + 1] - base) >> 5;
         bool valid = lane < nrow[s];
         int64_t k = row0[s] + lane;
-        int64_t b = valid ? ptr[k] : 0, rl = valid ? ptr[k + 1] - b : 0;
-        TI pad_idx = rl > 0 ? idx[b + rl - 1] : idx[ptr[row0[s]]];
+        int64_t r = valid ? item_row(order, k) : 0;
+        int64_t b = valid ? ptr[r] : 0, rl = valid ? ptr[r + 1] - b : 0;
+        TI pad_idx = rl > 0 ? idx[b + rl - 1] : idx[ptr[item_row(order, row0[s])]];
         for (int64_t j = 0; j < len; ++j) {
             int64_t q = base + 32 * j + lane;
             bool live = j < rl;
@@ -909,13 +874,13 @@ __global__ void sell_fill(int64_t ns, const int64_t* sl_ptr, const int64_t* row0
 }
 
 __global__ void sell_mcol(int64_t nms, const int64_t* row0, const int32_t* nrow, const int32_t* seg_col,
-                          int32_t* mcol)
+                          const uint32_t* order, int32_t* mcol)
 {
     GRID_STRIDE(t, nms * 32)
     {
         int64_t s = t >> 5;
         int lane = (int)(t & 31);
-        mcol[t] = lane < nrow[s] ? seg_col[row0[s] + lane] : -1;
+        mcol[t] = lane < nrow[s] ? seg_col[item_row(order, row0[s] + lane)] : -1;
     }
 }
 
@@ -1002,8 +967,9 @@ __global__ void gm_norms(int64_t Ngm, const int32_t* grp_row, const double* nsq,
 
 }  // namespace
 
-void cosine_stats(const SweepLayout& L, int64_t* nz, uint64_t* sum, int* d_err, cudaStream_t st)
+void cosine_stats(SweepLayout& L, int64_t* nz, uint64_t* sum, int* d_err, cudaStream_t st)
 {
+    ensure_gm_csr(L, st);
     int64_t Ngm = L.Ngm, N = L.N, nnz = L.nnz_gm;
     if (Ngm == 0) {
         *nz = 0;
@@ -1095,6 +1061,7 @@ __global__ void gram_fill(int64_t n, int64_t Ngm, const uint64_t* keys, const ui
 
 void build_group_gram(SweepLayout& L, int* d_err, cudaStream_t st)
 {
+    ensure_gm_csr(L, st);
     int64_t Ngm = L.Ngm, N = L.N, nnz = L.nnz_gm;
     L.gram_ptr.alloc(Ngm + 1, st);
     OBK_CUDA(cudaMemsetAsync(L.gram_ptr.p, 0, (Ngm + 1) * sizeof(int64_t), st));
@@ -1168,7 +1135,8 @@ void build_group_gram(SweepLayout& L, int* d_err, cudaStream_t st)
 // Sliced copies of the group-major rows and of the mirror segments: slices of
 // 32 are cut inside each (group, tile) segment, so the slices of one block's
 // tiles are contiguous in every group.
-void build_sell(SweepLayout& L, bool want_fp32, cudaStream_t st)
+void build_sell(SweepLayout& L, const int64_t* rp, const int32_t* ci, const double* v, bool want_fp32,
+                cudaStream_t st)
 {
     int64_t G = L.G, T = L.T, nsegs = G * T;
     // first slice of each group (slice index of segment g * T)
@@ -1194,8 +1162,8 @@ void build_sell(SweepLayout& L, bool want_fp32, cudaStream_t st)
     L.sl_row0.alloc(std::max<int64_t>(ns, 1), st);
     L.sl_nrow.alloc(std::max<int64_t>(ns, 1), st);
     if (ns) {
-        sell_lengths<<<grid_for(ns), kBlock, 0, st>>>(ns, nsegs, L.sl_tptr.p, L.gt_ptr.p, L.grp_rp.p, slen.p,
-                                                      L.sl_row0.p, L.sl_nrow.p);
+        sell_lengths<int32_t><<<grid_for(ns), kBlock, 0, st>>>(ns, nsegs, L.sl_tptr.p, L.gt_ptr.p, rp, L.grp_row.p,
+                                                               slen.p, L.sl_row0.p, L.sl_nrow.p);
         OBK_CHECK_LAUNCH();
     }
     exclusive_scan_i64(slen.p, L.sl_ptr.p, ns, st);
@@ -1204,9 +1172,9 @@ void build_sell(SweepLayout& L, bool want_fp32, cudaStream_t st)
     L.sv.alloc(std::max<int64_t>(L.sell_nnz, 1), st);
     if (want_fp32) L.sv32.alloc(std::max<int64_t>(L.sell_nnz, 1), st);
     if (ns) {
-        sell_fill<int32_t><<<grid_for(ns * 32), kBlock, 0, st>>>(ns, L.sl_ptr.p, L.sl_row0.p, L.sl_nrow.p,
-                                                                 L.grp_rp.p, L.grp_ci.p, L.grp_v.p, L.sci.p,
-                                                                 L.sv.p, want_fp32 ? L.sv32.p : nullptr);
+        sell_fill<int32_t, int32_t><<<grid_for(ns * 32), kBlock, 0, st>>>(ns, L.sl_ptr.p, L.sl_row0.p, L.sl_nrow.p,
+                                                                          rp, L.grp_row.p, ci, v, L.sci.p, L.sv.p,
+                                                                          want_fp32 ? L.sv32.p : nullptr);
         OBK_CHECK_LAUNCH();
     }
     // mirror segments
@@ -1216,8 +1184,8 @@ void build_sell(SweepLayout& L, bool want_fp32, cudaStream_t st)
     DBuf<int32_t> mnrow(std::max<int64_t>(nms, 1), st);
     L.ml_ptr.alloc(nms + 1, st);
     if (nms) {
-        sell_lengths<<<grid_for(nms), kBlock, 0, st>>>(nms, nsegs, L.ml_tptr.p, L.gts_ptr.p, L.seg_ptr.p, mlen.p,
-                                                       mrow0.p, mnrow.p);
+        sell_lengths<uint32_t><<<grid_for(nms), kBlock, 0, st>>>(nms, nsegs, L.ml_tptr.p, L.gts_ptr.p, L.seg_ptr.p,
+                                                                 L.seg_order.p, mlen.p, mrow0.p, mnrow.p);
         OBK_CHECK_LAUNCH();
     }
     exclusive_scan_i64(mlen.p, L.ml_ptr.p, nms, st);
@@ -1227,13 +1195,28 @@ void build_sell(SweepLayout& L, bool want_fp32, cudaStream_t st)
     L.mv.alloc(std::max<int64_t>(L.msell_nnz, 1), st);
     if (want_fp32) L.mv32.alloc(std::max<int64_t>(L.msell_nnz, 1), st);
     if (nms) {
-        sell_mcol<<<grid_for(nms * 32), kBlock, 0, st>>>(nms, mrow0.p, mnrow.p, L.seg_col.p, L.mcol.p);
+        sell_mcol<<<grid_for(nms * 32), kBlock, 0, st>>>(nms, mrow0.p, mnrow.p, L.seg_col.p, L.seg_order.p, L.mcol.p);
         OBK_CHECK_LAUNCH();
-        sell_fill<int32_t><<<grid_for(nms * 32), kBlock, 0, st>>>(nms, L.ml_ptr.p, mrow0.p, mnrow.p, L.seg_ptr.p,
-                                                                  L.mir_row.p, L.mir_val.p, L.mrow.p, L.mv.p,
-                                                                  want_fp32 ? L.mv32.p : nullptr);
+        sell_fill<int32_t, uint32_t><<<grid_for(nms * 32), kBlock, 0, st>>>(
+            nms, L.ml_ptr.p, mrow0.p, mnrow.p, L.seg_ptr.p, L.seg_order.p, L.mir_row.p, L.mir_val.p, L.mrow.p, L.mv.p,
+            want_fp32 ? L.mv32.p : nullptr);
         OBK_CHECK_LAUNCH();
     }
+}
+
+void ensure_gm_csr(SweepLayout& L, cudaStream_t st)
+{
+    if (L.has_gm_csr) return;
+    int64_t nnz_gm = L.nnz_gm;
+    L.grp_ci.alloc(std::max<int64_t>(nnz_gm, 1), st);
+    L.grp_v.alloc(std::max<int64_t>(nnz_gm, 1), st);
+    if (L.want_fp32) L.grp_v32.alloc(std::max<int64_t>(nnz_gm, 1), st);
+    if (L.Ngm) {
+        gm_copy<<<grid_for(L.Ngm * 32), kBlock, 0, st>>>(L.Ngm, L.grp_row.p, L.src_rp, L.src_ci, L.src_v, L.grp_rp.p,
+                                                         L.grp_ci.p, L.grp_v.p, L.want_fp32 ? L.grp_v32.p : nullptr);
+        OBK_CHECK_LAUNCH();
+    }
+    L.has_gm_csr = true;
 }
 
 void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* v, int64_t nnz,
@@ -1403,12 +1386,13 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
     exclusive_scan_i64(glen.p, L.grp_rp.p, Ngm, st);
     int64_t nnz_gm = read_scalar(L.grp_rp.p + Ngm, st);
     L.nnz_gm = nnz_gm;
-    L.grp_ci.alloc(nnz_gm, st);
-    L.grp_v.alloc(nnz_gm, st);
-    if (want_fp32) L.grp_v32.alloc(nnz_gm, st);
-    gm_copy<<<grid_for(Ngm * 32), kBlock, 0, st>>>(Ngm, L.grp_row.p, rp, ci, v, L.grp_rp.p, L.grp_ci.p,
-                                                   L.grp_v.p, want_fp32 ? L.grp_v32.p : nullptr);
-    OBK_CHECK_LAUNCH();
+    // the group-major copy of the entries is built on first use (ensure_gm_csr):
+    // the sliced copies read the permuted matrix directly
+    L.src_rp = rp;
+    L.src_ci = ci;
+    L.src_v = v;
+    L.want_fp32 = want_fp32;
+    L.has_gm_csr = false;
 
     mark();
     // 6. column mirror: CSC entries stably partitioned by the group of their row
@@ -1449,37 +1433,20 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
                                                        fscan.p, L.seg_ptr.p, L.seg_col.p, L.gseg_ptr.p);
         OBK_CHECK_LAUNCH();
     }
-    // 7. segments of each group ordered by (tile of the column, length, column),
-    // entries moved along; (group, tile) segment starts for the sliced copy
+    // 7. the order of the segments in the sliced copy: by (group, tile of the
+    // column, length, column); the mirror itself stays in (group, column) order
+    // and the sliced copy reads it through this order
     DBuf<int64_t> gts_ptr(nsegs + 1, st);
+    L.seg_order.alloc(std::max<int64_t>(nseg, 1), st);
     if (nseg >= 1) {
         DBuf<uint64_t> sk(nseg, st);
-        DBuf<uint32_t> sorder(nseg, st);
         int slbits = std::min(10, bits_for((uint64_t)max_segment_length(nseg, L.seg_ptr.p, st)));
         seg_keys<<<grid_for(nseg), kBlock, 0, st>>>(nseg, L.seg_ptr.p, L.gseg_ptr.p, L.seg_col.p, G, B, T, slbits,
-                                                    sk.p, sorder.p);
+                                                    sk.p, L.seg_order.p);
         OBK_CHECK_LAUNCH();
-        radix_sort_pairs(sk.p, sorder.p, nseg, sbits + slbits, st);
+        radix_sort_pairs(sk.p, L.seg_order.p, nseg, sbits + slbits, st);
         segment_starts<<<grid_for(nseg + 1), kBlock, 0, st>>>(nseg, sk.p, slbits, nsegs, gts_ptr.p);
         OBK_CHECK_LAUNCH();
-        sk.release();
-        DBuf<int64_t> slen(nseg, st), nptr(nseg + 1, st);
-        seg_lengths<<<grid_for(nseg), kBlock, 0, st>>>(nseg, sorder.p, L.seg_ptr.p, slen.p);
-        OBK_CHECK_LAUNCH();
-        exclusive_scan_i64(slen.p, nptr.p, nseg, st);
-        DBuf<int32_t> ncol(nseg, st), nrow(M, st);
-        DBuf<double> nval(M, st);
-        DBuf<float> nval32;
-        if (want_fp32) nval32.alloc(M, st);
-        seg_move<double><<<grid_for(nseg), kBlock, 0, st>>>(
-            nseg, sorder.p, L.seg_ptr.p, nptr.p, L.seg_col.p, ncol.p, L.mir_row.p, L.mir_val.p,
-            want_fp32 ? L.mir_val32.p : nullptr, nrow.p, nval.p, want_fp32 ? nval32.p : nullptr);
-        OBK_CHECK_LAUNCH();
-        L.seg_ptr = std::move(nptr);
-        L.seg_col = std::move(ncol);
-        L.mir_row = std::move(nrow);
-        L.mir_val = std::move(nval);
-        if (want_fp32) L.mir_val32 = std::move(nval32);
     } else {
         OBK_CUDA(cudaMemsetAsync(gts_ptr.p, 0, (nsegs + 1) * sizeof(int64_t), st));
     }
@@ -1499,7 +1466,7 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
                              cudaMemcpyDeviceToHost, st));
     OBK_CUDA(cudaStreamSynchronize(st));
     // 8. sliced ELL copies for the persistent sweep
-    build_sell(L, want_fp32, st);
+    build_sell(L, rp, ci, v, want_fp32, st);
 }
 
 }  // namespace obk

@@ -954,7 +954,7 @@ SolveResult run_solve(const SweepLayout& L, const double* f_gm, double fnorm2, d
         b32.alloc(std::max<int64_t>(L.Ngm, 1), st);
         y32.alloc(std::max<int64_t>(L.Ngm, 1), st);
         d32.alloc(std::max<int64_t>(L.N, 1), st);
-        if (!L.grp_v32.p && L.nnz_gm > 0) throw Error{-1, "precision form needs the FP32 layout"};
+        if (!L.sv32.p && L.nnz_gm > 0) throw Error{-1, "precision form needs the FP32 layout"};
     }
     OBK_CUDA(cudaMemsetAsync(ctrl.p, 0, 16 * sizeof(double), st));
     OBK_CUDA(cudaMemsetAsync(out.p, 0, 8 * sizeof(int64_t), st));
@@ -1033,6 +1033,8 @@ SolveResult run_solve(const SweepLayout& L, const double* f_gm, double fnorm2, d
     p.gb = GridBarrier{bar.p, d_err, a.spin_limit};
     int sub = a.sub;
     if (sub == 0) sub = choose_sub(L.Ngm ? (double)L.nnz_gm / (double)L.Ngm : 1.0);
+    if (sub > 1 && L.nnz_gm > 0 && (!L.has_gm_csr || (a.precision == 1 && !L.grp_v32.p)))
+        throw Error{-5, "internal error: group-major rows not built"};
     int64_t elt = a.precision == 1 ? (int64_t)sizeof(float) : (int64_t)sizeof(double);
     int64_t want_smem = (std::max(L.ywin_max, L.xwin_max) + 4) * elt;  // + the 16-byte rounding of a window
     bool big = a.block != 512;
