@@ -262,6 +262,9 @@ namespace obk {
 // Keys within a segment should be distinct for a deterministic result.
 void segmented_sort_u32(const int64_t* ptr, int64_t nseg, uint32_t* keys, uint32_t* vals,
                         cudaStream_t st);
+// true when the square pattern (sorted, distinct columns per row) lists (c, i)
+// for every entry (i, c)
+bool pattern_symmetric(int64_t n, const int64_t* rp, const int32_t* ci, int64_t nnz, cudaStream_t st);
 // Transpose of a CSR pattern (nrows x ncols, column indices of each row
 // distinct): column pointers cptr (ncols + 1) and, per column in ascending
 // row order, the row (trow) and the source entry index (tsrc) of each entry.

@@ -533,7 +533,8 @@ __global__ void column_scatter(int64_t nrows, const int64_t* __restrict__ rp, co
 // (one binary search, kSymBatch of a row in flight), each search fills both
 // slots, and a diagonal entry is its own slot.  Entries above / below the
 // diagonal are counted into cnt[0] / cnt[1]; a missing mirror sets *asym and
-// the caller falls back to the general path.
+// the caller falls back to the general path.  With tsrc NULL the kernel only
+// tests the pattern.
 constexpr int kSymBatch = 4;
 
 __global__ void symmetric_slots(int64_t n, int64_t stride, const int64_t* __restrict__ rp,
@@ -563,7 +564,7 @@ __global__ void symmetric_slots(int64_t n, int64_t stride, const int64_t* __rest
                     hi[t] = rp[c[t] + 1];
                     ++above;
                 } else if (c[t] == i) {
-                    tsrc[e0 + t] = (uint32_t)(e0 + t);
+                    if (tsrc) tsrc[e0 + t] = (uint32_t)(e0 + t);
                 } else if (c[t] >= 0) {
                     ++below;
                 }
@@ -589,8 +590,10 @@ __global__ void symmetric_slots(int64_t n, int64_t stride, const int64_t* __rest
                 if (c[t] > i) {
                     int64_t q = lo[t];
                     if (q < end[t] && (int64_t)ci[q] == i) {
-                        tsrc[q] = (uint32_t)(e0 + t);
-                        tsrc[e0 + t] = (uint32_t)q;
+                        if (tsrc) {
+                            tsrc[q] = (uint32_t)(e0 + t);
+                            tsrc[e0 + t] = (uint32_t)q;
+                        }
                     } else {
                         *asym = 1;
                     }
@@ -621,6 +624,46 @@ __global__ void widen_counts(const unsigned* cnt, int64_t n, int64_t* out)
 
 }  // namespace
 
+namespace {
+// Structural symmetry test of a square pattern (sorted, distinct columns per
+// row); with tsrc non-NULL it also fills the transpose slots of a symmetric
+// pattern.  A sample of about 8K rows goes first: most asymmetric patterns fail
+// it before the full pass.
+bool symmetric_pass(int64_t n, const int64_t* rp, const int32_t* ci, uint32_t* tsrc, cudaStream_t st)
+{
+    constexpr int kT = 256;
+    auto grid = [](int64_t m) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(m, kT), 65535)); };
+    DBuf<int> asym(1, st);
+    DBuf<unsigned long long> cnt(2, st);
+    OBK_CUDA(cudaMemsetAsync(asym.p, 0, sizeof(int), st));
+    OBK_CUDA(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(unsigned long long), st));
+    int64_t stride = std::max<int64_t>(1, n / 8192);
+    if (stride > 1) {
+        symmetric_slots<<<grid(ceil_div(n, stride)), kT, 0, st>>>(n, stride, rp, ci, tsrc, asym.p, cnt.p);
+        OBK_CHECK_LAUNCH();
+        OBK_CUDA(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(unsigned long long), st));
+    }
+    if (stride == 1 || read_scalar(asym.p, st) == 0) {
+        symmetric_slots<<<grid(n), kT, 0, st>>>(n, 1, rp, ci, tsrc, asym.p, cnt.p);
+        OBK_CHECK_LAUNCH();
+    }
+    struct {
+        unsigned long long c[2];
+        int a;
+    } r{};
+    OBK_CUDA(cudaMemcpyAsync(&r.c, cnt.p, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    OBK_CUDA(cudaMemcpyAsync(&r.a, asym.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    OBK_CUDA(cudaStreamSynchronize(st));
+    return r.a == 0 && r.c[0] == r.c[1];
+}
+}  // namespace
+
+bool pattern_symmetric(int64_t n, const int64_t* rp, const int32_t* ci, int64_t nnz, cudaStream_t st)
+{
+    if (nnz == 0) return true;
+    return symmetric_pass(n, rp, ci, nullptr, st);
+}
+
 void transpose_pattern(int64_t nrows, int64_t ncols, const int64_t* rp, const int32_t* ci, int64_t nnz,
                        DBuf<int64_t>& cptr, DBuf<uint32_t>& trow, DBuf<uint32_t>& tsrc, cudaStream_t st)
 {
@@ -632,30 +675,7 @@ void transpose_pattern(int64_t nrows, int64_t ncols, const int64_t* rp, const in
     if (nrows == ncols && nnz > 0) {
         // structurally symmetric patterns (the common case for square systems)
         // need no counting or sorting: the transpose has the pattern itself
-        DBuf<int> asym(1, st);
-        DBuf<unsigned long long> cnt(2, st);
-        OBK_CUDA(cudaMemsetAsync(asym.p, 0, sizeof(int), st));
-        OBK_CUDA(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(unsigned long long), st));
-        // a sample of about 8K rows first: most asymmetric patterns fail it
-        int64_t stride = std::max<int64_t>(1, nrows / 8192);
-        if (stride > 1) {
-            symmetric_slots<<<grid(ceil_div(nrows, stride)), kT, 0, st>>>(nrows, stride, rp, ci, tsrc.p, asym.p,
-                                                                         cnt.p);
-            OBK_CHECK_LAUNCH();
-            OBK_CUDA(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(unsigned long long), st));
-        }
-        if (stride == 1 || read_scalar(asym.p, st) == 0) {
-            symmetric_slots<<<grid(nrows), kT, 0, st>>>(nrows, 1, rp, ci, tsrc.p, asym.p, cnt.p);
-            OBK_CHECK_LAUNCH();
-        }
-        struct {
-            unsigned long long c[2];
-            int a;
-        } r{};
-        OBK_CUDA(cudaMemcpyAsync(&r.c, cnt.p, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-        OBK_CUDA(cudaMemcpyAsync(&r.a, asym.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-        OBK_CUDA(cudaStreamSynchronize(st));
-        if (r.a == 0 && r.c[0] == r.c[1]) {
+        if (symmetric_pass(nrows, rp, ci, tsrc.p, st)) {
             OBK_CUDA(cudaMemcpyAsync(cptr.p, rp, (nrows + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
             copy_cols_u32<<<grid(nnz), kT, 0, st>>>(ci, nnz, trow.p);
             OBK_CHECK_LAUNCH();

@@ -75,6 +75,44 @@ __global__ void merge_sym(int64_t N, const int64_t* rp, const int32_t* ci, const
     }
 }
 
+// A structurally symmetric pattern is its own transpose, so the graph is each
+// row without its diagonal entry.  Count: the row length less one when the
+// (sorted) row holds i.
+__global__ void drop_self_count(int64_t N, const int64_t* rp, const int32_t* ci, int64_t* deg)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = rp[i], hi = rp[i + 1];
+        const int64_t len = hi - lo;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)ci[mid] < i) lo = mid + 1;
+            else hi = mid;
+        }
+        deg[i] = len - (lo < rp[i + 1] && (int64_t)ci[lo] == i ? 1 : 0);
+    }
+}
+
+// Copy: one warp per row, the lanes over its entries in order; an entry after
+// the diagonal moves back by one.
+__global__ void drop_self_copy(int64_t N, const int64_t* rp, const int32_t* ci, const int64_t* gp, int32_t* adj)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < N; i += nw) {
+        const int64_t b = rp[i], e1 = rp[i + 1], out = gp[i];
+        int64_t shift = 0;
+        for (int64_t e0 = b; e0 < e1; e0 += 32) {
+            const int64_t e = e0 + lane;
+            const int32_t c = e < e1 ? ci[e] : -1;
+            const unsigned self = __ballot_sync(0xffffffffu, e < e1 && (int64_t)c == i);
+            const int64_t before = shift + __popc(self & ((1u << lane) - 1u));
+            if (e < e1 && (int64_t)c != i) adj[out + (e - b) - before] = c;
+            shift += __popc(self);
+        }
+    }
+}
+
 // ---- ranks in (deg, index) order ---------------------------------------------
 
 __global__ void deg_keys(int64_t N, const int64_t* gp, uint64_t* keys, uint32_t* vals, unsigned long long* dmax)
@@ -917,6 +955,19 @@ cudaStream_t aux_stream()
 void build_sym_graph(int64_t N, const int64_t* rp, const int32_t* ci, int64_t nnz, DBuf<int64_t>& gp,
                      DBuf<int32_t>& adj, cudaStream_t st)
 {
+    if (pattern_symmetric(N, rp, ci, nnz, st)) {
+        DBuf<int64_t> deg(N + 1, st);
+        drop_self_count<<<grid_for(N), kBlock, 0, st>>>(N, rp, ci, deg.p);
+        OBK_CHECK_LAUNCH();
+        gp.alloc(N + 1, st);
+        exclusive_scan_i64(deg.p, gp.p, N, st);
+        int64_t M = read_scalar(gp.p + N, st);
+        adj.alloc(M > 0 ? M : 1, st);
+        drop_self_copy<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(N, kBlock / 32), 65535 * 4)), kBlock, 0, st>>>(
+            N, rp, ci, gp.p, adj.p);
+        OBK_CHECK_LAUNCH();
+        return;
+    }
     // transpose pattern: the rows of each column, ascending
     DBuf<int64_t> tp;
     DBuf<uint32_t> trow, tsrc;

@@ -154,12 +154,24 @@ __global__ void permute_finish(int64_t nnz, const uint32_t* keys, const uint32_t
 
 // ---- norms and transposition -------------------------------------------------
 
+// nsq[i] = ||A_i||^2 as the left fold of the rounded squares over ascending
+// columns, s[i] = sqrt(nsq[i]); one thread per row, the values of a row loaded
+// eight at a time before they are folded in order
 __global__ void row_norms_exact(int64_t N, const int64_t* rp, const double* v, double* nsq, double* s)
 {
     GRID_STRIDE(i, N)
     {
         double acc = 0.0;
-        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) acc = __dadd_rn(acc, __dmul_rn(v[e], v[e]));
+        int64_t e = rp[i];
+        const int64_t e1 = rp[i + 1];
+        for (; e + 8 <= e1; e += 8) {
+            double a[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a[k] = v[e + k];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc = __dadd_rn(acc, __dmul_rn(a[k], a[k]));
+        }
+        for (; e < e1; ++e) acc = __dadd_rn(acc, __dmul_rn(v[e], v[e]));
         nsq[i] = acc;
         s[i] = __dsqrt_rn(acc);
     }

@@ -215,6 +215,34 @@ def test_setup_bit_exact(obk, name):
         assert info.n_conflicts == su.info.n_conflicts
 
 
+def test_setup_symmetric_pattern_with_missing_diagonals(obk):
+    # a structurally symmetric pattern (a 60 x 60 grid plus a kNN block) whose
+    # rows 0, 3, 6, ... hold no diagonal entry: the RCM graph of such a pattern
+    # is each row without its diagonal, taken without the merge with the
+    # transpose; an asymmetric copy (one extra entry) takes the merge
+    rng = np.random.default_rng(41)
+    r, c, v = _grid_coo(60, 60, rng)
+    N = 60 * 60
+    keep_diag = np.arange(N) % 3 != 0
+    d = np.arange(N)[keep_diag]
+    r = np.concatenate([r, d])
+    c = np.concatenate([c, d])
+    v = np.concatenate([v, 4.0 + rng.random(len(d))])
+    for extra in (False, True):
+        rr, cc, vv = r, c, v
+        if extra:
+            rr = np.concatenate([r, [5]])
+            cc = np.concatenate([c, [N - 7]])
+            vv = np.concatenate([v, [0.5]])
+        A = synth.csr_from_coo(N, N, rr, cc, vv)
+        f = A.matvec(rng.standard_normal(N))
+        su = oracle.setup(A.m, A.n, A.row_ptr, A.col_idx, A.val, f, thr=0.1)
+        with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
+            assert np.array_equal(h.perm(), su.perm)
+            assert np.array_equal(h.groups(), su.group_of)
+            assert h.info().bandwidth_after == su.info.bandwidth_after
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_solve_parity(obk, name):
     s, su = _case(name)
