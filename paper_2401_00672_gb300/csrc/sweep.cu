@@ -233,6 +233,34 @@ __device__ __forceinline__ void phase1(const SweepParams& p, int64_t r0, int64_t
 // rows), and the residual f_k starts the accumulator: no shuffle reduction
 // and no separate subtraction.
 
+// The slices' indices and values are read once per sweep: loaded without an
+// L1 line and with an evict-first L2 policy, so that the lines of x and y that
+// the gathers reuse stay cached.  (The matrix is read-only inside the kernel.)
+__device__ __forceinline__ uint64_t stream_policy()
+{
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p, uint64_t pol)
+{
+    int32_t v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float ld_stream(const float* p, uint64_t pol)
+{
+    float v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ld_stream(const double* p, uint64_t pol)
+{
+    double v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
 // acc + S * sum_{j<B} a[q + 32 j] * v[idx[q + 32 j] - off]   (S = -1 or +1; off
 // is the first index held by v when v is a window staged in shared memory)
 template <int B, int S, class T>
@@ -241,10 +269,11 @@ __device__ __forceinline__ T sell_batch(const int32_t* idx, const T* vals, const
 {
     int32_t c[B];
     T a[B];
+    const uint64_t pol = stream_policy();
 #pragma unroll
     for (int j = 0; j < B; ++j) {
-        c[j] = idx[q + 32 * j];
-        a[j] = vals[q + 32 * j];
+        c[j] = ld_stream(idx + q + 32 * j, pol);
+        a[j] = ld_stream(vals + q + 32 * j, pol);
     }
     T g[B];
 #pragma unroll
