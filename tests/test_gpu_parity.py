@@ -5,6 +5,8 @@ match x to ||x_gpu - x_oracle|| / ||x_oracle|| <= 1e-9 after the same number
 of sweeps, and stop within one sweep of the oracle.  Cases span several
 thread blocks and ragged tails, plus the degenerate inputs of the method.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -241,6 +243,68 @@ def test_setup_symmetric_pattern_with_missing_diagonals(obk):
             assert np.array_equal(h.perm(), su.perm)
             assert np.array_equal(h.groups(), su.group_of)
             assert h.info().bandwidth_after == su.info.bandwidth_after
+
+
+def _pair_cosine(rp, ci, v, nsq, i, j):
+    # RN(dot / RN(s_j s_i)), dot the left fold of the products over the columns
+    # rows i and j share, ascending (Sec. 3.3 cosine, the oracle's rounding)
+    a, ae, b, be = int(rp[i]), int(rp[i + 1]), int(rp[j]), int(rp[j + 1])
+    acc = 0.0
+    while a < ae and b < be:
+        if ci[a] == ci[b]:
+            acc = acc + float(v[a]) * float(v[b])
+            a += 1
+            b += 1
+        elif ci[a] < ci[b]:
+            a += 1
+        else:
+            b += 1
+    return acc / (math.sqrt(float(nsq[j])) * math.sqrt(float(nsq[i])))
+
+
+def test_conflicts_at_exact_pair_cosines(obk):
+    # thresholds equal to the cosine of an actual pair (and the doubles next to
+    # it) put that pair exactly on the decision boundary, where no bound on a
+    # lower-precision dot product can decide and the exact FP64 fold must
+    s = synth.knn_dominant(3000, 12, seed=1009)
+    A = s.A
+    base = oracle.setup(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1)
+    rp, ci, v, nsq = base.rp, base.ci, base.v, base.nsq
+    rng = np.random.default_rng(3)
+    picked = []
+    for i in rng.permutation(np.arange(200, base.N)):
+        cand = set()
+        for c in ci[rp[i]:rp[i + 1]]:
+            cand.update(int(j) for j in ci[rp[c]:rp[c + 1]] if j < i)
+        for j in sorted(cand):
+            t = abs(_pair_cosine(rp, ci, v, nsq, int(i), j))
+            if 0.02 <= t <= 0.6:
+                picked.append(t)
+                break
+        if len(picked) == 4:
+            break
+    assert len(picked) == 4
+    for t in picked:
+        for thr in (t, float(np.nextafter(t, np.inf)), float(np.nextafter(t, -np.inf))):
+            su = oracle.setup(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=thr)
+            with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=thr) as h:
+                assert h.info().n_conflicts == su.info.n_conflicts, thr
+                assert np.array_equal(h.groups(), su.group_of), thr
+
+
+def test_conflicts_with_values_outside_the_filter_range(obk):
+    # rows scaled by 2^45 and 2^-45 (and a threshold below 2^-20) leave the
+    # range in which FP32 bounds decide the pairs: every pair is then exact
+    s = synth.random_dominant(2000, 7, seed=1010)
+    A = s.A
+    v = A.val.copy()
+    for i, scale in ((3, 2.0 ** 45), (700, 2.0 ** -45), (1500, 2.0 ** 45)):
+        v[A.row_ptr[i]:A.row_ptr[i + 1]] *= scale
+    for thr in (0.1, 2.0 ** -25):
+        su = oracle.setup(A.m, A.n, A.row_ptr, A.col_idx, v, s.f, thr=thr)
+        with obk.Handle(A.row_ptr, A.col_idx, v, A.m, A.n, thr=thr) as h:
+            assert h.info().n_conflicts == su.info.n_conflicts
+            assert np.array_equal(h.groups(), su.group_of)
 
 
 @pytest.mark.parametrize("name", list(CASES))
