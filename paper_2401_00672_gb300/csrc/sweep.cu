@@ -327,6 +327,19 @@ __device__ __forceinline__ void row_slice(const SweepParams& p, int64_t s, const
     if (valid) y[k] = acc * inv[k];
 }
 
+// one row slice s whose entries [b0, b1) and first row k0 were located ahead
+template <class T, class TR>
+__device__ __forceinline__ void row_slice_at(const SweepParams& p, int64_t s, int64_t b0, int64_t b1, int64_t k0,
+                                             const T* sval, const T* inv, const TR* rhs, const T* xv, T* y)
+{
+    const int lane = threadIdx.x & 31;
+    const bool valid = lane < p.sl_nrow[s];
+    const int64_t k = k0 + lane;
+    T acc = valid ? (T)rhs[k] : T(0);
+    acc = sell_lane<-1, T>(p.sci, sval, xv, b0 + lane, (b1 - b0) >> 5, acc, 0);
+    if (valid) y[k] = acc * inv[k];
+}
+
 // one mirror slice s: xv_c += sum_k A_kc y_k for its (up to) 32 columns
 template <class T>
 __device__ __forceinline__ void col_slice(const SweepParams& p, int64_t s, const T* mval, const T* y, T* xv,
@@ -337,6 +350,17 @@ __device__ __forceinline__ void col_slice(const SweepParams& p, int64_t s, const
     int32_t c = p.mcol[s * 32 + lane];
     T acc = c >= 0 ? xv[c] : T(0);
     acc = sell_lane<1, T>(p.mrow, mval, y, base + lane, len, acc, yoff);
+    if (c >= 0) xv[c] = acc;
+}
+
+// one mirror slice whose lane column c and entries [b0, b1) were loaded ahead
+template <class T>
+__device__ __forceinline__ void col_slice_at(const SweepParams& p, int32_t c, int64_t b0, int64_t b1, const T* mval,
+                                             const T* y, T* xv)
+{
+    const int lane = threadIdx.x & 31;
+    T acc = c >= 0 ? xv[c] : T(0);
+    acc = sell_lane<1, T>(p.mrow, mval, y, b0 + lane, (b1 - b0) >> 5, acc, 0);
     if (c >= 0) xv[c] = acc;
 }
 
@@ -717,7 +741,22 @@ __device__ bool flow_sweep(const SweepParams& p, FlowState& f, const T* sval, co
                 int64_t a0 = stage<T>(win, xv, x0, x1);
                 for (int64_t s = s0 + w; s < s1; s += nw) row_slice<T, TR>(p, s, sval, inv, rhs, win, y, (int32_t)a0);
             } else {
-                for (int64_t s = s0 + w; s < s1; s += nw) row_slice<T, TR>(p, s, sval, inv, rhs, xv, y);
+                // each slice's bounds and first row are loaded one slice ahead
+                int64_t s = s0 + w, nb0 = 0, nb1 = 0, nk0 = 0;
+                if (s < s1) {
+                    nb0 = p.sl_ptr[s];
+                    nb1 = p.sl_ptr[s + 1];
+                    nk0 = p.sl_row0[s];
+                }
+                for (; s < s1; s += nw) {
+                    const int64_t b0 = nb0, b1 = nb1, k0 = nk0;
+                    if (s + nw < s1) {
+                        nb0 = p.sl_ptr[s + nw];
+                        nb1 = p.sl_ptr[s + nw + 1];
+                        nk0 = p.sl_row0[s + nw];
+                    }
+                    row_slice_at<T, TR>(p, s, b0, b1, k0, sval, inv, rhs, xv, y);
+                }
             }
             flow_done(p, f);
         } else {
@@ -731,7 +770,28 @@ __device__ bool flow_sweep(const SweepParams& p, FlowState& f, const T* sval, co
                 int64_t a0 = stage<T>(win, y, y0, y1);
                 for (int64_t s = m0 + w; s < m1; s += nw) col_slice<T>(p, s, mval, win, xv, (int32_t)a0);
             } else {
-                for (int64_t s = m0 + w; s < m1; s += nw) col_slice<T>(p, s, mval, y, xv);
+                // A mirror slice is a chain of three loads (its bounds and
+                // columns, then its entries and x at the columns, then the
+                // gathers of y) for a few entries per lane: the next slice's
+                // bounds and columns are loaded while this one runs.
+                const int lane = threadIdx.x & 31;
+                int64_t s = m0 + w, nb0 = 0, nb1 = 0;
+                int32_t nc = -1;
+                if (s < m1) {
+                    nb0 = p.ml_ptr[s];
+                    nb1 = p.ml_ptr[s + 1];
+                    nc = p.mcol[s * 32 + lane];
+                }
+                for (; s < m1; s += nw) {
+                    const int64_t b0 = nb0, b1 = nb1;
+                    const int32_t c = nc;
+                    if (s + nw < m1) {
+                        nb0 = p.ml_ptr[s + nw];
+                        nb1 = p.ml_ptr[s + nw + 1];
+                        nc = p.mcol[(s + nw) * 32 + lane];
+                    }
+                    col_slice_at<T>(p, c, b0, b1, mval, y, xv);
+                }
             }
             flow_done(p, f);
         } else {
