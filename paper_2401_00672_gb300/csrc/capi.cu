@@ -98,6 +98,50 @@ __global__ void check_finite(const double* a, int64_t n, int* bad)
     GRID_STRIDE(i, n) if (!isfinite(a[i])) atomicOr(bad, 32);
 }
 
+__global__ void values_finite(const double* v, int64_t nnz, int* bad)
+{
+    GRID_STRIDE(k, nnz) if (!isfinite(v[k])) atomicOr(bad, 8);
+}
+
+// The values of a host CSR are first needed by the permutation, after the
+// reordering, which reads only the pattern: their copy runs on a second stream
+// of its own beside the pattern's validation and RCM.  Until the stream that
+// owns the buffer has waited for that copy, the buffer must not go back to the
+// pool and the caller's host array must stay untouched, so every exit waits.
+struct ValueUpload {
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t ready = nullptr;
+    cudaStream_t owner = nullptr;
+    bool pending = false;
+    void start(double* dst, const double* src, int64_t n, cudaStream_t st)
+    {
+        owner = st;
+        OBK_CUDA(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
+        OBK_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+        OBK_CUDA(cudaEventRecord(ready, st));  // dst is allocated in st's order
+        OBK_CUDA(cudaStreamWaitEvent(st2, ready, 0));
+        pending = true;
+        OBK_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, st2));
+        OBK_CUDA(cudaEventRecord(ready, st2));
+    }
+    // later work on the owner stream sees the values
+    void join()
+    {
+        if (!pending) return;
+        OBK_CUDA(cudaStreamWaitEvent(owner, ready, 0));
+        pending = false;
+    }
+    ~ValueUpload()
+    {
+        if (pending) {
+            cudaEventSynchronize(ready);
+            cudaStreamWaitEvent(owner, ready, 0);
+        }
+        if (ready) cudaEventDestroy(ready);
+        if (st2) cudaStreamDestroy(st2);
+    }
+};
+
 __global__ void gather_gm(int64_t Ngm, const int32_t* src, const double* f, int64_t m, double* out)
 {
     GRID_STRIDE(k, Ngm)
@@ -354,16 +398,18 @@ obk_status obk_create_on_stream(const obk_csr* A, int64_t m, int64_t n, double t
         to_device(rp.p, A->row_ptr, m + 1, dev, st);
         const int32_t* ci_p = A->col_idx;
         const double* v_p = A->val;
+        ValueUpload vup;  // declared after v_copy: ends before it is freed
         if (!dev || nnz == 0) {
             ci_copy.alloc(std::max<int64_t>(nnz, 1), st);
             v_copy.alloc(std::max<int64_t>(nnz, 1), st);
             to_device(ci_copy.p, A->col_idx, nnz, dev, st);
-            to_device(v_copy.p, A->val, nnz, dev, st);
+            if (!dev && nnz > 0) vup.start(v_copy.p, A->val, nnz, st);
+            else to_device(v_copy.p, A->val, nnz, dev, st);
             ci_p = ci_copy.p;
             v_p = v_copy.p;
         }
         DBuf<int> bad(1, st);
-        validate_csr(m, n, rp.p, ci_p, v_p, nnz, bad.p, st);
+        validate_csr(m, n, rp.p, ci_p, vup.pending ? nullptr : v_p, nnz, bad.p, st);
         check_rowptr_ends<<<1, 32, 0, st>>>(rp.p, m, nnz, bad.p);
         OBK_CHECK_LAUNCH();
         int b = read_scalar(bad.p, st);
@@ -381,6 +427,13 @@ obk_status obk_create_on_stream(const obk_csr* A, int64_t m, int64_t n, double t
         h->perm.alloc(N, st);
         rcm_reorder(N, rp.p, ci_p, nnz, h->perm.p, kDefaultSpins, h->err.p, &h->rcm, st, &clock);
         clock.mark(st);  // Cuthill-McKee order, reversed
+        if (vup.pending) {  // the values, copied meanwhile, must be finite
+            vup.join();
+            OBK_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+            values_finite<<<grid_for(nnz), kBlock, 0, st>>>(v_p, nnz, bad.p);
+            OBK_CHECK_LAUNCH();
+            if (read_scalar(bad.p, st)) throw Error{-1, "malformed CSR (code 8: non-finite value)"};
+        }
         DBuf<int32_t> iperm(N, st);
         DBuf<int64_t> rpt(N + 1, st);
         DBuf<int32_t> cit(std::max<int64_t>(nnz, 1), st);

@@ -46,7 +46,7 @@ __global__ void validate_rows(int64_t m, int64_t n, const int64_t* rp, const int
             int32_t c = ci[k];
             if (c < 0 || (int64_t)c >= n) { atomicOr(bad, 2); break; }
             if (k > b && c <= ci[k - 1]) { atomicOr(bad, 4); break; }
-            if (!isfinite(v[k])) { atomicOr(bad, 8); break; }
+            if (v && !isfinite(v[k])) { atomicOr(bad, 8); break; }  // v NULL: the pattern only
         }
     }
 }
