@@ -876,7 +876,7 @@ obk_status obk_autotune(obk_handle* h, int32_t precision, obk_tune* out)
         double ms = 0.0;
         if (!(c.sub > 2 * avg + 2)) {  // more lanes than entries: skip
             ms = time_sweep(h->L, c.sub, precision, c.block, c.staging, c.sync, h->err.p, h->st);
-            if (ms < best) { best = ms; choice = c; }
+            if (ms > 0.0 && ms < best) { best = ms; choice = c; }
         }
         t.candidate_ms[k++] = ms;
     }
