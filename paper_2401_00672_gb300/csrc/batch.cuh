@@ -12,6 +12,10 @@ namespace obk {
 // Whether obk_solve_batch can take this system (capi.cu).
 bool batch_eligible(const obk_handle* h);
 
+// Builds what the batch kernel reads (the group-major rows) on the handle's
+// own stream, without waiting (capi.cu); obk_solve_batch does it otherwise.
+void prepare_batch(obk_handle* h);
+
 // The stream a handle was created on (capi.cu).
 void* handle_stream(const obk_handle* h);
 

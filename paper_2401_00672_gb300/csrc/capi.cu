@@ -104,10 +104,37 @@ __global__ void values_finite(const double* v, int64_t nnz, int* bad)
 }
 
 // The values of a host CSR are first needed by the permutation, after the
-// reordering, which reads only the pattern: their copy runs on a second stream
-// of its own beside the pattern's validation and RCM.  Until the stream that
-// owns the buffer has waited for that copy, the buffer must not go back to the
-// pool and the caller's host array must stay untouched, so every exit waits.
+// reordering, which reads only the pattern: for a large matrix in pinned host
+// memory (a copy from pageable memory is staged by the driver and gains
+// nothing) their copy runs on a second stream of the calling thread beside
+// the pattern's validation and RCM.  Until the stream that owns the buffer has
+// waited for that copy, the buffer must not go back to the pool and the
+// caller's host array must stay untouched, so every exit waits.
+constexpr int64_t kOverlapValues = int64_t(1) << 20;  // entries
+
+bool pinned_host(const void* p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+// the calling thread's copy stream on the current device (created on first
+// use, kept for the thread's lifetime)
+cudaStream_t copy_stream()
+{
+    constexpr int kMaxDev = 64;
+    thread_local cudaStream_t streams[kMaxDev] = {};
+    int dev = 0;
+    OBK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDev) throw Error{-5, "device index out of range"};
+    if (!streams[dev]) OBK_CUDA(cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking));
+    return streams[dev];
+}
+
 struct ValueUpload {
     cudaStream_t st2 = nullptr;
     cudaEvent_t ready = nullptr;
@@ -116,7 +143,7 @@ struct ValueUpload {
     void start(double* dst, const double* src, int64_t n, cudaStream_t st)
     {
         owner = st;
-        OBK_CUDA(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
+        st2 = copy_stream();
         OBK_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
         OBK_CUDA(cudaEventRecord(ready, st));  // dst is allocated in st's order
         OBK_CUDA(cudaStreamWaitEvent(st2, ready, 0));
@@ -138,7 +165,6 @@ struct ValueUpload {
             cudaStreamWaitEvent(owner, ready, 0);
         }
         if (ready) cudaEventDestroy(ready);
-        if (st2) cudaStreamDestroy(st2);
     }
 };
 
@@ -403,7 +429,7 @@ obk_status obk_create_on_stream(const obk_csr* A, int64_t m, int64_t n, double t
             ci_copy.alloc(std::max<int64_t>(nnz, 1), st);
             v_copy.alloc(std::max<int64_t>(nnz, 1), st);
             to_device(ci_copy.p, A->col_idx, nnz, dev, st);
-            if (!dev && nnz > 0) vup.start(v_copy.p, A->val, nnz, st);
+            if (!dev && nnz >= kOverlapValues && pinned_host(A->val)) vup.start(v_copy.p, A->val, nnz, st);
             else to_device(v_copy.p, A->val, nnz, dev, st);
             ci_p = ci_copy.p;
             v_p = v_copy.p;
@@ -769,6 +795,11 @@ namespace obk {
 bool batch_eligible(const obk_handle* h)
 {
     return h && batch_smem_bytes(h->N, h->L.Ngm) <= batch_smem_limit();
+}
+
+void prepare_batch(obk_handle* h)
+{
+    if (h) ensure_gm_csr(h->L, h->st);
 }
 
 void* handle_stream(const obk_handle* h) { return h ? (void*)h->st : nullptr; }

@@ -268,6 +268,9 @@ bool pattern_symmetric(int64_t n, const int64_t* rp, const int32_t* ci, int64_t 
 // Transpose of a CSR pattern (nrows x ncols, column indices of each row
 // distinct): column pointers cptr (ncols + 1) and, per column in ascending
 // row order, the row (trow) and the source entry index (tsrc) of each entry.
+// A structurally symmetric square pattern sets *symmetric (when given); its
+// trow equals ci and is filled only when need_trow.
 void transpose_pattern(int64_t nrows, int64_t ncols, const int64_t* rp, const int32_t* ci, int64_t nnz,
-                       DBuf<int64_t>& cptr, DBuf<uint32_t>& trow, DBuf<uint32_t>& tsrc, cudaStream_t st);
+                       DBuf<int64_t>& cptr, DBuf<uint32_t>& trow, DBuf<uint32_t>& tsrc, cudaStream_t st,
+                       bool* symmetric = nullptr, bool need_trow = true);
 }  // namespace obk

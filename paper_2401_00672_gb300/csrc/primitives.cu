@@ -665,8 +665,10 @@ bool pattern_symmetric(int64_t n, const int64_t* rp, const int32_t* ci, int64_t 
 }
 
 void transpose_pattern(int64_t nrows, int64_t ncols, const int64_t* rp, const int32_t* ci, int64_t nnz,
-                       DBuf<int64_t>& cptr, DBuf<uint32_t>& trow, DBuf<uint32_t>& tsrc, cudaStream_t st)
+                       DBuf<int64_t>& cptr, DBuf<uint32_t>& trow, DBuf<uint32_t>& tsrc, cudaStream_t st,
+                       bool* symmetric, bool need_trow)
 {
+    if (symmetric) *symmetric = false;
     constexpr int kT = 256;
     auto grid = [](int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kT), 65535)); };
     cptr.alloc(ncols + 1, st);
@@ -677,8 +679,11 @@ void transpose_pattern(int64_t nrows, int64_t ncols, const int64_t* rp, const in
         // need no counting or sorting: the transpose has the pattern itself
         if (symmetric_pass(nrows, rp, ci, tsrc.p, st)) {
             OBK_CUDA(cudaMemcpyAsync(cptr.p, rp, (nrows + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
-            copy_cols_u32<<<grid(nnz), kT, 0, st>>>(ci, nnz, trow.p);
-            OBK_CHECK_LAUNCH();
+            if (need_trow) {
+                copy_cols_u32<<<grid(nnz), kT, 0, st>>>(ci, nnz, trow.p);
+                OBK_CHECK_LAUNCH();
+            }
+            if (symmetric) *symmetric = true;
             return;
         }
     }

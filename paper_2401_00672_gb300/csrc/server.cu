@@ -206,9 +206,11 @@ static void worker_loop(obk_server* s)
         obk_status rc = obk_create_on_stream(&A, r->m, r->n, r->thr, (void*)st, &h);
         if (rc == OBK_OK && r->opts.precision == 0 && r->opts.pinv_iters == 0 && obk::batch_eligible(h) &&
             !r->cancel.load()) {
-            // small system: stage f (and x0) on the device, then join the ready list
+            // small system: build its group-major rows and stage f (and x0)
+            // on the device, on this worker's stream, then join the ready list
             bool ok = true;
             try {
+                obk::prepare_batch(h);
                 r->fdev.alloc((size_t)r->m, st);
                 r->xdev.alloc((size_t)r->n, st);
                 ok = cudaMemcpyAsync(r->fdev.p, r->f.data(), (size_t)r->m * sizeof(double), cudaMemcpyHostToDevice,

@@ -190,6 +190,19 @@ __global__ void csc_fill(int64_t nnz, const uint32_t* src, const uint32_t* trow,
     }
 }
 
+// The same for a structurally symmetric pattern, where the CSC slot of entry
+// e is tsrc[e] and the entry of slot p is tsrc[p]: coalesced writes only.
+__global__ void csc_fill_symmetric(int64_t nnz, const uint32_t* tsrc, const double* v, double* cval,
+                                   int64_t* pos_of)
+{
+    GRID_STRIDE(p, nnz)
+    {
+        const uint32_t e = tsrc[p];
+        cval[p] = v[e];
+        pos_of[p] = (int64_t)e;
+    }
+}
+
 // ub[i] = number of (earlier row, shared column) incidences of row i; the rank
 // of entry (i, c) in column c counts the earlier rows of that column.
 __global__ void pair_upper_bound(int64_t N, const int64_t* rp, const int32_t* ci, const int64_t* cptr,
@@ -955,11 +968,18 @@ void build_csc(int64_t nrows, int64_t ncols, const int64_t* rp, const int32_t* c
                cudaStream_t st)
 {
     DBuf<uint32_t> trow, tsrc;
-    transpose_pattern(nrows, ncols, rp, ci, nnz, cptr, trow, tsrc, st);
+    bool sym = false;
+    transpose_pattern(nrows, ncols, rp, ci, nnz, cptr, trow, tsrc, st, &sym, false);
     pos_of.alloc(std::max<int64_t>(nnz, 1), st);
     crow.alloc(std::max<int64_t>(nnz, 1), st);
     cval.alloc(std::max<int64_t>(nnz, 1), st);
-    if (nnz) {
+    if (nnz && sym) {
+        // the transpose has the pattern itself: its rows are the column
+        // indices, and the slot map pairs each entry with its mirror both ways
+        OBK_CUDA(cudaMemcpyAsync(crow.p, ci, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        csc_fill_symmetric<<<grid_for(nnz), kBlock, 0, st>>>(nnz, tsrc.p, v, cval.p, pos_of.p);
+        OBK_CHECK_LAUNCH();
+    } else if (nnz) {
         csc_fill<<<grid_for(nnz), kBlock, 0, st>>>(nnz, tsrc.p, trow.p, v, crow.p, cval.p, pos_of.p);
         OBK_CHECK_LAUNCH();
     }

@@ -109,7 +109,8 @@ struct SweepParams {
     const int64_t* gt_ptr;      // G*T + 1: first group-major row of each (group, tile)
     int64_t tile_rows;          // B
     int64_t smem_bytes;         // dynamic shared memory of the launch (staging windows)
-    int staging;                // 1 = stage windows in shared memory when worth it, 0 or 2 = never
+    int staging;
+    int l2_stream;  // slices larger than half the L2: evict-first loads                // 1 = stage windows in shared memory when worth it, 0 or 2 = never
     double* partial;  // gridDim.x
     double* ctrl;     // [0] rr, [1] beta, [2..11] history
     int64_t* out;     // [0] sweeps, [1] status, [2] outer, [3] stop, [4] sweep ns, [5] inner,
@@ -234,12 +235,16 @@ __device__ __forceinline__ void phase1(const SweepParams& p, int64_t r0, int64_t
 // and no separate subtraction.
 
 // The slices' indices and values are read once per sweep: loaded without an
-// L1 line and with an evict-first L2 policy, so that the lines of x and y that
-// the gathers reuse stay cached.  (The matrix is read-only inside the kernel.)
-__device__ __forceinline__ uint64_t stream_policy()
+// L1 line, and, when the sliced matrix is larger than half the L2
+// (SweepParams::l2_stream), with an evict-first L2 policy, so that the lines of
+// x and y that the gathers reuse stay cached.  A matrix that fits in L2 keeps
+// the normal policy and is read from L2 by the next sweep.  (The matrix is
+// read-only inside the kernel.)
+__device__ __forceinline__ uint64_t stream_policy(bool evict_first)
 {
     uint64_t pol;
-    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    if (evict_first) asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    else asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
     return pol;
 }
 __device__ __forceinline__ int32_t ld_stream(const int32_t* p, uint64_t pol)
@@ -265,11 +270,10 @@ __device__ __forceinline__ double ld_stream(const double* p, uint64_t pol)
 // is the first index held by v when v is a window staged in shared memory)
 template <int B, int S, class T>
 __device__ __forceinline__ T sell_batch(const int32_t* idx, const T* vals, const T* v, int64_t q, T acc,
-                                        int32_t off)
+                                        int32_t off, uint64_t pol)
 {
     int32_t c[B];
     T a[B];
-    const uint64_t pol = stream_policy();
 #pragma unroll
     for (int j = 0; j < B; ++j) {
         c[j] = ld_stream(idx + q + 32 * j, pol);
@@ -286,18 +290,18 @@ __device__ __forceinline__ T sell_batch(const int32_t* idx, const T* vals, const
 // one lane's row (or segment) of a slice: len entries from position q
 template <int S, class T>
 __device__ __forceinline__ T sell_lane(const int32_t* idx, const T* vals, const T* v, int64_t q, int64_t len, T acc,
-                                       int32_t off = 0)
+                                       int32_t off, uint64_t pol)
 {
     int64_t j = 0;
-    for (; j + kBatch <= len; j += kBatch, q += 32 * kBatch) acc = sell_batch<kBatch, S, T>(idx, vals, v, q, acc, off);
+    for (; j + kBatch <= len; j += kBatch, q += 32 * kBatch) acc = sell_batch<kBatch, S, T>(idx, vals, v, q, acc, off, pol);
     switch ((int)(len - j)) {  // the same for the whole warp
-        case 7: acc = sell_batch<7, S, T>(idx, vals, v, q, acc, off); break;
-        case 6: acc = sell_batch<6, S, T>(idx, vals, v, q, acc, off); break;
-        case 5: acc = sell_batch<5, S, T>(idx, vals, v, q, acc, off); break;
-        case 4: acc = sell_batch<4, S, T>(idx, vals, v, q, acc, off); break;
-        case 3: acc = sell_batch<3, S, T>(idx, vals, v, q, acc, off); break;
-        case 2: acc = sell_batch<2, S, T>(idx, vals, v, q, acc, off); break;
-        case 1: acc = sell_batch<1, S, T>(idx, vals, v, q, acc, off); break;
+        case 7: acc = sell_batch<7, S, T>(idx, vals, v, q, acc, off, pol); break;
+        case 6: acc = sell_batch<6, S, T>(idx, vals, v, q, acc, off, pol); break;
+        case 5: acc = sell_batch<5, S, T>(idx, vals, v, q, acc, off, pol); break;
+        case 4: acc = sell_batch<4, S, T>(idx, vals, v, q, acc, off, pol); break;
+        case 3: acc = sell_batch<3, S, T>(idx, vals, v, q, acc, off, pol); break;
+        case 2: acc = sell_batch<2, S, T>(idx, vals, v, q, acc, off, pol); break;
+        case 1: acc = sell_batch<1, S, T>(idx, vals, v, q, acc, off, pol); break;
         default: break;
     }
     return acc;
@@ -323,7 +327,7 @@ __device__ __forceinline__ void row_slice(const SweepParams& p, int64_t s, const
     bool valid = lane < p.sl_nrow[s];
     int64_t k = p.sl_row0[s] + lane;
     T acc = valid ? (T)rhs[k] : T(0);
-    acc = sell_lane<-1, T>(p.sci, sval, xv, base + lane, len, acc, xoff);
+    acc = sell_lane<-1, T>(p.sci, sval, xv, base + lane, len, acc, xoff, stream_policy(p.l2_stream));
     if (valid) y[k] = acc * inv[k];
 }
 
@@ -336,7 +340,7 @@ __device__ __forceinline__ void row_slice_at(const SweepParams& p, int64_t s, in
     const bool valid = lane < p.sl_nrow[s];
     const int64_t k = k0 + lane;
     T acc = valid ? (T)rhs[k] : T(0);
-    acc = sell_lane<-1, T>(p.sci, sval, xv, b0 + lane, (b1 - b0) >> 5, acc, 0);
+    acc = sell_lane<-1, T>(p.sci, sval, xv, b0 + lane, (b1 - b0) >> 5, acc, 0, stream_policy(p.l2_stream));
     if (valid) y[k] = acc * inv[k];
 }
 
@@ -349,7 +353,7 @@ __device__ __forceinline__ void col_slice(const SweepParams& p, int64_t s, const
     int64_t base = p.ml_ptr[s], len = (p.ml_ptr[s + 1] - base) >> 5;
     int32_t c = p.mcol[s * 32 + lane];
     T acc = c >= 0 ? xv[c] : T(0);
-    acc = sell_lane<1, T>(p.mrow, mval, y, base + lane, len, acc, yoff);
+    acc = sell_lane<1, T>(p.mrow, mval, y, base + lane, len, acc, yoff, stream_policy(p.l2_stream));
     if (c >= 0) xv[c] = acc;
 }
 
@@ -360,7 +364,7 @@ __device__ __forceinline__ void col_slice_at(const SweepParams& p, int32_t c, in
 {
     const int lane = threadIdx.x & 31;
     T acc = c >= 0 ? xv[c] : T(0);
-    acc = sell_lane<1, T>(p.mrow, mval, y, b0 + lane, (b1 - b0) >> 5, acc, 0);
+    acc = sell_lane<1, T>(p.mrow, mval, y, b0 + lane, (b1 - b0) >> 5, acc, 0, stream_policy(p.l2_stream));
     if (c >= 0) xv[c] = acc;
 }
 
@@ -455,7 +459,7 @@ __device__ void residual_partial(const SweepParams& p, bool store_r)
             bool valid = lane < p.sl_nrow[s];
             int64_t k = p.sl_row0[s] + lane;
             double acc = valid ? p.f[k] : 0.0;
-            acc = sell_lane<-1, double>(p.sci, p.sv, p.x, base + lane, len, acc);
+            acc = sell_lane<-1, double>(p.sci, p.sv, p.x, base + lane, len, acc, 0, stream_policy(p.l2_stream));
             if (valid) {
                 if (store_r) p.r64[k] = acc;
                 local = fma(acc, acc, local);
@@ -1117,6 +1121,10 @@ SolveResult run_solve(const SweepLayout& L, const double* f_gm, double fnorm2, d
     p.gt_ptr = L.gt_ptr.p;
     p.tile_rows = L.B;
     p.staging = a.staging;
+    {
+        const double sliced = (double)(L.sell_nnz + L.msell_nnz) * (4.0 + (a.precision == 1 ? 4.0 : 8.0));
+        p.l2_stream = sliced > 0.5 * (double)dev_info().l2_bytes ? 1 : 0;
+    }
     p.ctrl = ctrl.p;
     p.out = out.p;
     p.gb = GridBarrier{bar.p, d_err, a.spin_limit};

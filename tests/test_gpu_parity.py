@@ -600,6 +600,35 @@ def test_invalid_inputs(obk):
             h.solve(s.f, tol=0.0)
 
 
+def test_large_pinned_host_matrix(obk):
+    # a matrix of more than 2^20 entries in pinned host memory takes the path
+    # whose value copy overlaps the reordering (finiteness checked after it):
+    # the same setup and solution as from device arrays, and a NaN still
+    # rejected as invalid input
+    import torch
+
+    s = synth.random_dominant(150000, 7, seed=1011)
+    A = s.A
+    assert A.nnz >= 1 << 20
+    rp_h = torch.from_numpy(A.row_ptr).pin_memory()
+    ci_h = torch.from_numpy(A.col_idx).pin_memory()
+    v_h = torch.from_numpy(A.val).pin_memory()
+    dev = torch.device("cuda:0")
+    with obk.Handle(rp_h, ci_h, v_h, A.m, A.n) as hh, \
+            obk.Handle(rp_h.to(dev), ci_h.to(dev), v_h.to(dev), A.m, A.n) as hd:
+        assert np.array_equal(hh.perm(), hd.perm())
+        assert np.array_equal(hh.groups(), hd.groups())
+        assert np.array_equal(hh.row_norms().view(np.uint64), hd.row_norms().view(np.uint64))
+        _, xh, _ = hh.solve(s.f, tol=1e-8, maxit=2000)
+        _, xd, _ = hd.solve(s.f, tol=1e-8, maxit=2000)
+        assert np.array_equal(xh, xd)
+    v_bad = v_h.clone().pin_memory()
+    v_bad[A.nnz // 2] = float("nan")
+    with pytest.raises(obk.ObkError) as e:
+        obk.Handle(rp_h, ci_h, v_bad, A.m, A.n)
+    assert e.value.status == obk.OBK_ERR_INVALID and "non-finite" in str(e.value)
+
+
 def test_bounded_wait_times_out_and_context_survives(obk):
     # a wait limit of a few polls cannot cover the grid barrier of a multi-block
     # sweep: the kernel must give up, report OBK_ERR_TIMEOUT, and leave the
