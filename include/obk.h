@@ -52,7 +52,10 @@ typedef enum {
  * to nnz; columns strictly increase inside each row (sorted, no duplicates);
  * values are finite.  device_ptrs = 1 when the three arrays live in device
  * memory of the current device (obk_create then reads col_idx and val in place
- * while it runs and keeps its own permuted copy), 0 for host memory. */
+ * while it runs and keeps its own permuted copy), 0 for host memory (copied;
+ * pinned arrays of at least 2^20 entries have their values copied on a second
+ * stream of the calling thread while the pattern is reordered).  Host arrays
+ * must stay unchanged until obk_create returns. */
 typedef struct {
     const int64_t* row_ptr;
     const int32_t* col_idx;
