@@ -384,11 +384,16 @@ def test_autotune_keeps_results_and_parity(obk):
         assert t["staging"] in ("global", "shared") and t["sync"] in ("barriers", "counters") and t["sweep_ms"] > 0
         key = (t["rows_per_warp"], t["block_threads"], t["sync"], t["staging"])
         assert t["candidate_ms"][key] == t["sweep_ms"]
+        # a timed candidate reads a positive time (0 = skipped), and the kept one is the fastest
+        assert all(ms >= 0 for ms in t["candidate_ms"].values())
+        assert t["sweep_ms"] == min(ms for ms in t["candidate_ms"].values() if ms > 0)
         timed = [k for k, ms in t["candidate_ms"].items() if ms > 0]
         assert {(32, b, "counters", p) for b in (1024, 512) for p in ("global", "shared")} <= set(timed)
         assert {(32, b, "barriers", "global") for b in (1024, 512)} <= set(timed)
         t1 = h.autotune(1)
         assert t1["rows_per_warp"] in (1, 2, 4, 8, 16, 32)
+        assert all(ms >= 0 for ms in t1["candidate_ms"].values())
+        assert t1["sweep_ms"] == min(ms for ms in t1["candidate_ms"].values() if ms > 0)
         st, x, info = h.solve(s.f, None, tol=1e-300, maxit=5)  # the tuned FP64 setting
         assert info.sweeps == 5
         assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) <= XTOL
