@@ -76,6 +76,14 @@ void permute_csr(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
                  cudaStream_t st);
 
 // Everything the sweep needs, in device memory.
+// Mirror slices of a (group, tile) piece with at least kMirrorDoubleMin
+// column segments hold two segments per lane, entries interleaved (the
+// sweep's phase 2 folds both of a lane's columns in one pass over its
+// entries); a smaller piece keeps one segment per lane, so that its few
+// slices still spread over a block's warps.
+constexpr int64_t kMirrorDoubleMin = 4096;
+constexpr int32_t kOneColumn = -2;  // second column word of a one-column mirror slice
+
 struct SweepLayout {
     int64_t N = 0, nnz = 0;
     int64_t G = 0;          // groups
@@ -137,7 +145,7 @@ struct SweepLayout {
     DBuf<double> sv;                 // sell_nnz
     DBuf<float> sv32;                // sell_nnz (precision form)
     DBuf<int64_t> ml_ptr;            // nms+1
-    DBuf<int32_t> mcol;              // 32 nms, column of each slice lane (-1: padding)
+    DBuf<int32_t> mcol;              // 64 nms: the two columns of each slice lane (-1: none)
     DBuf<int32_t> mrow;              // msell_nnz, group-major row index
     DBuf<double> mv;                 // msell_nnz
     DBuf<float> mv32;                // msell_nnz
@@ -153,6 +161,7 @@ struct SweepLayout {
     DBuf<int64_t> gt_ptr, gts_ptr;          // G*T + 1 (device)
     std::vector<int64_t> h_sl_tptr, h_ml_tptr;  // G*T + 1
     DBuf<int64_t> sl_tptr, ml_tptr;         // device copies
+    std::vector<int32_t> h_ml_pdbl;             // G*T: the piece's mirror slices hold two segments per lane
     DBuf<int32_t> reach_lo, reach_hi;       // T
     // largest staging windows of a one-tile block: x columns of its reach, and
     // group-major rows of one group in its reach

@@ -898,14 +898,100 @@ __global__ void sell_fill(int64_t ns, const int64_t* sl_ptr, const int64_t* row0
     }
 }
 
-__global__ void sell_mcol(int64_t nms, const int64_t* row0, const int32_t* nrow, const int32_t* seg_col,
-                          const uint32_t* order, int32_t* mcol)
+// Mirror slices of a (group, tile) piece with at least kMirrorDoubleMin
+// segments hold 64 of them: lane l takes the neighbouring segments row0 + 2l
+// (column a) and row0 + 2l + 1 (column b), of about the same length in the
+// length order, their entries interleaved (even positions a, odd positions b,
+// the shorter one padded), so that a slice costs one round of loads and
+// gathers for twice the entries and the two columns' sums run as independent
+// chains.  Slices of a smaller piece hold 32 segments, one per lane; their
+// second column word is kOneColumn, which tells the sweep the format (dbl[s]
+// tells msell_fill).
+__global__ void msell_lengths(int64_t nms, int64_t G, const int64_t* sg, const int64_t* item_g, const int64_t* ptr,
+                              const uint32_t* order, const int32_t* pdbl, int64_t* slen, int64_t* row0, int32_t* nrow,
+                              int32_t* dbl)
+{
+    GRID_STRIDE(s, nms)
+    {
+        int64_t lo = 0, hi = G;  // piece of slice s: largest g with sg[g] <= s
+        while (hi - lo > 1) {
+            int64_t mid = (lo + hi) >> 1;
+            if (sg[mid] <= s) lo = mid;
+            else hi = mid;
+        }
+        const int64_t w = pdbl[lo] ? 64 : 32;
+        const int64_t k0 = item_g[lo] + (s - sg[lo]) * w;
+        const int64_t k1 = k0 + w < item_g[lo + 1] ? k0 + w : item_g[lo + 1];
+        int64_t mx = 0;
+        for (int64_t k = k0; k < k1; ++k) {
+            const int64_t r = order[k];
+            mx = max(mx, ptr[r + 1] - ptr[r]);
+        }
+        slen[s] = w * mx;  // 32 lanes x (1 or 2 segments) x the longest segment
+        row0[s] = k0;
+        nrow[s] = (int32_t)(k1 - k0);
+        dbl[s] = pdbl[lo];
+    }
+}
+
+// entries and lane columns (mcol[64 s + l] = a, mcol[64 s + 32 + l] = b) of the
+// mirror slices; a padding entry (value 0) repeats the last index of its
+// column's segment, or the first index of the slice's first segment for a
+// column without one, so that its load stays inside the band
+__global__ void msell_fill(int64_t nms, const int64_t* ml_ptr, const int64_t* row0, const int32_t* nrow,
+                           const int32_t* dbl, const int64_t* ptr, const uint32_t* order, const int32_t* seg_col,
+                           const int32_t* idx, const double* val, int32_t* sidx, double* sval, float* sval32,
+                           int32_t* mcol)
 {
     GRID_STRIDE(t, nms * 32)
     {
-        int64_t s = t >> 5;
-        int lane = (int)(t & 31);
-        mcol[t] = lane < nrow[s] ? seg_col[item_row(order, row0[s] + lane)] : -1;
+        const int64_t s = t >> 5;
+        const int lane = (int)(t & 31);
+        const int64_t base = ml_ptr[s], len = (ml_ptr[s + 1] - base) >> 5;
+        const int n = nrow[s];
+        if (!dbl[s]) {  // one segment per lane, entries in order
+            const bool va = lane < n;
+            const int64_t ra = va ? (int64_t)order[row0[s] + lane] : 0;
+            const int64_t ba = va ? ptr[ra] : 0, la = va ? ptr[ra + 1] - ba : 0;
+            const int32_t pad = la > 0 ? idx[ba + la - 1] : idx[ptr[order[row0[s]]]];
+            for (int64_t j = 0; j < len; ++j) {
+                const int64_t q = base + 32 * j + lane;
+                const bool live = j < la;
+                const double a = live ? val[ba + j] : 0.0;
+                sidx[q] = live ? idx[ba + j] : pad;
+                sval[q] = a;
+                if (sval32) sval32[q] = (float)a;
+            }
+            mcol[s * 64 + lane] = va ? seg_col[ra] : -1;
+            mcol[s * 64 + 32 + lane] = kOneColumn;
+            continue;
+        }
+        const bool va = 2 * lane < n, vb = 2 * lane + 1 < n;
+        const int64_t ra = va ? (int64_t)order[row0[s] + 2 * lane] : 0;
+        const int64_t rb = vb ? (int64_t)order[row0[s] + 2 * lane + 1] : 0;
+        const int64_t ba = va ? ptr[ra] : 0, la = va ? ptr[ra + 1] - ba : 0;
+        const int64_t bb = vb ? ptr[rb] : 0, lb = vb ? ptr[rb + 1] - bb : 0;
+        const int32_t first = idx[ptr[order[row0[s]]]];
+        const int32_t pad_a = la > 0 ? idx[ba + la - 1] : first;
+        const int32_t pad_b = lb > 0 ? idx[bb + lb - 1] : pad_a;
+        for (int64_t j = 0; j < len; ++j) {
+            const int64_t q = base + 32 * j + lane;
+            const int64_t u = j >> 1;
+            int32_t c;
+            double a = 0.0;
+            if ((j & 1) == 0) {
+                c = pad_a;
+                if (u < la) { c = idx[ba + u]; a = val[ba + u]; }
+            } else {
+                c = pad_b;
+                if (u < lb) { c = idx[bb + u]; a = val[bb + u]; }
+            }
+            sidx[q] = c;
+            sval[q] = a;
+            if (sval32) sval32[q] = (float)a;
+        }
+        mcol[s * 64 + lane] = va ? seg_col[ra] : -1;
+        mcol[s * 64 + 32 + lane] = vb ? seg_col[rb] : -1;
     }
 }
 
@@ -1215,23 +1301,24 @@ void build_sell(SweepLayout& L, const int64_t* rp, const int32_t* ci, const doub
     DBuf<int64_t> mlen(std::max<int64_t>(nms, 1), st), mrow0(std::max<int64_t>(nms, 1), st);
     DBuf<int32_t> mnrow(std::max<int64_t>(nms, 1), st);
     L.ml_ptr.alloc(nms + 1, st);
+    DBuf<int32_t> mdbl(std::max<int64_t>(nms, 1), st);
     if (nms) {
-        sell_lengths<uint32_t><<<grid_for(nms), kBlock, 0, st>>>(nms, nsegs, L.ml_tptr.p, L.gts_ptr.p, L.seg_ptr.p,
-                                                                 L.seg_order.p, mlen.p, mrow0.p, mnrow.p);
+        DBuf<int32_t> pdbl(std::max<int64_t>(nsegs, 1), st);
+        OBK_CUDA(cudaMemcpyAsync(pdbl.p, L.h_ml_pdbl.data(), nsegs * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        msell_lengths<<<grid_for(nms), kBlock, 0, st>>>(nms, nsegs, L.ml_tptr.p, L.gts_ptr.p, L.seg_ptr.p,
+                                                         L.seg_order.p, pdbl.p, mlen.p, mrow0.p, mnrow.p, mdbl.p);
         OBK_CHECK_LAUNCH();
     }
     exclusive_scan_i64(mlen.p, L.ml_ptr.p, nms, st);
     L.msell_nnz = read_scalar(L.ml_ptr.p + nms, st);
-    L.mcol.alloc(std::max<int64_t>(nms * 32, 1), st);
+    L.mcol.alloc(std::max<int64_t>(nms * 64, 1), st);
     L.mrow.alloc(std::max<int64_t>(L.msell_nnz, 1), st);
     L.mv.alloc(std::max<int64_t>(L.msell_nnz, 1), st);
     if (want_fp32) L.mv32.alloc(std::max<int64_t>(L.msell_nnz, 1), st);
     if (nms) {
-        sell_mcol<<<grid_for(nms * 32), kBlock, 0, st>>>(nms, mrow0.p, mnrow.p, L.seg_col.p, L.seg_order.p, L.mcol.p);
-        OBK_CHECK_LAUNCH();
-        sell_fill<int32_t, uint32_t><<<grid_for(nms * 32), kBlock, 0, st>>>(
-            nms, L.ml_ptr.p, mrow0.p, mnrow.p, L.seg_ptr.p, L.seg_order.p, L.mir_row.p, L.mir_val.p, L.mrow.p, L.mv.p,
-            want_fp32 ? L.mv32.p : nullptr);
+        msell_fill<<<grid_for(nms * 32), kBlock, 0, st>>>(nms, L.ml_ptr.p, mrow0.p, mnrow.p, mdbl.p, L.seg_ptr.p,
+                                                          L.seg_order.p, L.seg_col.p, L.mir_row.p, L.mir_val.p,
+                                                          L.mrow.p, L.mv.p, want_fp32 ? L.mv32.p : nullptr, L.mcol.p);
         OBK_CHECK_LAUNCH();
     }
 }
@@ -1488,8 +1575,12 @@ void group_build(int64_t N, const int64_t* rp, const int32_t* ci, const double* 
                                  st));
         OBK_CUDA(cudaStreamSynchronize(st));
         L.h_ml_tptr.assign(nsegs + 1, 0);
-        for (int64_t q = 0; q < nsegs; ++q)
-            L.h_ml_tptr[q + 1] = L.h_ml_tptr[q] + ceil_div(h_gts[q + 1] - h_gts[q], (int64_t)32);
+        L.h_ml_pdbl.assign(nsegs, 0);
+        for (int64_t q = 0; q < nsegs; ++q) {
+            const int64_t items = h_gts[q + 1] - h_gts[q];
+            L.h_ml_pdbl[q] = items >= kMirrorDoubleMin ? 1 : 0;
+            L.h_ml_tptr[q + 1] = L.h_ml_tptr[q] + ceil_div(items, (int64_t)(L.h_ml_pdbl[q] ? 64 : 32));
+        }
         L.gts_ptr = std::move(gts_ptr);
     }
     mark();

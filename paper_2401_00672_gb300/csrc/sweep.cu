@@ -344,28 +344,75 @@ __device__ __forceinline__ void row_slice_at(const SweepParams& p, int64_t s, in
     if (valid) y[k] = acc * inv[k];
 }
 
-// one mirror slice s: xv_c += sum_k A_kc y_k for its (up to) 32 columns
+// Mirror slices: lane l holds two columns, a and b (neighbouring segments),
+// their entries interleaved: even positions a, odd positions b.  Each column's
+// sum starts from x at the column and adds its entries in order, as for one
+// segment per lane; the two sums are independent chains.
+template <int B, class T>
+__device__ __forceinline__ void mirror_batch(const int32_t* idx, const T* vals, const T* y, int64_t q, T& acc_a,
+                                             T& acc_b, int32_t off, uint64_t pol)
+{
+    static_assert(B % 2 == 0, "entries come in (a, b) pairs");
+    int32_t c[B];
+    T a[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+        c[j] = ld_stream(idx + q + 32 * j, pol);
+        a[j] = ld_stream(vals + q + 32 * j, pol);
+    }
+    T g[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) g[j] = y[c[j] - off];
+#pragma unroll
+    for (int j = 0; j < B; j += 2) {
+        acc_a = fma(a[j], g[j], acc_a);
+        acc_b = fma(a[j + 1], g[j + 1], acc_b);
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void mirror_lane(const int32_t* idx, const T* vals, const T* y, int64_t q, int64_t len,
+                                            T& acc_a, T& acc_b, int32_t off, uint64_t pol)
+{
+    int64_t j = 0;
+    for (; j + kBatch <= len; j += kBatch, q += 32 * kBatch)
+        mirror_batch<kBatch, T>(idx, vals, y, q, acc_a, acc_b, off, pol);
+    switch ((int)(len - j)) {  // even, the same for the whole warp
+        case 6: mirror_batch<6, T>(idx, vals, y, q, acc_a, acc_b, off, pol); break;
+        case 4: mirror_batch<4, T>(idx, vals, y, q, acc_a, acc_b, off, pol); break;
+        case 2: mirror_batch<2, T>(idx, vals, y, q, acc_a, acc_b, off, pol); break;
+        default: break;
+    }
+}
+
+// one mirror slice whose lane columns ca, cb (cb = kOneColumn: one column
+// per lane) and entries [b0, b1) are known: xv_c += sum_k A_kc y_k for its
+// (up to) 32 or 64 columns
+template <class T>
+__device__ __forceinline__ void col_slice_at(const SweepParams& p, int32_t ca, int32_t cb, int64_t b0, int64_t b1,
+                                             const T* mval, const T* y, T* xv, int32_t yoff = 0)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t pol = stream_policy(p.l2_stream);
+    T acc_a = ca >= 0 ? xv[ca] : T(0);
+    if (cb != kOneColumn) {  // the same for the whole warp
+        T acc_b = cb >= 0 ? xv[cb] : T(0);
+        mirror_lane<T>(p.mrow, mval, y, b0 + lane, (b1 - b0) >> 5, acc_a, acc_b, yoff, pol);
+        if (cb >= 0) xv[cb] = acc_b;
+    } else {
+        acc_a = sell_lane<1, T>(p.mrow, mval, y, b0 + lane, (b1 - b0) >> 5, acc_a, yoff, pol);
+    }
+    if (ca >= 0) xv[ca] = acc_a;
+}
+
+// one mirror slice s
 template <class T>
 __device__ __forceinline__ void col_slice(const SweepParams& p, int64_t s, const T* mval, const T* y, T* xv,
                                           int32_t yoff = 0)
 {
-    int lane = threadIdx.x & 31;
-    int64_t base = p.ml_ptr[s], len = (p.ml_ptr[s + 1] - base) >> 5;
-    int32_t c = p.mcol[s * 32 + lane];
-    T acc = c >= 0 ? xv[c] : T(0);
-    acc = sell_lane<1, T>(p.mrow, mval, y, base + lane, len, acc, yoff, stream_policy(p.l2_stream));
-    if (c >= 0) xv[c] = acc;
-}
-
-// one mirror slice whose lane column c and entries [b0, b1) were loaded ahead
-template <class T>
-__device__ __forceinline__ void col_slice_at(const SweepParams& p, int32_t c, int64_t b0, int64_t b1, const T* mval,
-                                             const T* y, T* xv)
-{
     const int lane = threadIdx.x & 31;
-    T acc = c >= 0 ? xv[c] : T(0);
-    acc = sell_lane<1, T>(p.mrow, mval, y, b0 + lane, (b1 - b0) >> 5, acc, 0, stream_policy(p.l2_stream));
-    if (c >= 0) xv[c] = acc;
+    col_slice_at<T>(p, p.mcol[s * 64 + lane], p.mcol[s * 64 + 32 + lane], p.ml_ptr[s], p.ml_ptr[s + 1], mval, y, xv,
+                    yoff);
 }
 
 // phase 1 over all row slices of group g (whole grid)
@@ -780,21 +827,23 @@ __device__ bool flow_sweep(const SweepParams& p, FlowState& f, const T* sval, co
                 // bounds and columns are loaded while this one runs.
                 const int lane = threadIdx.x & 31;
                 int64_t s = m0 + w, nb0 = 0, nb1 = 0;
-                int32_t nc = -1;
+                int32_t nca = -1, ncb = -1;
                 if (s < m1) {
                     nb0 = p.ml_ptr[s];
                     nb1 = p.ml_ptr[s + 1];
-                    nc = p.mcol[s * 32 + lane];
+                    nca = p.mcol[s * 64 + lane];
+                    ncb = p.mcol[s * 64 + 32 + lane];
                 }
                 for (; s < m1; s += nw) {
                     const int64_t b0 = nb0, b1 = nb1;
-                    const int32_t c = nc;
+                    const int32_t ca = nca, cb = ncb;
                     if (s + nw < m1) {
                         nb0 = p.ml_ptr[s + nw];
                         nb1 = p.ml_ptr[s + nw + 1];
-                        nc = p.mcol[(s + nw) * 32 + lane];
+                        nca = p.mcol[(s + nw) * 64 + lane];
+                        ncb = p.mcol[(s + nw) * 64 + 32 + lane];
                     }
-                    col_slice_at<T>(p, c, b0, b1, mval, y, xv);
+                    col_slice_at<T>(p, ca, cb, b0, b1, mval, y, xv);
                 }
             }
             flow_done(p, f);

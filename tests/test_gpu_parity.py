@@ -775,6 +775,30 @@ def test_full_size_knn_1m_parity(obk):
     assert np.linalg.norm(x2 - x_o) / np.linalg.norm(x_o) <= XTOL
 
 
+def test_knn_2m_two_column_mirror_slices(obk):
+    # at n = 2,000,000 the largest groups' (group, tile) pieces hold more than
+    # 4096 column segments, so their mirror slices carry two columns per lane
+    # (the smaller groups' one): setup bit-exact, the FP64 x after a fixed
+    # number of sweeps and the FP32 + refinement x within 1e-9 of the oracle
+    s = synth.knn_dominant(2_000_000, 12, seed=1012)
+    A = s.A
+    k = 6
+    st_o, x_o, io, perm_o, gof_o = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1, tol=1e-300,
+                                                maxit=k, return_setup=True)
+    with obk.Handle(A.row_ptr, A.col_idx, A.val, A.m, A.n, thr=0.1) as h:
+        assert np.array_equal(h.perm(), perm_o)
+        assert np.array_equal(h.groups(), gof_o)
+        for sync in (1, 2):
+            _, x, info = h.solve(s.f, tol=1e-300, maxit=k, opts=obk.Opts(sync_mode=sync))
+            assert info.sweeps == k
+            assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) <= XTOL
+        st, x32, info = h.solve(s.f, tol=1e-10, maxit=20000, opts=obk.Opts(precision=1))
+        assert st == obk.OBK_OK and info.rel_res <= 1e-10
+    st64, x64, _ = oracle.solve(A.m, A.n, A.row_ptr, A.col_idx, A.val, s.f, thr=0.1, tol=1e-10, maxit=20000)
+    assert st64 == oracle.OK
+    assert np.linalg.norm(x32 - x64) / np.linalg.norm(x64) <= XTOL
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_cosine_stats_bit_exact(obk, name):
     """Definitions 1-2 from the GPU equal the oracle's on the permuted matrix."""
