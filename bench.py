@@ -69,7 +69,7 @@ def sweep_traffic(name: str):
         return None
 
 
-PRECISION = {"knn4m_ir": 1, "knn1m_ir": 1}  # workloads of the precision form; the rest run FP64
+PRECISION = {"knn4m_ir": 1, "knn2m_ir": 1, "knn1m_ir": 1}  # workloads of the precision form; the rest run FP64
 
 
 def workload(name: str, rank: int):
@@ -78,6 +78,10 @@ def workload(name: str, rank: int):
     if name == "knn4m_ir":
         s = synth.knn_dominant(4_000_000, 12, seed=replica_seed(1003, rank))
         return s, dict(workload="knn_n4e6_12nn_fp32_sweeps_fp64_refinement", n=4_000_000, knn=12, diag_factor=1.2,
+                       thr=0.1, tol=1e-10, precision="FP32 inner sweeps inside FP64 iterative refinement")
+    if name == "knn2m_ir":  # the traffic capture of the 4M sweep (same slice formats, a few GB on the device)
+        s = synth.knn_dominant(2_000_000, 12, seed=replica_seed(1003, rank))
+        return s, dict(workload="knn_n2e6_12nn_fp32_sweeps_fp64_refinement", n=2_000_000, knn=12, diag_factor=1.2,
                        thr=0.1, tol=1e-10, precision="FP32 inner sweeps inside FP64 iterative refinement")
     if name == "knn1m_ir":
         s = synth.knn_dominant(1_000_000, 12, seed=replica_seed(1003, rank))
