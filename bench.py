@@ -788,9 +788,13 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     infos = []
+    step_ev = []  # an event after each step: per-step times, the timed region unchanged
     for _ in range(args.steps):
         st, info = step()
         infos.append((st, info))
+        e_ = torch.cuda.Event(enable_timing=True)
+        e_.record(stream)
+        step_ev.append(e_)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -798,6 +802,7 @@ def main():
     launches = obk.kernel_launches() - launches0
     clocks = sampler.stop()
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, dev)
+    step_ms = [round(a.elapsed_time(b), 3) for a, b in zip([ev0] + step_ev[:-1], step_ev)]
     st, info = infos[-1]
     xh = x.cpu().numpy()
     err_xstar = float(np.linalg.norm(xh - s.xstar) / np.linalg.norm(s.xstar))
@@ -877,14 +882,19 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        e_steps = []
         for _ in range(k2):
             step_host()
+            e_ = torch.cuda.Event(enable_timing=True)
+            e_.record(stream)
+            e_steps.append(e_)
         e1.record(stream)
         torch.cuda.synchronize()
         ems = max_over_ranks(e0.elapsed_time(e1) / k2, dist, dev)
+        e2e_steps = [round(a.elapsed_time(b), 3) for a, b in zip([e0] + e_steps[:-1], e_steps)]
         h2d = A.row_ptr.nbytes + A.col_idx.nbytes + A.val.nbytes + s.f.nbytes
         e2e = {"value": ems / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(A.n * 8), "steps": k2}
+               "d2h_bytes_per_step": int(A.n * 8), "steps": k2, "step_ms": e2e_steps}
 
     parity = None
     if rank == 0 and prec == 1 and not args.no_extras:
@@ -909,7 +919,8 @@ def main():
     if rank == 0:
         line = {
             "metric": "time_to_solution", "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "step_ms": step_ms, "higher_is_better": False,
+            "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64" if prec == 1 else "f64", "data": "synthetic",
             "config": dict(cfg, parallelism=f"replicas{world}", l2="inputs larger than L2 (A = "
                            f"{(A.val.nbytes + A.col_idx.nbytes) / 1e6:.0f} MB), no flush"),
